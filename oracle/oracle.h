@@ -1,0 +1,137 @@
+/*
+ * oracle.h -- plain, slow FP64 CPU oracle of the multi-channel octree ray
+ * caster (Brix, Prassni, Hinrichs: "Visualization of Large Volumetric
+ * Multi-Channel Microscopy Data Streams on Standard PCs").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, loads or
+ * calls this code; only the tests, the smoke check and the benchmark's CPU
+ * baseline do.  It shares no source with the CUDA path.
+ *
+ * What it computes (each function cites the passage it follows):
+ *   - volume state: level-0 values (last writer wins, background where never
+ *     inserted), the mip levels by iterated round-half-up 2x2x2 means over
+ *     in-volume children (Sec. "CPU Data Structure", Eq. 1, "Incremental
+ *     Construction" step 2, "Handling Volumes of Arbitrary Dimensions"),
+ *     per-node min/max/AVG and the homogeneity flags (same sections, and
+ *     "Handling Multi-Channel Data");
+ *   - the render of Algorithm 1: per ray, fixed-step march, node at the
+ *     screen-space-error level by descent from the root, AVG or trilinear
+ *     sample per channel, per-channel transfer function, emission-absorption
+ *     compositing inside the channel loop, early ray termination;
+ *   - the exact FP64 adjoint of that render with respect to the transfer
+ *     function tables and the per-channel intensity scales.
+ *
+ * Precision: values, interpolation, transfer functions, compositing and
+ * gradients are FP64.  Ray GEOMETRY (directions, entry/exit, sample
+ * positions, level and node choice) is evaluated in IEEE single precision in
+ * a fixed operation order, because those quantities decide integers (the
+ * level, the node) and the CUDA path takes the same decisions in single
+ * precision.  The ERT decision (A >= ert) compares accumulated opacity and
+ * cannot be mirrored; the oracle reports every admissible stopping state in
+ * the band |A - ert| < OR_ERT_BAND.
+ *
+ * Parity pins: see tests/test_oracle_*.py (closed forms, hand-computed
+ * golden values, invariants, brute force on tiny inputs).
+ */
+#ifndef VR_ORACLE_H
+#define VR_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OR_MAXL 16
+#define OR_MAXC 4
+#define OR_MAXCAND 4
+#define OR_ERT_BAND 2e-4
+
+typedef struct {
+    int64_t dim[3];          /* level-0 extent X, Y, Z */
+    int C;                   /* channels */
+    int M;                   /* brick interior edge (even) */
+    int N;                   /* levels 0..N */
+    int64_t ldim[OR_MAXL][3]; /* real extent of level L: ceil(ldim[L-1] / 2) */
+    int64_t nb[OR_MAXL][3];   /* node grid of level L: ceil(ldim[L] / M) */
+    uint16_t bg;             /* background value of never-inserted voxels */
+    uint16_t tau;            /* homogeneity threshold (max - min < tau) */
+} or_geom;
+
+typedef struct {
+    int touched;      /* some in-volume level-0 voxel of the region was inserted */
+    int has_children; /* L > 0 and touched and not subtree-homogeneous */
+    int has_brick;    /* touched and not brick-homogeneous */
+    int brick_homog, subtree_homog;
+    uint16_t avg[OR_MAXC];
+    uint16_t bmin[OR_MAXC], bmax[OR_MAXC]; /* over the brick's in-volume level-L voxels */
+    uint16_t smin[OR_MAXC], smax[OR_MAXC]; /* over the node's in-volume level-0 voxels */
+    int64_t count;                         /* in-volume level-L voxels of the brick */
+} or_node;
+
+typedef struct or_volume or_volume;
+
+/* Geometry of the level hierarchy; returns 0 or -1 on invalid arguments. */
+int or_geom_init(or_geom* g, const int64_t dim[3], int C, int M, uint16_t bg, uint16_t tau);
+
+/* ---- dense volume: every level held as a flat array ---- */
+or_volume* or_dense_create(const int64_t dim[3], int C, int M, uint16_t bg, uint16_t tau);
+/* Insert a block (origin, extent) of values [ez][ey][ex][C]; overwrites (last writer wins). */
+int or_dense_insert(or_volume* v, const int64_t origin[3], const int64_t extent[3], const uint16_t* block);
+/* Recompute levels 1..N and all node records from level 0 and the inserted mask. */
+int or_dense_build(or_volume* v, int threads);
+/* Level L as [Z_L][Y_L][X_L][C] (pointer valid until destroy). */
+const uint16_t* or_dense_level(or_volume* v, int L);
+
+/* ---- lazy volume: level 0 from a generator callback, inserted z-range [z_lo, z_hi);
+ *      levels and nodes computed on demand and memoised ---- */
+typedef void (*or_gen_fn)(void* user, int64_t x, int64_t y, int64_t z, uint16_t* out);
+or_volume* or_lazy_create(const int64_t dim[3], int C, int M, uint16_t bg, uint16_t tau, or_gen_fn gen, void* user,
+                          int64_t z_lo, int64_t z_hi);
+
+void or_volume_destroy(or_volume* v);
+const or_geom* or_volume_geom(const or_volume* v);
+uint16_t or_value(or_volume* v, int L, int64_t x, int64_t y, int64_t z, int c);
+int or_node_info(or_volume* v, int L, int64_t i, int64_t j, int64_t k, or_node* out);
+
+/* ---- render ---- */
+typedef struct {
+    float eye[3], target[3], up[3];
+    float fov_y_deg;
+    int width, height;
+    float lod_error_px; /* epsilon of the screen-space error, pixels */
+    float step_voxels;  /* sampling step, level-0 voxel units */
+    float ert_alpha;    /* early ray termination threshold */
+    int n_clip;         /* 0..3 half-spaces n.p + d >= 0 */
+    float clip[3][4];
+} or_camera;
+
+typedef struct {
+    int n_cand;                      /* 1..OR_MAXCAND admissible RGBA results */
+    double rgba[OR_MAXCAND][4];      /* rgba[0] is the FP64-natural result */
+    int64_t samples;                 /* samples composited with the natural decisions */
+} or_pixel;
+
+/* Renders the listed pixels.  tf: [C][256][4] (table entries in [0,1]), scale: [C].
+ * mode 0 = emission-absorption (Algorithm 1), mode 1 = maximum intensity projection. */
+int or_render(or_volume* v, const or_camera* cam, const float* tf, const float* scale, int mode, int64_t n,
+              const int32_t* px, const int32_t* py, or_pixel* out, int threads);
+
+/* Gradient of sum_pixels sum_k dl[p][k] * I[p][k] with respect to tf and scale (FP64, natural
+ * decisions).  dl: [n][4].  Outputs are overwritten. */
+int or_render_grad(or_volume* v, const or_camera* cam, const float* tf, const float* scale, int64_t n,
+                   const int32_t* px, const int32_t* py, const double* dl, double* dtf, double* dscale, int threads);
+
+/* Single steps, exposed for the pins: trilinear value of level L at p (level-0 units),
+ * and the transfer-function lookup of intensity I with scale s in one channel's table [256][4]. */
+double or_sample_trilinear(or_volume* v, int L, const float p[3], int c);
+void or_tf_eval(const float* tf_channel, double s, double I, double rgba[4]);
+
+/* Derived camera quantities, exposed for the tests: ray direction of a pixel,
+ * [t0, t1) of its ray, and the level thresholds t_L (L = 1..N). */
+int or_ray(const or_geom* g, const or_camera* cam, int px, int py, float dir[3], float* t0, float* t1);
+int or_lod_thresholds(const or_geom* g, const or_camera* cam, float* tl /* [N+1], tl[0] = 0 */);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,483 @@
+/*
+ * oracle_render.c -- TEST INFRASTRUCTURE (FP64 CPU oracle; see oracle.h).
+ *
+ * Algorithm 1 (DVR ray traversal) and the surrounding text of Sec. "Basic
+ * Ray-Casting", written out sample by sample:
+ *
+ *   ray setup      pinhole camera; [t0, t1) = the ray inside the real volume
+ *                  box [0,X]x[0,Y]x[0,Z], inside every clip half-space
+ *                  n.p + d >= 0 (up to three clipping planes, Sec. "Integration
+ *                  into Voreen"), and t >= 0;
+ *   march          t_k = t0 + k*step while t_k < t1; segment length
+ *                  l_k = min(step, t1 - t_k);
+ *   LOD            the level whose voxel projects to the pixel size: the
+ *                  largest L <= N with t_k >= t_L,
+ *                  t_L = 2^L H / (2 eps tan(fov/2));
+ *   node           descend from the root to the child whose box holds the
+ *                  sample, until the desired level or a node without
+ *                  children (getNodeAtPosition);
+ *   intensity      per channel: the node's AVG if it has no brick, else
+ *                  trilinear interpolation of that level's values
+ *                  (clamp-to-edge at the real extent);
+ *   TF             x = clamp(s_c I / 65535, 0, 1), linear interpolation in the
+ *                  channel's 256-entry RGBA table;
+ *   composite      inside the channel loop (accumulation-level intermixing):
+ *                  a = 1 - (1 - alpha)^l, C += (1-A) a rgb, A += (1-A) a;
+ *   ERT            stop after a sample once A >= ert.
+ *
+ * Geometry is single precision in the operation order written here (see
+ * oracle.h); everything downstream of the sample position is double.
+ * This file must be compiled with -ffp-contract=off.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "oracle.h"
+#include "oracle_internal.h"
+
+typedef struct {
+    float ff[3], rr[3], uu[3]; /* forward, right, up (unit) */
+    float kx, ky;              /* tan(fov/2) * W/H, tan(fov/2) */
+    float tl[OR_MAXL];         /* level thresholds, tl[0] = 0 */
+} cam_derived;
+
+static void cam_setup(const or_geom* g, const or_camera* cam, cam_derived* cd) {
+    double th = tan(((double)cam->fov_y_deg * M_PI) / 360.0);
+    double f[3], r[3], u[3], up[3];
+    for (int a = 0; a < 3; ++a) {
+        f[a] = (double)cam->target[a] - (double)cam->eye[a];
+        up[a] = (double)cam->up[a];
+    }
+    double nf = sqrt((f[0] * f[0] + f[1] * f[1]) + f[2] * f[2]);
+    for (int a = 0; a < 3; ++a) f[a] = f[a] / nf;
+    r[0] = f[1] * up[2] - f[2] * up[1];
+    r[1] = f[2] * up[0] - f[0] * up[2];
+    r[2] = f[0] * up[1] - f[1] * up[0];
+    double nr = sqrt((r[0] * r[0] + r[1] * r[1]) + r[2] * r[2]);
+    for (int a = 0; a < 3; ++a) r[a] = r[a] / nr;
+    u[0] = r[1] * f[2] - r[2] * f[1];
+    u[1] = r[2] * f[0] - r[0] * f[2];
+    u[2] = r[0] * f[1] - r[1] * f[0];
+    for (int a = 0; a < 3; ++a) {
+        cd->ff[a] = (float)f[a];
+        cd->rr[a] = (float)r[a];
+        cd->uu[a] = (float)u[a];
+    }
+    cd->kx = (float)((th * (double)cam->width) / (double)cam->height);
+    cd->ky = (float)th;
+    cd->tl[0] = 0.0f;
+    for (int L = 1; L <= g->N; ++L)
+        cd->tl[L] = (float)(ldexp((double)cam->height, L) / ((2.0 * (double)cam->lod_error_px) * th));
+}
+
+/* Ray direction and [t0, t1); returns 0 for an empty interval. */
+static int ray_setup(const or_geom* g, const or_camera* cam, const cam_derived* cd, int px, int py, float dir[3],
+                     float* t0o, float* t1o) {
+    float a = (float)(2 * px + 1);
+    float cxp = a / (float)cam->width - 1.0f;
+    float b = (float)(2 * py + 1);
+    float cyp = 1.0f - b / (float)cam->height;
+    float x = cxp * cd->kx, y = cyp * cd->ky;
+    float d[3];
+    for (int i = 0; i < 3; ++i) d[i] = (cd->ff[i] + x * cd->rr[i]) + y * cd->uu[i];
+    float n2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
+    float s = sqrtf(n2);
+    for (int i = 0; i < 3; ++i) dir[i] = d[i] / s;
+    float t0 = 0.0f, t1 = INFINITY;
+    for (int i = 0; i < 3; ++i) {
+        float o = cam->eye[i], D = (float)g->dim[i];
+        if (dir[i] != 0.0f) {
+            float ta = (0.0f - o) / dir[i], tb = (D - o) / dir[i];
+            t0 = fmaxf(t0, fminf(ta, tb));
+            t1 = fminf(t1, fmaxf(ta, tb));
+        } else if (o < 0.0f || o > D) {
+            return 0;
+        }
+    }
+    for (int p = 0; p < cam->n_clip; ++p) {
+        const float* n = cam->clip[p];
+        float sv = ((n[0] * cam->eye[0] + n[1] * cam->eye[1]) + n[2] * cam->eye[2]) + n[3];
+        float q = (n[0] * dir[0] + n[1] * dir[1]) + n[2] * dir[2];
+        if (q == 0.0f) {
+            if (sv < 0.0f) return 0;
+        } else {
+            float tc = (-sv) / q;
+            if (q > 0.0f)
+                t0 = fmaxf(t0, tc);
+            else
+                t1 = fminf(t1, tc);
+        }
+    }
+    *t0o = t0;
+    *t1o = t1;
+    return t0 < t1;
+}
+
+int or_ray(const or_geom* g, const or_camera* cam, int px, int py, float dir[3], float* t0, float* t1) {
+    cam_derived cd;
+    cam_setup(g, cam, &cd);
+    return ray_setup(g, cam, &cd, px, py, dir, t0, t1);
+}
+
+int or_lod_thresholds(const or_geom* g, const or_camera* cam, float* tl) {
+    cam_derived cd;
+    cam_setup(g, cam, &cd);
+    for (int L = 0; L <= g->N; ++L) tl[L] = cd.tl[L];
+    return 0;
+}
+
+/* getNodeAtPosition (Algorithm 1, and the descent described after it): start at the
+ * root and descend to the child whose box contains p until level Lstar is reached or
+ * the current node has no children.  Child boxes follow from halving the parent box;
+ * the child index along an axis is floor(p / size) clamped to the parent's two
+ * children and to the real node grid. */
+static int descend(or_volume* v, const float p[3], int Lstar, or_node* nd) {
+    const or_geom* g = or_volume_geom(v);
+    int lev = g->N;
+    int64_t idx[3] = {0, 0, 0};
+    or_node_info(v, lev, 0, 0, 0, nd);
+    while (lev > Lstar && nd->has_children) {
+        --lev;
+        float size = (float)((int64_t)g->M << lev);
+        for (int a = 0; a < 3; ++a) {
+            int64_t q = (int64_t)floorf(p[a] / size);
+            int64_t c0 = 2 * idx[a];
+            if (q < c0) q = c0;
+            if (q > c0 + 1) q = c0 + 1;
+            if (q > g->nb[lev][a] - 1) q = g->nb[lev][a] - 1;
+            idx[a] = q;
+        }
+        or_node_info(v, lev, idx[0], idx[1], idx[2], nd);
+    }
+    return lev;
+}
+
+/* Trilinear interpolation of level L at p (level-0 units; voxel i centred at (i+0.5) 2^L). */
+static double trilinear(or_volume* v, int L, const float p[3], int c) {
+    const or_geom* g = or_volume_geom(v);
+    int64_t i0[3], i1[3];
+    double f[3];
+    for (int a = 0; a < 3; ++a) {
+        double u = ldexp((double)p[a], -L) - 0.5;
+        double fl = floor(u);
+        f[a] = u - fl;
+        int64_t i = (int64_t)fl, hi = g->ldim[L][a] - 1;
+        i0[a] = i < 0 ? 0 : (i > hi ? hi : i);
+        i1[a] = i + 1 < 0 ? 0 : (i + 1 > hi ? hi : i + 1);
+    }
+    double s = 0.0;
+    for (int dz = 0; dz < 2; ++dz)
+        for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx) {
+                double w = (dx ? f[0] : 1.0 - f[0]) * (dy ? f[1] : 1.0 - f[1]) * (dz ? f[2] : 1.0 - f[2]);
+                s += w * (double)or_value(v, L, dx ? i1[0] : i0[0], dy ? i1[1] : i0[1], dz ? i1[2] : i0[2], c);
+            }
+    return s;
+}
+
+double or_sample_trilinear(or_volume* v, int L, const float p[3], int c) { return trilinear(v, L, p, c); }
+
+/* Transfer function (Alg. 1 applyTF): x = clamp(s I / 65535, 0, 1) indexes the 256 entries
+ * at x * 255; the value is linear between the two neighbouring entries. */
+static int tf_index(double s, double I, double* lam, double* xr_out) {
+    double xr = s * I / 65535.0;
+    double x = xr < 0.0 ? 0.0 : (xr > 1.0 ? 1.0 : xr);
+    double w = x * 255.0;
+    int i = (int)floor(w);
+    if (i > 254) i = 254;
+    *lam = w - (double)i;
+    if (xr_out) *xr_out = xr;
+    return i;
+}
+
+void or_tf_eval(const float* tfc, double s, double I, double rgba[4]) {
+    double lam;
+    int i = tf_index(s, I, &lam, NULL);
+    for (int q = 0; q < 4; ++q) rgba[q] = (1.0 - lam) * (double)tfc[4 * i + q] + lam * (double)tfc[4 * i + 4 + q];
+}
+
+/* Per-(sample, channel) record for the adjoint. */
+typedef struct {
+    double I, lam, alpha, a, ell, A_before;
+    int i, inside, aclamped, c;
+} rec_t;
+
+typedef struct {
+    rec_t* r;
+    int64_t n, cap;
+} recbuf;
+
+static void rec_push(recbuf* b, const rec_t* r) {
+    if (b->n == b->cap) {
+        b->cap = b->cap ? 2 * b->cap : 4096;
+        b->r = (rec_t*)realloc(b->r, sizeof(rec_t) * (size_t)b->cap);
+    }
+    b->r[b->n++] = *r;
+}
+
+#define ALPHA_MAX (1.0 - 1e-6)
+
+/* One ray.  mode 0: emission-absorption with ERT candidates; mode 1: MIP.
+ * rec != NULL records the natural-decision forward for the adjoint. */
+static void march(or_volume* v, const or_camera* cam, const cam_derived* cd, const float* tf, const float* scale,
+                  int mode, int px, int py, or_pixel* out, recbuf* rec) {
+    const or_geom* g = or_volume_geom(v);
+    int C = g->C;
+    memset(out, 0, sizeof(*out));
+    out->n_cand = 1;
+    float dir[3], t0, t1;
+    if (!ray_setup(g, cam, cd, px, py, dir, &t0, &t1)) return;
+    const float dt = cam->step_voxels;
+    const double ert = (double)cam->ert_alpha;
+    double Cacc[3] = {0, 0, 0}, A = 0.0;
+    double mip[OR_MAXC];
+    for (int c = 0; c < C; ++c) mip[c] = -1.0;
+    int have_nat = 0, have_early = 0;
+    double st_nat[4] = {0}, st_early[4] = {0}, st_prev[4] = {0}, st_late[4] = {0};
+    int have_prev = 0, have_late = 0;
+    int64_t nsamp = 0;
+    for (int64_t k = 0;; ++k) {
+        float tk = t0 + (float)k * dt;
+        if (!(tk < t1)) break;
+        float ell = fminf(dt, t1 - tk);
+        float p[3];
+        for (int a = 0; a < 3; ++a) p[a] = cam->eye[a] + tk * dir[a];
+        int Lstar = 0;
+        for (int L = 1; L <= g->N; ++L)
+            if (tk >= cd->tl[L]) Lstar = L;
+        or_node nd;
+        int lev = descend(v, p, Lstar, &nd);
+        if (!have_nat || mode == 1) ++nsamp;
+        for (int c = 0; c < C; ++c) {
+            double I = nd.has_brick ? trilinear(v, lev, p, c) : (double)nd.avg[c];
+            if (mode == 1) {
+                if (I > mip[c]) mip[c] = I;
+                continue;
+            }
+            double lam, xr, rgba[4];
+            int i = tf_index((double)scale[c], I, &lam, &xr);
+            or_tf_eval(tf + (size_t)c * 1024, (double)scale[c], I, rgba);
+            double alpha = rgba[3];
+            int acl = 0;
+            if (alpha > ALPHA_MAX) {
+                alpha = ALPHA_MAX;
+                acl = 1;
+            }
+            if (alpha < 0.0) {
+                alpha = 0.0;
+                acl = 1;
+            }
+            double aa = 1.0 - pow(1.0 - alpha, (double)ell);
+            if (rec && !have_nat) {
+                rec_t r = {I, lam, alpha, aa, (double)ell, A, i, (xr > 0.0 && xr < 1.0), acl, c};
+                rec_push(rec, &r);
+            }
+            for (int q = 0; q < 3; ++q) Cacc[q] += (1.0 - A) * aa * rgba[q];
+            A += (1.0 - A) * aa;
+        }
+        if (mode == 1) continue;
+        double st[4] = {Cacc[0], Cacc[1], Cacc[2], A};
+        if (!have_early && A >= ert - OR_ERT_BAND) {
+            have_early = 1;
+            memcpy(st_early, st, sizeof st);
+        }
+        if (!have_nat && A >= ert) {
+            have_nat = 1;
+            memcpy(st_nat, st, sizeof st);
+            out->samples = nsamp;
+        }
+        if (A >= ert + OR_ERT_BAND) {
+            have_late = 1;
+            memcpy(st_late, st, sizeof st);
+            break;
+        }
+        if (have_early) {
+            have_prev = 1;
+            memcpy(st_prev, st, sizeof st);
+        }
+    }
+    if (mode == 1) {
+        out->samples = nsamp;
+        if (nsamp == 0) return;
+        double Cm[3] = {0, 0, 0}, Am = 0.0;
+        for (int c = 0; c < C; ++c) {
+            double rgba[4];
+            or_tf_eval(tf + (size_t)c * 1024, (double)scale[c], mip[c], rgba);
+            double alpha = rgba[3] > ALPHA_MAX ? ALPHA_MAX : rgba[3];
+            for (int q = 0; q < 3; ++q) Cm[q] += (1.0 - Am) * alpha * rgba[q];
+            Am += (1.0 - Am) * alpha;
+        }
+        out->rgba[0][0] = Cm[0];
+        out->rgba[0][1] = Cm[1];
+        out->rgba[0][2] = Cm[2];
+        out->rgba[0][3] = Am;
+        return;
+    }
+    double fin[4] = {Cacc[0], Cacc[1], Cacc[2], A};
+    if (!have_nat) {
+        out->samples = nsamp;
+        memcpy(out->rgba[0], fin, sizeof fin);
+    } else {
+        memcpy(out->rgba[0], st_nat, sizeof st_nat);
+    }
+    /* admissible alternatives: the stopping states an FP32 accumulation may reach */
+    int n = 1;
+    double* cands[3] = {have_early ? st_early : NULL, have_prev ? st_prev : NULL,
+                        have_late ? st_late : (have_early ? fin : NULL)};
+    for (int q = 0; q < 3; ++q) {
+        if (!cands[q]) continue;
+        int dup = 0;
+        for (int m = 0; m < n; ++m)
+            if (memcmp(out->rgba[m], cands[q], sizeof(double) * 4) == 0) dup = 1;
+        if (!dup && n < OR_MAXCAND) memcpy(out->rgba[n++], cands[q], sizeof(double) * 4);
+    }
+    out->n_cand = n;
+}
+
+typedef struct {
+    or_volume* v;
+    const or_camera* cam;
+    cam_derived cd;
+    const float* tf;
+    const float* scale;
+    int mode;
+    const int32_t* px;
+    const int32_t* py;
+    or_pixel* out;
+} render_job;
+
+static void render_range(void* p, int64_t b, int64_t e) {
+    render_job* j = (render_job*)p;
+    for (int64_t i = b; i < e; ++i) march(j->v, j->cam, &j->cd, j->tf, j->scale, j->mode, j->px[i], j->py[i], &j->out[i], NULL);
+}
+
+static int cam_valid(const or_camera* cam) {
+    if (!cam || cam->width <= 0 || cam->height <= 0 || !(cam->step_voxels > 0.0f) || !(cam->lod_error_px > 0.0f) ||
+        cam->n_clip < 0 || cam->n_clip > 3 || !(cam->fov_y_deg > 0.0f && cam->fov_y_deg < 180.0f))
+        return 0;
+    return 1;
+}
+
+int or_render(or_volume* v, const or_camera* cam, const float* tf, const float* scale, int mode, int64_t n,
+              const int32_t* px, const int32_t* py, or_pixel* out, int threads) {
+    if (!v || !cam_valid(cam) || !tf || !scale || !px || !py || !out || (mode != 0 && mode != 1)) return -1;
+    render_job j;
+    j.v = v;
+    j.cam = cam;
+    cam_setup(or_volume_geom(v), cam, &j.cd);
+    j.tf = tf;
+    j.scale = scale;
+    j.mode = mode;
+    j.px = px;
+    j.py = py;
+    j.out = out;
+    or_parallel_for(n, 16, threads, render_range, &j);
+    return 0;
+}
+
+/* ---- adjoint ---- */
+typedef struct {
+    render_job rj;
+    const double* dl;
+    double* dtf;    /* [threads][C*256*4] */
+    double* dscale; /* [threads][C] */
+    int64_t next, n;
+    int nthreads;
+} grad_job;
+
+typedef struct {
+    grad_job* g;
+    int tid;
+} grad_worker_arg;
+
+/* Reverse sweep over the recorded (sample, channel) updates
+ *   C' = C + (1-A) a rgb,  A' = A + (1-A) a,
+ * with a = 1 - (1 - alpha)^l and (rgb, alpha) = (1-lam) T[i] + lam T[i+1],
+ * lam = 255 x - i, x = s I / 65535 (clamped to [0,1]). */
+static void ray_grad(const or_geom* g, const float* tf, const recbuf* rb, const double* dl, double* dtf, double* dscale) {
+    double gC[3] = {dl[0], dl[1], dl[2]}, gA = dl[3];
+    (void)g;
+    for (int64_t n = rb->n - 1; n >= 0; --n) {
+        const rec_t* r = &rb->r[n];
+        const float* T0 = tf + ((size_t)r->c * 256 + (size_t)r->i) * 4;
+        const float* T1 = T0 + 4;
+        double rgba[4];
+        for (int q = 0; q < 4; ++q) rgba[q] = (1.0 - r->lam) * (double)T0[q] + r->lam * (double)T1[q];
+        double A = r->A_before, a = r->a;
+        double gCrgb = gC[0] * rgba[0] + gC[1] * rgba[1] + gC[2] * rgba[2];
+        double ga = (1.0 - A) * (gA + gCrgb);
+        double gv[4];
+        for (int q = 0; q < 3; ++q) gv[q] = gC[q] * (1.0 - A) * a;
+        double dadal = r->aclamped ? 0.0 : r->ell * pow(1.0 - r->alpha, r->ell - 1.0);
+        gv[3] = ga * dadal;
+        double* D0 = dtf + ((size_t)r->c * 256 + (size_t)r->i) * 4;
+        double glam = 0.0;
+        for (int q = 0; q < 4; ++q) {
+            D0[q] += (1.0 - r->lam) * gv[q];
+            D0[q + 4] += r->lam * gv[q];
+            glam += gv[q] * ((double)T1[q] - (double)T0[q]);
+        }
+        if (r->inside) dscale[r->c] += glam * 255.0 * r->I / 65535.0;
+        gA = gA * (1.0 - a) - a * gCrgb;
+    }
+}
+
+static void* grad_worker(void* p) {
+    grad_worker_arg* wa = (grad_worker_arg*)p;
+    grad_job* j = wa->g;
+    const or_geom* g = or_volume_geom(j->rj.v);
+    double* dtf = j->dtf + (size_t)wa->tid * (size_t)g->C * 1024;
+    double* dsc = j->dscale + (size_t)wa->tid * (size_t)g->C;
+    recbuf rb = {NULL, 0, 0};
+    for (;;) {
+        int64_t i = __atomic_fetch_add(&j->next, 1, __ATOMIC_RELAXED);
+        if (i >= j->n) break;
+        rb.n = 0;
+        or_pixel px;
+        march(j->rj.v, j->rj.cam, &j->rj.cd, j->rj.tf, j->rj.scale, 0, j->rj.px[i], j->rj.py[i], &px, &rb);
+        ray_grad(g, j->rj.tf, &rb, j->dl + 4 * i, dtf, dsc);
+    }
+    free(rb.r);
+    return NULL;
+}
+
+int or_render_grad(or_volume* v, const or_camera* cam, const float* tf, const float* scale, int64_t n,
+                   const int32_t* px, const int32_t* py, const double* dl, double* dtf, double* dscale, int threads) {
+    if (!v || !cam_valid(cam) || !tf || !scale || !px || !py || !dl || !dtf || !dscale) return -1;
+    const or_geom* g = or_volume_geom(v);
+    int C = g->C;
+    threads = or_threads(threads);
+    grad_job j;
+    memset(&j, 0, sizeof j);
+    j.rj.v = v;
+    j.rj.cam = cam;
+    cam_setup(g, cam, &j.rj.cd);
+    j.rj.tf = tf;
+    j.rj.scale = scale;
+    j.rj.px = px;
+    j.rj.py = py;
+    j.n = n;
+    j.dl = dl;
+    j.nthreads = threads;
+    j.dtf = (double*)calloc((size_t)threads * (size_t)C * 1024, sizeof(double));
+    j.dscale = (double*)calloc((size_t)threads * (size_t)C, sizeof(double));
+    pthread_t th[256];
+    grad_worker_arg wa[256];
+    for (int t = 0; t < threads; ++t) {
+        wa[t].g = &j;
+        wa[t].tid = t;
+        pthread_create(&th[t], NULL, grad_worker, &wa[t]);
+    }
+    for (int t = 0; t < threads; ++t) pthread_join(th[t], NULL);
+    memset(dtf, 0, sizeof(double) * (size_t)C * 1024);
+    memset(dscale, 0, sizeof(double) * (size_t)C);
+    for (int t = 0; t < threads; ++t) {
+        for (int q = 0; q < C * 1024; ++q) dtf[q] += j.dtf[(size_t)t * C * 1024 + q];
+        for (int c = 0; c < C; ++c) dscale[c] += j.dscale[(size_t)t * C + c];
+    }
+    free(j.dtf);
+    free(j.dscale);
+    return 0;
+}
