@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""Benchmark of the hot path on the 24 GiB workload (2048x2048x1024 x 3 channels uint16, 32^3
+bricks, tau = 3277; 1920x1080 frames along a 60-frame orbit).
+
+One step = insert a block of 8 z-slices (overwriting, rotating through four z positions; every
+level of the insertion path is rebuilt) + render one 1920x1080 orbit frame: every row of the
+hot path (construction a1-a3, rendering a4-a10).  The metric is ray samples composited per
+second over the whole step; ms/frame (render only) is reported beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank holds its own replica of the volume and renders its own frames (the
+rays shard with no data exchange): weak scaling, value summed over ranks, time = max over ranks.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ray samples/s and ms/frame at 1920x1080, 3ch; fraction of HBM roofline vs FP64 oracle"
+SLICES_PER_STEP = 8
+INSERT_FRACTIONS = (0.125, 0.375, 0.625, 0.875)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms while running."""
+
+    def __init__(self, index):
+        self.index, self.rows, self.proc = index, [], None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if len(r) > 8 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 8 and r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            for i, n in enumerate(names):
+                if len(r) > 5 + i and r[5 + i].lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def build_volume(w, r, torch):
+    """Inserts the whole volume from the device generator in blocks of 8 slices; returns seconds."""
+    spec = w.spec()
+    X, Y, Z = w.dims
+    buf = torch.empty((SLICES_PER_STEP, Y, X, 3), dtype=torch.int16, device="cuda")
+    st = torch.cuda.current_stream().cuda_stream
+    torch.cuda.synchronize()
+    t = time.time()
+    for z0 in range(0, Z, SLICES_PER_STEP):
+        z1 = min(Z, z0 + SLICES_PER_STEP)
+        spec.generate_device(buf.data_ptr(), z0, z1, st)
+        r.insert_block((0, 0, z0), buf[: z1 - z0])
+    torch.cuda.synchronize()
+    return time.time() - t, spec
+
+
+def cpu_baseline(w, spec, n_rays, seed=0, threads=0):
+    """The oracle as it stands (lazy volume from the host generator, tau = 0 -- the only setting in
+    which it needs no full-volume node scans) on n_rays random pixels of orbit frame 0."""
+    from oracle import oracle as O
+
+    X, Y, Z = w.dims
+    lazy = O.LazyVolume(w.dims, 3, w.brick, spec.voxel_fn, spec.handle, 0, Z, tau=0)
+    cam = w.cameras[0]
+    rng = np.random.default_rng(seed)
+    # pixels whose ray meets the volume (the image centre region)
+    px = rng.integers(cam["width"] // 4, 3 * cam["width"] // 4, size=n_rays).astype(np.int32)
+    py = rng.integers(cam["height"] // 4, 3 * cam["height"] // 4, size=n_rays).astype(np.int32)
+    t = time.time()
+    _, _, samples = O.render(lazy, cam, w.tf(), [1.0, 1.0, 1.0], (px, py), 0, threads)
+    dt = time.time() - t
+    cores = threads if threads > 0 else os.cpu_count()
+    return float(samples.sum()), dt, cores
+
+
+def run_reference(args):
+    """--impl reference: the FP64 oracle on the host cores, each step a bounded sample (rays) of
+    the same workload, same metric and unit."""
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    from synth import synth as S
+
+    w = S.large(tau=0, frames=(0,))
+    spec = w.spec()
+    cpu_baseline(w, spec, 4, seed=99)  # warm the memo tables (untimed)
+    tot_s, tot_t, cores = 0.0, 0.0, os.cpu_count()
+    for k in range(args.warmup):
+        cpu_baseline(w, spec, 8, seed=1000 + k)
+    for k in range(args.steps):
+        s, t, cores = cpu_baseline(w, spec, 8, seed=k)
+        tot_s += s
+        tot_t += t
+    v = tot_s / tot_t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "samples/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tot_t / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name + " orbit frame 0 at 1920x1080", "sample": "8 random rays per step"},
+            "cpu_baseline": {"value": v, "unit": "samples/s", "cores": cores, "kind": "oracle",
+                             "sample": "8 random rays of orbit frame 0 per step, lazy oracle volume, tau = 0"},
+            "e2e": {"value": v, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=120)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-rays", type=int, default=1536)
+    ap.add_argument("--workload", default="large", choices=["large", "streamed", "medium"],
+                    help="large = the 24 GiB volume (default); medium = 1024x1024x256 (profiling size)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+
+    __graft_entry__.build_all(import_package=True)
+    import paper_1407_2074_b300 as vr
+    from synth import synth as S
+
+    frames = list(range(60))
+    if args.workload == "large":
+        w = S.large(tau=3277, frames=frames)
+    elif args.workload == "streamed":
+        w = S.streamed(tau=3277)
+        w.cameras = [S.streamed(tau=3277, frame=f).cameras[0] for f in frames]
+    else:
+        w = S.large(tau=3277, frames=frames, dims=(1024, 1024, 256), nuclei=10000)
+    r = vr.Renderer(w.dims, 3, w.brick, tau=w.tau)
+    build_s, spec = build_volume(w, r, torch)
+    tf = torch.from_numpy(w.tf()).cuda()
+    sc = torch.ones(3, device="cuda")
+    r.set_transfer_functions(tf, sc)
+    X, Y, Z = w.dims
+    # insert blocks for the timed steps (device) and pinned host copies for the end-to-end pass
+    st = torch.cuda.current_stream().cuda_stream
+    blocks = []
+    for fz in INSERT_FRACTIONS:
+        z0 = int(fz * Z) // SLICES_PER_STEP * SLICES_PER_STEP
+        b = torch.empty((SLICES_PER_STEP, Y, X, 3), dtype=torch.int16, device="cuda")
+        spec.generate_device(b.data_ptr(), z0, z0 + SLICES_PER_STEP, st)
+        blocks.append((z0, b))
+    torch.cuda.synchronize()
+    nsteps = args.warmup + args.steps
+    frame_of = [(rank * nsteps + i) % 60 for i in range(nsteps)]
+    H, W = w.cameras[0]["height"], w.cameras[0]["width"]
+    images = [torch.empty((H, W, 4), dtype=torch.float32, device="cuda") for _ in range(2)]
+    # samples per frame (deterministic; measured once, untimed)
+    samples_of = {}
+    for f in sorted(set(frame_of)):
+        r.render([w.cameras[f]], [images[0]])
+        samples_of[f] = r.stats().last_render_samples
+    # per-kernel launch count per step: level updates (N + 1) + the render kernel
+    launches_per_step = r.levels + 1
+
+    def step(i, host=False):
+        z0, b = blocks[i % len(blocks)]
+        if host:
+            r.insert_block((0, 0, z0), hblocks[i % len(hblocks)])
+        else:
+            r.insert_block((0, 0, z0), b)
+        ev[i][1].record()
+        r.render([w.cameras[frame_of[i]]], [images[i % 2]])
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
+    for i in range(args.warmup):
+        ev[i][0].record()
+        step(i)
+        ev[i][2].record()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        start.record()
+        for i in range(args.warmup, nsteps):
+            ev[i][0].record()
+            step(i)
+            ev[i][2].record()
+        stop.record()
+        torch.cuda.synchronize()
+    total_ms = start.elapsed_time(stop)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    timed = range(args.warmup, nsteps)
+    render_ms = float(np.mean([ev[i][1].elapsed_time(ev[i][2]) for i in timed]))
+    insert_ms = float(np.mean([ev[i][0].elapsed_time(ev[i][1]) for i in timed]))
+    samples = float(sum(samples_of[frame_of[i]] for i in timed))
+    if dist:
+        t = torch.tensor([samples], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t)
+        samples = float(t.item())
+    value = samples / (total_ms / 1000.0)
+    ms_per_step = total_ms / args.steps
+
+    # end-to-end through the C ABI with host buffers: pinned slices in, image out every step
+    e2e = None
+    hblocks = []
+    if not args.no_e2e:
+        for z0, b in blocks:
+            h = torch.empty(b.shape, dtype=torch.int16, pin_memory=True)
+            h.copy_(b)
+            hblocks.append(h.numpy())
+        out_host = [torch.empty((H, W, 4), dtype=torch.float32, pin_memory=True) for _ in range(2)]
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for i in range(args.warmup, nsteps):
+            ev[i][0].record()
+            step(i, host=True)
+            out_host[i % 2].copy_(images[i % 2], non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        e2e_ms = e0.elapsed_time(e1)
+        if dist:
+            t = torch.tensor([e2e_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": samples / (e2e_ms / 1000.0), "unit": "samples/s",
+               "h2d_bytes_per_step": int(SLICES_PER_STEP * X * Y * 3 * 2), "d2h_bytes_per_step": int(H * W * 16),
+               "ms_per_step": e2e_ms / args.steps}
+
+    # algorithmic footprint of the render (frame 0): distinct voxels x C x 2 B + node entries x 16 B
+    # + transfer-function tables + image
+    vox, nodes = r.footprint([w.cameras[frame_of[args.warmup]]])
+    U = sum(vox) * 3 * 2 + nodes * 16 + 3 * 256 * 16 + H * W * 16
+    peak, peak_kind = peaks()
+    achieved = U / (render_ms / 1000.0) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "render_kernel<3,4,DVR>", "algorithmic_bytes_per_launch": U,
+            "peak_kind": peak_kind, "distinct_voxels_per_level": vox, "distinct_nodes": nodes}
+    tr = os.path.join(ROOT, "profiles", f"render_{args.workload}_traffic.json")
+    if os.path.exists(tr):
+        d = json.load(open(tr))
+        if d.get("source_hash") == source_hash():
+            roof["traffic"] = d.get("traffic_bytes_per_launch")
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        s, t, cores = cpu_baseline(w, spec, args.cpu_rays)
+        cpu = {"value": s / t, "unit": "samples/s", "cores": cores, "kind": "oracle",
+               "sample": f"{args.cpu_rays} random rays of orbit frame 0 (1920x1080), lazy oracle volume with "
+                         f"tau = 0, {t:.1f} s"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": w.name + ": insert 8 slices + render one 1920x1080 orbit frame per step",
+                           "dims": list(w.dims), "channels": 3, "brick": w.brick, "tau": w.tau, "step_voxels": 0.5,
+                           "lod_error_px": 1.0, "ert_alpha": 0.99, "l2": "inputs larger than L2 (brick pool "
+                           f"{r.stats().pool_bytes / 1e9:.1f} GB)", "parallelism": f"replicas x{ws}"},
+                "ms_per_frame": render_ms, "insert_ms_per_8_slices": insert_ms,
+                "samples_per_frame": samples / args.steps / ws, "build_s_full_volume": build_s,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches_per_step * args.steps, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def source_hash():
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1407_2074_b300", "csrc"))):
+        h.update(open(os.path.join(ROOT, "paper_1407_2074_b300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,179 @@
+/*
+ * vr.h -- C ABI of libvr, a B300 (sm_103a) implementation of the data-parallel hot path of
+ * Brix, Prassni, Hinrichs, "Visualization of Large Volumetric Multi-Channel Microscopy Data
+ * Streams on Standard PCs" (arXiv 1407.2074):
+ *   - incremental construction of a bricked multi-channel octree while slices stream in
+ *     (Sec. "Incremental Construction", steps 1-3; Sec. "Handling Volumes of Arbitrary
+ *     Dimensions"; Sec. "Handling Multi-Channel Data");
+ *   - front-to-back ray casting of that octree (Algorithm 1 and Sec. "Basic Ray-Casting":
+ *     screen-space-error level of detail, descent, trilinear brick sampling, per-channel
+ *     transfer functions, emission-absorption compositing, clip planes, early termination);
+ *   - the adjoint of the compositing with respect to the transfer functions and the
+ *     per-channel intensity scales (an addition of this library; the paper has none).
+ *
+ * Conventions shared by every call:
+ *   - Every call returns a vr_status.  After a device-side error (reported through the
+ *     library's error word) the context answers VR_ERR_STATE until vr_destroy.
+ *   - Stream-ordered calls take a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Borrowed input pointers must stay valid until the stream reaches the call.
+ *   - The library owns its device memory (brick pool, node tables, staging); callers own
+ *     images and gradient buffers.  A context is not thread-safe.
+ *   - Coordinates are level-0 voxel units; voxel i is centred at i + 0.5.
+ *   - There is no CPU fallback: without a CUDA device vr_create fails with VR_ERR_CUDA.
+ */
+#ifndef VR_H
+#define VR_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vr_ctx vr_ctx;
+
+typedef enum {
+    VR_OK = 0,
+    VR_ERR_INVALID_ARG = 1,
+    VR_ERR_OUT_OF_MEMORY = 2,
+    VR_ERR_CUDA = 3,
+    VR_ERR_STATE = 4,
+    VR_ERR_TIMEOUT = 5,
+    VR_ERR_DEVICE_ASSERT = 6
+} vr_status;
+
+enum { VR_FP32 = 0, VR_FP16_INTERP = 1 };
+enum { VR_MODE_DVR = 0, VR_MODE_MIP = 1 };
+#define VR_MAX_CHANNELS 4
+#define VR_MAX_LEVELS 16
+#define VR_MAX_CLIP 3
+
+/* Optional device allocator (for instance PyTorch's caching allocator).  alloc returns NULL on
+ * failure.  Both are called on the host, with the context's device current. */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* user, void* stream);
+    void (*free)(void* p, void* user, void* stream);
+    void* user;
+} vr_allocator;
+
+typedef struct {
+    uint16_t background;        /* value of never-inserted voxels (Sec. "Incremental Construction") */
+    uint16_t homog_threshold;   /* tau: a brick is homogeneous if max - min < tau in every channel
+                                   (Sec. "CPU Data Structure"); 0 disables pruning */
+    size_t pool_capacity_bytes; /* brick pool size; 0 = room for every brick of the full tree */
+    int precision;              /* VR_FP32 or VR_FP16_INTERP (samples interpolated in FP16) */
+} vr_options;
+
+/* One view.  The camera looks from eye at target; up fixes the roll.  fov_y_deg is the vertical
+ * field of view.  Pixel (0,0) is the top-left corner.  lod_error_px is the screen-space error
+ * epsilon: level L is used from the distance t_L = 2^L H / (2 eps tan(fov/2)) on (Sec. "Basic
+ * Ray-Casting", optimal LOD).  step_voxels is the sampling step (Alg. 1 samplingStep, >= 1e-3;
+ * a ray takes at most 2^24 samples).
+ * ert_alpha stops a ray once its opacity reaches it (a value > 1 disables early termination).
+ * clip[i] = (n, d) keeps the half-space n.p + d >= 0 (up to three planes, Sec. "Integration
+ * into Voreen").  n_clip = -1 selects the context's planes set by vr_set_clip_planes. */
+typedef struct {
+    float eye[3], target[3], up[3];
+    float fov_y_deg;
+    int width, height;
+    float lod_error_px, step_voxels, ert_alpha;
+    int n_clip;
+    float clip[VR_MAX_CLIP][4];
+} vr_camera;
+
+typedef struct {
+    int64_t dims[3];
+    int channels, brick_size, levels; /* levels = N + 1 */
+    int64_t nodes;                    /* entries of the dense node tables (all levels) */
+    int64_t slots_capacity, slots_used;
+    int64_t pool_bytes, node_table_bytes;
+    int64_t last_render_samples;      /* samples composited by the last vr_render (all cameras) */
+    int64_t last_render_rays;         /* rays with a non-empty interval */
+} vr_stats_t;
+
+/* Create a context for a volume of final resolution dims (X, Y, Z), channels 1..4 and brick
+ * edge brick_size (even, >= 4).  Only the final resolution and the channel count are known in
+ * advance (Sec. "Incremental Construction").  The volume is virtually extended to
+ * brick_size * 2^N per axis (Eq. 1, Sec. "Handling Volumes of Arbitrary Dimensions").  The root
+ * exists from the start and holds the background value.  opts and alloc may be NULL (defaults:
+ * background 0, tau 0, full-tree pool, FP32; cudaMalloc).  The current CUDA device is used.
+ * Errors: VR_ERR_INVALID_ARG (bad dims/channels/brick size), VR_ERR_OUT_OF_MEMORY, VR_ERR_CUDA. */
+vr_status vr_create(const int64_t dims[3], int channels, int brick_size, const vr_options* opts,
+                    const vr_allocator* alloc, vr_ctx** out);
+
+/* Release every resource of the context (synchronises the device first). */
+vr_status vr_destroy(vr_ctx* ctx);
+
+/* Insert the cuboid block [origin, origin + extent) of values block[ez][ey][ex][C] (uint16, the
+ * channels interleaved per voxel as in Sec. "Handling Multi-Channel Data").  Already inserted
+ * values are overwritten (Sec. "Incremental Construction", step 1); every level on the
+ * insertion path is updated by 2x2x2 round-half-up half-sampling (step 2) and the homogeneity
+ * flags and AVG values of the touched nodes are refreshed (step 3).  on_device != 0: block is a
+ * device pointer; otherwise a host pointer copied by the library (pinned memory makes the copy
+ * asynchronous; pageable memory is copied before the call returns).  Stream-ordered.
+ * Errors: VR_ERR_INVALID_ARG (block outside the volume, NULL block), VR_ERR_OUT_OF_MEMORY (the
+ * brick pool is exhausted; nothing is modified), VR_ERR_STATE, VR_ERR_CUDA. */
+vr_status vr_insert_block(vr_ctx* ctx, const int64_t origin[3], const int64_t extent[3], const uint16_t* block,
+                          int on_device, void* cuda_stream);
+
+/* The slice-wise form of vr_insert_block: slice z (0 <= z < Z) of values slice[Y][X][C]. */
+vr_status vr_insert_slice(vr_ctx* ctx, int64_t z, const uint16_t* slice, int on_device, void* cuda_stream);
+
+/* Per-channel transfer functions: tf[C][256][4] RGBA (alpha = opacity per level-0 voxel of
+ * path length) and intensity scales scale[C]; intensity I maps to x = clamp(s I / 65535, 0, 1)
+ * and the table is read linearly at 255 x (Alg. 1 applyTF).  Device pointers; copied on the
+ * stream.  Errors: VR_ERR_INVALID_ARG (NULL pointers). */
+vr_status vr_set_transfer_functions(vr_ctx* ctx, const float* tf, const float* scale, void* cuda_stream);
+
+/* Context-wide clip planes (up to three half-spaces n.p + d >= 0, Sec. "Integration into
+ * Voreen"), used by every camera whose n_clip is -1.  planes[n][4] is a host array, copied.
+ * Errors: VR_ERR_INVALID_ARG (n outside 0..3, NULL planes with n > 0). */
+vr_status vr_set_clip_planes(vr_ctx* ctx, int n, const float* planes);
+
+/* Render n_cams views in one launch.  images[i] is a device buffer [H_i][W_i][4] of
+ * premultiplied RGBA FP32 (caller-owned); mode VR_MODE_DVR (Algorithm 1) or VR_MODE_MIP.
+ * Stream-ordered.  Errors: VR_ERR_INVALID_ARG (bad camera, NULL image, no transfer functions
+ * set), VR_ERR_STATE, VR_ERR_CUDA. */
+vr_status vr_render(vr_ctx* ctx, const vr_camera* cams, int n_cams, float* const* images, int mode,
+                    void* cuda_stream);
+
+/* Adjoint of vr_render (DVR) for dL/dimage given per view (device [H_i][W_i][4]): writes
+ * dl_dtf[C][256][4] and dl_dscale[C] (device, overwritten).  Each ray's forward march is
+ * recomputed, never stored.  Stream-ordered.  The paper has no counterpart. */
+vr_status vr_render_backward(vr_ctx* ctx, const vr_camera* cams, int n_cams, const float* const* dl_dimages,
+                             float* dl_dtf, float* dl_dscale, void* cuda_stream);
+
+/* Measurement hook: vr_render (DVR) that also sets, for every distinct level-L voxel read by a
+ * trilinear corner, bit (z*Y_L + y)*X_L + x of voxel_marks[L] (device, N+1 bitmaps of
+ * ceil(X_L*Y_L*Z_L/32) words, caller-zeroed), and bit n of node_marks for every node entry the
+ * descent reads (global index over all levels, ceil(nodes/32) words).  The counts give the
+ * algorithmic bytes a frame must move.  The paper has no counterpart. */
+vr_status vr_render_footprint(vr_ctx* ctx, const vr_camera* cams, int n_cams, float* const* images,
+                              uint32_t* const* voxel_marks, uint32_t* node_marks, void* cuda_stream);
+
+/* Test hook: level L of the volume as out[Z_L][Y_L][X_L][C] (host buffer), gathered from the
+ * brick pool (never-touched bricks read as the background).  Synchronises the stream. */
+vr_status vr_read_level(vr_ctx* ctx, int level, uint16_t* out, void* cuda_stream);
+
+/* Test hook: values of n level-L voxels, xyz[n][3] (host) -> out[n][C] (host).  Synchronises.
+ * Errors: VR_ERR_INVALID_ARG for a coordinate outside level L. */
+vr_status vr_read_voxels(vr_ctx* ctx, int level, int64_t n, const int64_t* xyz, uint16_t* out, void* cuda_stream);
+
+/* Test hook: the render record of node (level, i, j, k): flags bit0 has_children, bit1
+ * has_brick, bit2 touched; avg[C].  Synchronises.  Errors: VR_ERR_INVALID_ARG outside the grid. */
+vr_status vr_read_node(vr_ctx* ctx, int level, int64_t i, int64_t j, int64_t k, uint32_t* flags, uint16_t* avg,
+                       void* cuda_stream);
+
+vr_status vr_stats(vr_ctx* ctx, vr_stats_t* out);
+
+/* Ray-tile shape of the render queue: each warp renders tile_w x tile_h pixels (tile_w * tile_h
+ * must be 32).  Default 8 x 4.  Chosen per workload by the autotuner of the Python package. */
+vr_status vr_set_tile_shape(vr_ctx* ctx, int tile_w, int tile_h);
+
+/* Message of the last error of this context (or of the last failed vr_create when ctx is NULL). */
+const char* vr_last_error(const vr_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

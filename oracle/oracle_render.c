@@ -240,7 +240,7 @@ static void march(or_volume* v, const or_camera* cam, const cam_derived* cd, con
     int64_t nsamp = 0;
     for (int64_t k = 0;; ++k) {
         float tk = t0 + (float)k * dt;
-        if (!(tk < t1)) break;
+        if (!(tk < t1) || k >= ((int64_t)1 << 24)) break; /* at most 2^24 samples per ray */
         float ell = fminf(dt, t1 - tk);
         float p[3];
         for (int a = 0; a < 3; ++a) p[a] = cam->eye[a] + tk * dir[a];

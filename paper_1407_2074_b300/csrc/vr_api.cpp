@@ -1,0 +1,614 @@
+// vr_api.cpp -- host side of libvr: the C ABI declared in include/vr.h.
+//
+// The host keeps only what it needs to allocate brick slots (a mirror of the slot index of every
+// node) and to derive per-camera constants; volume values, node records, homogeneity and images
+// live on the device and are produced by the kernels in vr_insert.cu and vr_render.cu.
+// Build with -ffp-contract=off: the camera constants below are double-precision expressions whose
+// rounding must not depend on FMA contraction (they decide sample levels).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "vr.h"
+#include "vr_internal.h"
+
+using namespace vrk;
+
+struct vr_ctx {
+    int dev = 0;
+    Geo g{};
+    vr_options opt{};
+    vr_allocator alloc{};
+    bool has_alloc = false;
+    int sms = 148;
+    uint16_t* pool = nullptr;
+    RNode* rn = nullptr;
+    NStat* ns = nullptr;
+    PStat* ps = nullptr;
+    int* err = nullptr;
+    float4* tf2 = nullptr;
+    float* scl = nullptr;
+    bool tf_set = false;
+    unsigned int* counter = nullptr;
+    unsigned long long* stats = nullptr;
+    std::vector<int32_t> h_slot;
+    long long slots_used = 0;
+    uint16_t* stage = nullptr;
+    size_t stage_bytes = 0;
+    SlotInit* d_list = nullptr;
+    SlotInit* h_list = nullptr;
+    int list_cap = 0;
+    cudaEvent_t list_ev = nullptr;
+    CamParam* d_cams = nullptr;
+    CamParam* h_cams = nullptr;
+    int cams_cap = 0;
+    cudaEvent_t cams_ev = nullptr;
+    int n_clip_default = 0;
+    float clip_default[VR_MAX_CLIP][4] = {};
+    int tile_w = 8, tile_h = 4;
+    bool failed = false;
+    std::string msg;
+};
+
+static std::string g_create_error;
+
+static vr_status fail(vr_ctx* c, vr_status s, const std::string& m) {
+    if (c) {
+        c->msg = m;
+        if (s == VR_ERR_CUDA || s == VR_ERR_DEVICE_ASSERT) c->failed = true;
+    } else {
+        g_create_error = m;
+    }
+    return s;
+}
+
+static vr_status cuda_fail(vr_ctx* c, cudaError_t e, const char* where) {
+    return fail(c, VR_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(ctx, expr)                                          \
+    do {                                                       \
+        cudaError_t e_ = (expr);                               \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #expr); \
+    } while (0)
+
+static void* dalloc(vr_ctx* c, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (c->has_alloc) return c->alloc.alloc(bytes, c->alloc.user, nullptr);
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+static void dfree(vr_ctx* c, void* p) {
+    if (!p) return;
+    if (c->has_alloc)
+        c->alloc.free(p, c->alloc.user, nullptr);
+    else
+        cudaFree(p);
+}
+
+static void destroy_all(vr_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->dev);
+    cudaDeviceSynchronize();
+    dfree(c, c->pool);
+    dfree(c, c->rn);
+    dfree(c, c->ns);
+    dfree(c, c->ps);
+    dfree(c, c->err);
+    dfree(c, c->tf2);
+    dfree(c, c->scl);
+    dfree(c, c->counter);
+    dfree(c, c->stats);
+    dfree(c, c->stage);
+    dfree(c, c->d_list);
+    dfree(c, c->d_cams);
+    if (c->h_list) cudaFreeHost(c->h_list);
+    if (c->h_cams) cudaFreeHost(c->h_cams);
+    if (c->list_ev) cudaEventDestroy(c->list_ev);
+    if (c->cams_ev) cudaEventDestroy(c->cams_ev);
+    delete c;
+}
+
+extern "C" {
+
+vr_status vr_create(const int64_t dims[3], int channels, int brick_size, const vr_options* opts,
+                    const vr_allocator* alloc, vr_ctx** out) {
+    if (!out) return fail(nullptr, VR_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!dims) return fail(nullptr, VR_ERR_INVALID_ARG, "dims is NULL");
+    for (int a = 0; a < 3; ++a)
+        if (dims[a] <= 0 || dims[a] >= (1 << 21)) return fail(nullptr, VR_ERR_INVALID_ARG, "dims must be in 1..2^21-1");
+    if (channels < 1 || channels > VR_MAX_CHANNELS) return fail(nullptr, VR_ERR_INVALID_ARG, "channels must be 1..4");
+    if (brick_size < 4 || brick_size > 128 || (brick_size & 1))
+        return fail(nullptr, VR_ERR_INVALID_ARG, "brick_size must be even and in 4..128");
+    if (alloc && (!alloc->alloc || !alloc->free)) return fail(nullptr, VR_ERR_INVALID_ARG, "allocator incomplete");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    int ndev = 0;
+    if (e != cudaSuccess || cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(nullptr, VR_ERR_CUDA, "no CUDA device");
+    }
+    vr_ctx* c = new vr_ctx();
+    c->dev = dev;
+    if (opts) c->opt = *opts;
+    if (c->opt.precision != VR_FP32 && c->opt.precision != VR_FP16_INTERP) {
+        delete c;
+        return fail(nullptr, VR_ERR_INVALID_ARG, "unknown precision");
+    }
+    if (alloc) {
+        c->alloc = *alloc;
+        c->has_alloc = true;
+    }
+    cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
+    Geo& g = c->g;
+    g.C = channels;
+    g.M = brick_size;
+    g.S = brick_size + 2;
+    g.VS = channels == 1 ? 1 : (channels == 2 ? 2 : 4);
+    g.pow2 = (brick_size & (brick_size - 1)) == 0;
+    g.bg = c->opt.background;
+    g.tau = c->opt.homog_threshold;
+    long long nbmax = 1;
+    for (int a = 0; a < 3; ++a) nbmax = std::max<long long>(nbmax, (dims[a] + brick_size - 1) / brick_size);
+    int N = 0;
+    while ((1LL << N) < nbmax) ++N;
+    if (N + 1 > MAXL) {
+        delete c;
+        return fail(nullptr, VR_ERR_INVALID_ARG, "too many levels");
+    }
+    g.N = N;
+    for (int a = 0; a < 3; ++a) g.ldim[0][a] = dims[a];
+    for (int L = 1; L <= N; ++L)
+        for (int a = 0; a < 3; ++a) g.ldim[L][a] = (g.ldim[L - 1][a] + 1) / 2;
+    long long nodes = 0, full_slots = 0;
+    for (int L = 0; L <= N; ++L) {
+        for (int a = 0; a < 3; ++a) g.nb[L][a] = (g.ldim[L][a] + brick_size - 1) / brick_size;
+        g.noff[L] = nodes;
+        nodes += g.nb[L][0] * g.nb[L][1] * g.nb[L][2];
+    }
+    g.noff[N + 1] = nodes;
+    full_slots = nodes;
+    g.slot_elems = (long long)g.S * g.S * g.S * g.VS;
+    const long long slot_bytes = g.slot_elems * 2;
+    long long cap = full_slots;
+    if (c->opt.pool_capacity_bytes > 0) cap = std::min<long long>(full_slots, (long long)(c->opt.pool_capacity_bytes / slot_bytes));
+    if (cap < 1) {
+        delete c;
+        return fail(nullptr, VR_ERR_INVALID_ARG, "pool capacity below one brick");
+    }
+    g.n_slots_cap = cap;
+    c->h_slot.assign((size_t)nodes, -1);
+    c->pool = (uint16_t*)dalloc(c, (size_t)(cap * slot_bytes));
+    c->rn = (RNode*)dalloc(c, sizeof(RNode) * (size_t)nodes);
+    c->ns = (NStat*)dalloc(c, sizeof(NStat) * (size_t)nodes);
+    c->ps = (PStat*)dalloc(c, sizeof(PStat) * (size_t)(cap * brick_size * channels));
+    c->err = (int*)dalloc(c, sizeof(int));
+    c->tf2 = (float4*)dalloc(c, sizeof(float4) * 512 * channels);
+    c->scl = (float*)dalloc(c, sizeof(float) * 4);
+    c->counter = (unsigned int*)dalloc(c, sizeof(unsigned int) * 4);
+    c->stats = (unsigned long long*)dalloc(c, sizeof(unsigned long long) * 4);
+    if (!c->pool || !c->rn || !c->ns || !c->ps || !c->err || !c->tf2 || !c->scl || !c->counter || !c->stats) {
+        destroy_all(c);
+        return fail(nullptr, VR_ERR_OUT_OF_MEMORY, "device allocation failed");
+    }
+    if (cudaEventCreateWithFlags(&c->list_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->cams_ev, cudaEventDisableTiming) != cudaSuccess) {
+        destroy_all(c);
+        return fail(nullptr, VR_ERR_CUDA, "event creation failed");
+    }
+    cudaMemset(c->err, 0, sizeof(int));
+    cudaMemset(c->stats, 0, sizeof(unsigned long long) * 4);
+    e = launch_init_nodes(g, c->rn, c->ns, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        std::string m = std::string("init: ") + cudaGetErrorString(e);
+        destroy_all(c);
+        return fail(nullptr, VR_ERR_CUDA, m);
+    }
+    *out = c;
+    return VR_OK;
+}
+
+vr_status vr_destroy(vr_ctx* c) {
+    if (!c) return VR_ERR_INVALID_ARG;
+    destroy_all(c);
+    return VR_OK;
+}
+
+static vr_status check_ctx(vr_ctx* c) {
+    if (!c) return VR_ERR_INVALID_ARG;
+    if (c->failed) return fail(c, VR_ERR_STATE, "context failed earlier: " + c->msg);
+    cudaSetDevice(c->dev);
+    return VR_OK;
+}
+
+static long long ceil_div(long long a, long long b) { return (a + b - 1) / b; }
+
+vr_status vr_insert_block(vr_ctx* c, const int64_t origin[3], const int64_t extent[3], const uint16_t* block,
+                          int on_device, void* stream) {
+    vr_status s = check_ctx(c);
+    if (s != VR_OK) return s;
+    if (!origin || !extent || !block) return fail(c, VR_ERR_INVALID_ARG, "NULL argument");
+    const Geo& g = c->g;
+    for (int a = 0; a < 3; ++a)
+        if (origin[a] < 0 || extent[a] <= 0 || origin[a] + extent[a] > g.ldim[0][a])
+            return fail(c, VR_ERR_INVALID_ARG, "block outside the volume");
+    cudaStream_t st = (cudaStream_t)stream;
+    // slots for every brick whose interior the block reaches, on every level (step 1: nodes and
+    // bricks on the insertion path are created); count first so that a full pool changes nothing
+    long long lo[MAXL][3], hi[MAXL][3];
+    long long need = 0;
+    for (int L = 0; L <= g.N; ++L) {
+        for (int a = 0; a < 3; ++a) {
+            lo[L][a] = origin[a] >> L;
+            hi[L][a] = (origin[a] + extent[a] - 1) >> L;
+        }
+        for (long long k = lo[L][2] / g.M; k <= hi[L][2] / g.M; ++k)
+            for (long long j = lo[L][1] / g.M; j <= hi[L][1] / g.M; ++j)
+                for (long long i = lo[L][0] / g.M; i <= hi[L][0] / g.M; ++i)
+                    if (c->h_slot[(size_t)(g.noff[L] + (k * g.nb[L][1] + j) * g.nb[L][0] + i)] < 0) ++need;
+    }
+    if (c->slots_used + need > g.n_slots_cap) return fail(c, VR_ERR_OUT_OF_MEMORY, "brick pool exhausted");
+    // stage host data
+    const uint16_t* src = block;
+    const size_t bytes = (size_t)extent[0] * extent[1] * extent[2] * g.C * sizeof(uint16_t);
+    if (!on_device) {
+        if (bytes > c->stage_bytes) {
+            CK(c, cudaStreamSynchronize(st));
+            dfree(c, c->stage);
+            c->stage = (uint16_t*)dalloc(c, bytes);
+            c->stage_bytes = c->stage ? bytes : 0;
+            if (!c->stage) return fail(c, VR_ERR_OUT_OF_MEMORY, "staging allocation failed");
+        }
+        CK(c, cudaMemcpyAsync(c->stage, block, bytes, cudaMemcpyHostToDevice, st));
+        src = c->stage;
+    }
+    if (need > 0) {
+        if (need > c->list_cap) {
+            CK(c, cudaEventSynchronize(c->list_ev));
+            CK(c, cudaStreamSynchronize(st));
+            dfree(c, c->d_list);
+            if (c->h_list) cudaFreeHost(c->h_list);
+            c->h_list = nullptr;
+            int cap = (int)std::max<long long>(need, 4096);
+            c->d_list = (SlotInit*)dalloc(c, sizeof(SlotInit) * (size_t)cap);
+            if (!c->d_list || cudaMallocHost(&c->h_list, sizeof(SlotInit) * (size_t)cap) != cudaSuccess) {
+                c->list_cap = 0;
+                return fail(c, VR_ERR_OUT_OF_MEMORY, "slot list allocation failed");
+            }
+            c->list_cap = cap;
+        }
+        CK(c, cudaEventSynchronize(c->list_ev));
+        int n = 0;
+        for (int L = 0; L <= g.N; ++L)
+            for (long long k = lo[L][2] / g.M; k <= hi[L][2] / g.M; ++k)
+                for (long long j = lo[L][1] / g.M; j <= hi[L][1] / g.M; ++j)
+                    for (long long i = lo[L][0] / g.M; i <= hi[L][0] / g.M; ++i) {
+                        long long nid = g.noff[L] + (k * g.nb[L][1] + j) * g.nb[L][0] + i;
+                        if (c->h_slot[(size_t)nid] >= 0) continue;
+                        int slot = (int)c->slots_used++;
+                        c->h_slot[(size_t)nid] = slot;
+                        c->h_list[n++] = SlotInit{nid, L, slot, (int)i, (int)j, (int)k};
+                    }
+        CK(c, cudaMemcpyAsync(c->d_list, c->h_list, sizeof(SlotInit) * (size_t)n, cudaMemcpyHostToDevice, st));
+        CK(c, cudaEventRecord(c->list_ev, st));
+        CK(c, launch_slot_init(g, c->pool, c->rn, c->ps, c->d_list, n, st));
+    }
+    const long long org[3] = {origin[0], origin[1], origin[2]}, ext[3] = {extent[0], extent[1], extent[2]};
+    for (int L = 0; L <= g.N; ++L)
+        CK(c, launch_level_update(g, L, lo[L], hi[L], src, org, ext, c->pool, c->rn, c->ns, c->ps, c->err, st));
+    return VR_OK;
+}
+
+vr_status vr_insert_slice(vr_ctx* c, int64_t z, const uint16_t* slice, int on_device, void* stream) {
+    if (!c) return VR_ERR_INVALID_ARG;
+    if (z < 0 || z >= c->g.ldim[0][2]) return fail(c, VR_ERR_INVALID_ARG, "slice z outside the volume");
+    const int64_t o[3] = {0, 0, z}, e[3] = {c->g.ldim[0][0], c->g.ldim[0][1], 1};
+    return vr_insert_block(c, o, e, slice, on_device, stream);
+}
+
+vr_status vr_set_transfer_functions(vr_ctx* c, const float* tf, const float* scale, void* stream) {
+    vr_status s = check_ctx(c);
+    if (s != VR_OK) return s;
+    if (!tf || !scale) return fail(c, VR_ERR_INVALID_ARG, "NULL transfer function or scale");
+    CK(c, launch_prepare_tf(c->g.C, tf, scale, c->tf2, c->scl, (cudaStream_t)stream));
+    c->tf_set = true;
+    return VR_OK;
+}
+
+vr_status vr_set_clip_planes(vr_ctx* c, int n, const float* planes) {
+    vr_status s = check_ctx(c);
+    if (s != VR_OK) return s;
+    if (n < 0 || n > VR_MAX_CLIP || (n > 0 && !planes)) return fail(c, VR_ERR_INVALID_ARG, "bad clip planes");
+    c->n_clip_default = n;
+    for (int i = 0; i < n; ++i)
+        for (int q = 0; q < 4; ++q) c->clip_default[i][q] = planes[4 * i + q];
+    return VR_OK;
+}
+
+// Per-camera constants.  The expressions and their evaluation order are part of the
+// contract: sample levels and sample positions depend on their rounding.
+static bool derive_camera(const vr_ctx* c, const vr_camera& cam, CamParam& cp) {
+    if (cam.width <= 0 || cam.height <= 0 || !(cam.step_voxels >= 1e-3f) || !(cam.lod_error_px > 0.0f) ||
+        !(cam.fov_y_deg > 0.0f && cam.fov_y_deg < 180.0f) || cam.n_clip < -1 || cam.n_clip > VR_MAX_CLIP)
+        return false;
+    const Geo& g = c->g;
+    const double th = std::tan(((double)cam.fov_y_deg * M_PI) / 360.0);
+    double f[3], r[3], u[3], up[3];
+    for (int a = 0; a < 3; ++a) {
+        f[a] = (double)cam.target[a] - (double)cam.eye[a];
+        up[a] = (double)cam.up[a];
+    }
+    const double nf = std::sqrt((f[0] * f[0] + f[1] * f[1]) + f[2] * f[2]);
+    if (!(nf > 0.0)) return false;
+    for (int a = 0; a < 3; ++a) f[a] = f[a] / nf;
+    r[0] = f[1] * up[2] - f[2] * up[1];
+    r[1] = f[2] * up[0] - f[0] * up[2];
+    r[2] = f[0] * up[1] - f[1] * up[0];
+    const double nr = std::sqrt((r[0] * r[0] + r[1] * r[1]) + r[2] * r[2]);
+    if (!(nr > 0.0)) return false;
+    for (int a = 0; a < 3; ++a) r[a] = r[a] / nr;
+    u[0] = r[1] * f[2] - r[2] * f[1];
+    u[1] = r[2] * f[0] - r[0] * f[2];
+    u[2] = r[0] * f[1] - r[1] * f[0];
+    for (int a = 0; a < 3; ++a) {
+        cp.eye[a] = cam.eye[a];
+        cp.ff[a] = (float)f[a];
+        cp.rr[a] = (float)r[a];
+        cp.uu[a] = (float)u[a];
+    }
+    cp.kx = (float)((th * (double)cam.width) / (double)cam.height);
+    cp.ky = (float)th;
+    cp.dt = cam.step_voxels;
+    cp.ert = cam.ert_alpha;
+    for (int L = 0; L <= MAXL; ++L) cp.tl[L] = INFINITY;
+    cp.tl[0] = 0.0f;
+    for (int L = 1; L <= g.N; ++L)
+        cp.tl[L] = (float)(std::ldexp((double)cam.height, L) / ((2.0 * (double)cam.lod_error_px) * th));
+    cp.W = cam.width;
+    cp.H = cam.height;
+    const int nc = cam.n_clip < 0 ? c->n_clip_default : cam.n_clip;
+    cp.n_clip = nc;
+    for (int i = 0; i < VR_MAX_CLIP; ++i)
+        for (int q = 0; q < 4; ++q) cp.clip[i][q] = (i < nc) ? (cam.n_clip < 0 ? c->clip_default[i][q] : cam.clip[i][q]) : 0.0f;
+    return true;
+}
+
+static vr_status prepare_cams(vr_ctx* c, const vr_camera* cams, int n, float* const* imgs, const float* const* dimgs,
+                              cudaStream_t st, long long* total_tiles) {
+    if (n > c->cams_cap) {
+        CK(c, cudaEventSynchronize(c->cams_ev));
+        CK(c, cudaStreamSynchronize(st));
+        dfree(c, c->d_cams);
+        if (c->h_cams) cudaFreeHost(c->h_cams);
+        c->h_cams = nullptr;
+        int cap = std::max(n, 64);
+        c->d_cams = (CamParam*)dalloc(c, sizeof(CamParam) * (size_t)cap);
+        if (!c->d_cams || cudaMallocHost(&c->h_cams, sizeof(CamParam) * (size_t)cap) != cudaSuccess) {
+            c->cams_cap = 0;
+            return fail(c, VR_ERR_OUT_OF_MEMORY, "camera buffer allocation failed");
+        }
+        c->cams_cap = cap;
+    }
+    CK(c, cudaEventSynchronize(c->cams_ev));
+    long long tiles = 0;
+    for (int i = 0; i < n; ++i) {
+        CamParam& cp = c->h_cams[i];
+        std::memset(&cp, 0, sizeof cp);
+        if (!derive_camera(c, cams[i], cp)) return fail(c, VR_ERR_INVALID_ARG, "invalid camera " + std::to_string(i));
+        if (imgs) {
+            if (!imgs[i]) return fail(c, VR_ERR_INVALID_ARG, "NULL image");
+            cp.img = imgs[i];
+        }
+        if (dimgs) {
+            if (!dimgs[i]) return fail(c, VR_ERR_INVALID_ARG, "NULL image gradient");
+            cp.dimg = dimgs[i];
+        }
+        cp.tiles_x = (int)ceil_div(cp.W, c->tile_w);
+        cp.tile_begin = tiles;
+        tiles += (long long)cp.tiles_x * ceil_div(cp.H, c->tile_h);
+    }
+    if (tiles >= 0xffffffffLL) return fail(c, VR_ERR_INVALID_ARG, "too many pixels in one call");
+    CK(c, cudaMemcpyAsync(c->d_cams, c->h_cams, sizeof(CamParam) * (size_t)n, cudaMemcpyHostToDevice, st));
+    CK(c, cudaEventRecord(c->cams_ev, st));
+    *total_tiles = tiles;
+    return VR_OK;
+}
+
+static RenderArgs make_args(vr_ctx* c, int n, long long tiles) {
+    RenderArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.g = c->g;
+    a.pool = c->pool;
+    a.rnodes = c->rn;
+    a.tf = c->tf2;
+    a.scl = c->scl;
+    a.cams = c->d_cams;
+    a.n_cams = n;
+    a.total_tiles = tiles;
+    a.tile_w = c->tile_w;
+    a.tile_h = c->tile_h;
+    a.counter = c->counter;
+    a.stats = c->stats;
+    a.err = c->err;
+    return a;
+}
+
+static int grid_for(vr_ctx* c, long long tiles, int threads, int per_sm) {
+    long long warps = tiles, per_block = threads / 32;
+    long long need = (warps + per_block - 1) / per_block;
+    long long maxb = (long long)c->sms * per_sm;
+    if (need > maxb) need = maxb;
+    return (int)(need < 1 ? 1 : need);
+}
+
+vr_status vr_render(vr_ctx* c, const vr_camera* cams, int n, float* const* images, int mode, void* stream) {
+    vr_status s = check_ctx(c);
+    if (s != VR_OK) return s;
+    if (!cams || n <= 0 || !images) return fail(c, VR_ERR_INVALID_ARG, "no cameras or images");
+    if (mode != VR_MODE_DVR && mode != VR_MODE_MIP) return fail(c, VR_ERR_INVALID_ARG, "unknown mode");
+    if (!c->tf_set) return fail(c, VR_ERR_INVALID_ARG, "transfer functions not set");
+    cudaStream_t st = (cudaStream_t)stream;
+    long long tiles = 0;
+    s = prepare_cams(c, cams, n, images, nullptr, st, &tiles);
+    if (s != VR_OK) return s;
+    CK(c, cudaMemsetAsync(c->counter, 0, sizeof(unsigned int), st));
+    CK(c, cudaMemsetAsync(c->stats, 0, 2 * sizeof(unsigned long long), st));
+    RenderArgs a = make_args(c, n, tiles);
+    CK(c, launch_render(a, mode, c->opt.precision == VR_FP16_INTERP, grid_for(c, tiles, 256, 8), 256, st));
+    return VR_OK;
+}
+
+vr_status vr_render_backward(vr_ctx* c, const vr_camera* cams, int n, const float* const* dl, float* dtf,
+                             float* dscale, void* stream) {
+    vr_status s = check_ctx(c);
+    if (s != VR_OK) return s;
+    if (!cams || n <= 0 || !dl || !dtf || !dscale) return fail(c, VR_ERR_INVALID_ARG, "NULL argument");
+    if (!c->tf_set) return fail(c, VR_ERR_INVALID_ARG, "transfer functions not set");
+    cudaStream_t st = (cudaStream_t)stream;
+    long long tiles = 0;
+    s = prepare_cams(c, cams, n, nullptr, dl, st, &tiles);
+    if (s != VR_OK) return s;
+    CK(c, cudaMemsetAsync(dtf, 0, sizeof(float) * 1024 * c->g.C, st));
+    CK(c, cudaMemsetAsync(dscale, 0, sizeof(float) * c->g.C, st));
+    CK(c, cudaMemsetAsync(c->counter, 0, sizeof(unsigned int), st));
+    RenderArgs a = make_args(c, n, tiles);
+    a.stats = nullptr;
+    a.dtf = dtf;
+    a.dscale = dscale;
+    CK(c, launch_render_backward(a, grid_for(c, tiles, 256, 4), 256, st));
+    return VR_OK;
+}
+
+vr_status vr_render_footprint(vr_ctx* c, const vr_camera* cams, int n, float* const* images,
+                              uint32_t* const* voxel_marks, uint32_t* node_marks, void* stream) {
+    vr_status s = check_ctx(c);
+    if (s != VR_OK) return s;
+    if (!cams || n <= 0 || !images || !voxel_marks || !node_marks) return fail(c, VR_ERR_INVALID_ARG, "NULL argument");
+    for (int L = 0; L <= c->g.N; ++L)
+        if (!voxel_marks[L]) return fail(c, VR_ERR_INVALID_ARG, "NULL voxel bitmap");
+    if (!c->tf_set) return fail(c, VR_ERR_INVALID_ARG, "transfer functions not set");
+    cudaStream_t st = (cudaStream_t)stream;
+    long long tiles = 0;
+    s = prepare_cams(c, cams, n, images, nullptr, st, &tiles);
+    if (s != VR_OK) return s;
+    CK(c, cudaMemsetAsync(c->counter, 0, sizeof(unsigned int), st));
+    CK(c, cudaMemsetAsync(c->stats, 0, 2 * sizeof(unsigned long long), st));
+    RenderArgs a = make_args(c, n, tiles);
+    for (int L = 0; L <= c->g.N; ++L) a.vmark[L] = voxel_marks[L];
+    a.nmark = node_marks;
+    CK(c, launch_render(a, 2, 0, grid_for(c, tiles, 256, 8), 256, st));
+    return VR_OK;
+}
+
+static vr_status poll_error(vr_ctx* c, cudaStream_t st) {
+    int h = 0;
+    CK(c, cudaMemcpyAsync(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(c, cudaStreamSynchronize(st));
+    if (h) return fail(c, VR_ERR_DEVICE_ASSERT, "device check failed (code " + std::to_string(h) + ")");
+    return VR_OK;
+}
+
+vr_status vr_read_level(vr_ctx* c, int level, uint16_t* out, void* stream) {
+    vr_status s = check_ctx(c);
+    if (s != VR_OK) return s;
+    if (!out || level < 0 || level > c->g.N) return fail(c, VR_ERR_INVALID_ARG, "bad level or NULL output");
+    const Geo& g = c->g;
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t bytes = (size_t)g.ldim[level][0] * g.ldim[level][1] * g.ldim[level][2] * g.C * sizeof(uint16_t);
+    uint16_t* tmp = (uint16_t*)dalloc(c, bytes);
+    if (!tmp) return fail(c, VR_ERR_OUT_OF_MEMORY, "read buffer allocation failed");
+    cudaError_t e = launch_read_level(g, level, c->pool, c->rn, tmp, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    dfree(c, tmp);
+    if (e != cudaSuccess) return cuda_fail(c, e, "read_level");
+    return poll_error(c, st);
+}
+
+vr_status vr_read_voxels(vr_ctx* c, int level, int64_t n, const int64_t* xyz, uint16_t* out, void* stream) {
+    vr_status s = check_ctx(c);
+    if (s != VR_OK) return s;
+    const Geo& g = c->g;
+    if (level < 0 || level > g.N || n < 0 || (n > 0 && (!xyz || !out))) return fail(c, VR_ERR_INVALID_ARG, "bad arguments");
+    for (int64_t i = 0; i < n; ++i)
+        for (int a = 0; a < 3; ++a)
+            if (xyz[3 * i + a] < 0 || xyz[3 * i + a] >= g.ldim[level][a])
+                return fail(c, VR_ERR_INVALID_ARG, "voxel outside the level");
+    if (n == 0) return VR_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    long long* dxyz = (long long*)dalloc(c, sizeof(long long) * 3 * (size_t)n);
+    uint16_t* dout = (uint16_t*)dalloc(c, sizeof(uint16_t) * (size_t)(n * g.C));
+    cudaError_t e = (!dxyz || !dout) ? cudaErrorMemoryAllocation : cudaSuccess;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dxyz, xyz, sizeof(long long) * 3 * (size_t)n, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_read_voxels(g, level, c->pool, c->rn, dxyz, n, dout, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, sizeof(uint16_t) * (size_t)(n * g.C), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    dfree(c, dxyz);
+    dfree(c, dout);
+    if (e != cudaSuccess) return cuda_fail(c, e, "read_voxels");
+    return poll_error(c, st);
+}
+
+vr_status vr_read_node(vr_ctx* c, int level, int64_t i, int64_t j, int64_t k, uint32_t* flags, uint16_t* avg,
+                       void* stream) {
+    vr_status s = check_ctx(c);
+    if (s != VR_OK) return s;
+    const Geo& g = c->g;
+    if (level < 0 || level > g.N || i < 0 || j < 0 || k < 0 || i >= g.nb[level][0] || j >= g.nb[level][1] ||
+        k >= g.nb[level][2] || !flags)
+        return fail(c, VR_ERR_INVALID_ARG, "node outside the grid");
+    cudaStream_t st = (cudaStream_t)stream;
+    RNode r;
+    CK(c, cudaMemcpyAsync(&r, c->rn + g.noff[level] + (k * g.nb[level][1] + j) * g.nb[level][0] + i, sizeof(RNode),
+                          cudaMemcpyDeviceToHost, st));
+    CK(c, cudaStreamSynchronize(st));
+    *flags = r.flags;
+    if (avg)
+        for (int q = 0; q < g.C; ++q) avg[q] = r.avg[q];
+    return poll_error(c, st);
+}
+
+vr_status vr_stats(vr_ctx* c, vr_stats_t* out) {
+    if (!c || !out) return VR_ERR_INVALID_ARG;
+    cudaSetDevice(c->dev);
+    const Geo& g = c->g;
+    std::memset(out, 0, sizeof *out);
+    for (int a = 0; a < 3; ++a) out->dims[a] = g.ldim[0][a];
+    out->channels = g.C;
+    out->brick_size = g.M;
+    out->levels = g.N + 1;
+    out->nodes = g.noff[g.N + 1];
+    out->slots_capacity = g.n_slots_cap;
+    out->slots_used = c->slots_used;
+    out->pool_bytes = g.n_slots_cap * g.slot_elems * 2;
+    out->node_table_bytes = out->nodes * (long long)(sizeof(RNode) + sizeof(NStat));
+    unsigned long long h[2] = {0, 0};
+    if (cudaMemcpy(h, c->stats, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return cuda_fail(c, cudaGetLastError(), "stats");
+    out->last_render_samples = (int64_t)h[0];
+    out->last_render_rays = (int64_t)h[1];
+    return VR_OK;
+}
+
+const char* vr_last_error(const vr_ctx* c) { return c ? c->msg.c_str() : g_create_error.c_str(); }
+
+// Tile shape of the ray queue (tw x th pixels per warp, tw * th = 32).  Used by the autotuner.
+vr_status vr_set_tile_shape(vr_ctx* c, int tw, int th) {
+    if (!c || tw <= 0 || th <= 0 || tw * th != 32) return VR_ERR_INVALID_ARG;
+    c->tile_w = tw;
+    c->tile_h = th;
+    return VR_OK;
+}
+
+} // extern "C"

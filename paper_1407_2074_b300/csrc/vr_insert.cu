@@ -1,0 +1,453 @@
+// vr_insert.cu -- incremental octree construction on the device (Sec. "Incremental
+// Construction", steps 1-3; Sec. "Handling Volumes of Arbitrary Dimensions"; Sec. "Handling
+// Multi-Channel Data").
+//
+// One launch per level L = 0..N, each over the bricks of level L whose slot (interior + border)
+// covers the part of level L changed by the inserted block.  A CTA owns one slot, so no two CTAs
+// write the same memory:
+//   L = 0   copy the block's voxels into the slot positions that map onto them (interior and
+//           the one-voxel borders of neighbouring bricks, clamp-replicated at the real extent);
+//   L > 0   recompute those positions as the round-half-up mean of their in-volume children
+//           (2x2x2, read from ONE child slot: with an even M and a one-voxel border the eight
+//           children of any slot position lie in the child brick that holds 2x);
+//   then    refresh the per-plane min/max/sum of the touched interior planes and finalize the
+//           node: brick min/max/AVG, subtree min/max from the children (already final: previous
+//           launch), homogeneity (max - min < tau in every channel) and the render record.
+// The launches are ordered on the caller's stream; level L reads only level L-1 and its own
+// slot, so the result is independent of scheduling.
+#include <cuda_runtime.h>
+
+#include "vr_internal.h"
+
+namespace vrk {
+
+__device__ __forceinline__ long long clampll(long long v, long long lo, long long hi) {
+    return v < lo ? lo : (v > hi ? hi : v);
+}
+
+__device__ __forceinline__ uint16_t rhu(unsigned long long S, unsigned long long k) {
+    return (uint16_t)((2ull * S + k) / (2ull * k));
+}
+
+__global__ void init_nodes_kernel(Geo g, RNode* rn, NStat* ns) {
+    long long n = g.noff[g.N + 1];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        RNode r;
+        r.slot = -1;
+        r.flags = 0;
+        for (int c = 0; c < 4; ++c) r.avg[c] = g.bg;
+        rn[i] = r;
+        NStat s;
+        for (int c = 0; c < MAXC; ++c) {
+            s.bmin[c] = s.bmax[c] = s.smin[c] = s.smax[c] = g.bg;
+            s.bsum[c] = 0;
+        }
+        s.count = 0;
+        ns[i] = s;
+    }
+}
+
+cudaError_t launch_init_nodes(const Geo& g, RNode* rn, NStat* ns, cudaStream_t st) {
+    long long n = g.noff[g.N + 1];
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    init_nodes_kernel<<<blocks, 256, 0, st>>>(g, rn, ns);
+    return cudaGetLastError();
+}
+
+// Fill a newly allocated slot with the current level values at its positions: its own interior
+// is untouched (background); borders come from touched neighbours, else background.
+__global__ void slot_init_kernel(Geo g, uint16_t* __restrict__ pool, RNode* __restrict__ rn, PStat* __restrict__ ps,
+                                 const SlotInit* __restrict__ list) {
+    const SlotInit e = list[blockIdx.x];
+    const int L = e.level, M = g.M, S = g.S, VS = g.VS, C = g.C;
+    const long long b[3] = {e.bi, e.bj, e.bk};
+    uint16_t* dst = pool + (long long)e.slot * g.slot_elems;
+    const long long n = (long long)S * S * S;
+    for (long long t = threadIdx.x; t < n; t += blockDim.x) {
+        int l[3] = {(int)(t % S), (int)((t / S) % S), (int)(t / ((long long)S * S))};
+        long long xc[3], ob[3];
+        bool own = true;
+        for (int a = 0; a < 3; ++a) {
+            xc[a] = clampll(b[a] * M - 1 + l[a], 0, g.ldim[L][a] - 1);
+            ob[a] = xc[a] / M;
+            own = own && (ob[a] == b[a]);
+        }
+        uint16_t v[4] = {g.bg, g.bg, g.bg, g.bg};
+        if (C < 4) v[3] = 0;
+        if (C == 3) v[3] = 0;
+        if (!own) {
+            long long nid = g.noff[L] + (ob[2] * g.nb[L][1] + ob[1]) * g.nb[L][0] + ob[0];
+            RNode r = rn[nid];
+            if ((r.flags & F_TOUCHED) && r.slot >= 0 && r.slot < g.n_slots_cap) {
+                const uint16_t* src = pool + (long long)r.slot * g.slot_elems +
+                                      (((xc[2] - ob[2] * M + 1) * S + (xc[1] - ob[1] * M + 1)) * S +
+                                       (xc[0] - ob[0] * M + 1)) * VS;
+                for (int c = 0; c < C; ++c) v[c] = src[c];
+            }
+        }
+        uint16_t* d = dst + t * VS;
+        for (int c = 0; c < VS; ++c) d[c] = (c < C) ? v[c] : (uint16_t)0;
+    }
+    // plane statistics of a background brick
+    long long nin[3];
+    for (int a = 0; a < 3; ++a) {
+        long long r = g.ldim[L][a] - b[a] * M;
+        nin[a] = r < M ? (r > 0 ? r : 0) : M;
+    }
+    for (int t = threadIdx.x; t < M * C; t += blockDim.x) {
+        PStat p;
+        p.mn = p.mx = g.bg;
+        p.sum = (uint32_t)((unsigned long long)g.bg * (unsigned long long)(nin[0] * nin[1]));
+        ps[((long long)e.slot * M) * C + t] = p;
+    }
+    if (threadIdx.x == 0) rn[e.node].slot = e.slot;
+}
+
+cudaError_t launch_slot_init(const Geo& g, uint16_t* pool, RNode* rn, PStat* ps, const SlotInit* list, int n,
+                             cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    slot_init_kernel<<<n, 256, 0, st>>>(g, pool, rn, ps, list);
+    return cudaGetLastError();
+}
+
+struct LevelArgs {
+    Geo g;
+    int L;
+    long long lo[3], hi[3];  // changed box of level L, inclusive
+    long long blo[3], bn[3]; // brick range of the grid
+    const uint16_t* block;   // L = 0 input
+    long long org[3], ext[3];
+    uint16_t* pool;
+    RNode* rn;
+    NStat* ns;
+    PStat* ps;
+    int* err;
+};
+
+template <int C>
+__device__ __forceinline__ void block_reduce_stats(uint32_t (&mn)[C], uint32_t (&mx)[C], unsigned long long (&sm)[C]) {
+    __shared__ uint32_t s_mn[32][C], s_mx[32][C];
+    __shared__ unsigned long long s_sm[32][C];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[c] = min(mn[c], __shfl_xor_sync(0xffffffffu, mn[c], o));
+            mx[c] = max(mx[c], __shfl_xor_sync(0xffffffffu, mx[c], o));
+            sm[c] += __shfl_xor_sync(0xffffffffu, sm[c], o);
+        }
+        if (lane == 0) {
+            s_mn[wid][c] = mn[c];
+            s_mx[wid][c] = mx[c];
+            s_sm[wid][c] = sm[c];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < nw; ++w)
+            for (int c = 0; c < C; ++c) {
+                mn[c] = min(mn[c], s_mn[w][c]);
+                mx[c] = max(mx[c], s_mx[w][c]);
+                sm[c] += s_sm[w][c];
+            }
+    }
+    __syncthreads();
+}
+
+template <int C, int VS>
+__global__ void __launch_bounds__(256) level_update_kernel(LevelArgs a) {
+    const Geo& g = a.g;
+    const int L = a.L, M = g.M, S = g.S;
+    long long bb = blockIdx.x;
+    long long b[3];
+    b[0] = a.blo[0] + bb % a.bn[0];
+    bb /= a.bn[0];
+    b[1] = a.blo[1] + bb % a.bn[1];
+    b[2] = a.blo[2] + bb / a.bn[1];
+    const long long nid = g.noff[L] + (b[2] * g.nb[L][1] + b[1]) * g.nb[L][0] + b[0];
+    const int slot = a.rn[nid].slot;
+    if (slot < 0) return; // untouched neighbour without a slot: nothing stored to update
+    if (slot >= g.n_slots_cap) {
+        if (threadIdx.x == 0) atomicOr(a.err, ERR_SLOT_RANGE);
+        return;
+    }
+    // slot positions whose clamped coordinate lies in [lo, hi]
+    int l0[3], l1[3];
+    bool interior = true;
+    for (int d = 0; d < 3; ++d) {
+        long long base = b[d] * M - 1, ext = g.ldim[L][d];
+        long long s0 = (a.lo[d] == 0) ? 0 : a.lo[d] - base;
+        long long s1 = (a.hi[d] == ext - 1) ? S - 1 : a.hi[d] - base;
+        if (s0 < 0) s0 = 0;
+        if (s1 > S - 1) s1 = S - 1;
+        l0[d] = (int)s0;
+        l1[d] = (int)s1;
+        if (s0 > s1) return;
+        interior = interior && (b[d] * M <= a.hi[d]) && (b[d] * M + M - 1 >= a.lo[d]);
+    }
+    uint16_t* dst = a.pool + (long long)slot * g.slot_elems;
+    const int nx = l1[0] - l0[0] + 1, ny = l1[1] - l0[1] + 1, nz = l1[2] - l0[2] + 1;
+    const long long n = (long long)nx * ny * nz;
+    for (long long t = threadIdx.x; t < n; t += blockDim.x) {
+        const int lx = l0[0] + (int)(t % nx), ly = l0[1] + (int)((t / nx) % ny), lz = l0[2] + (int)(t / ((long long)nx * ny));
+        const long long x = clampll(b[0] * M - 1 + lx, 0, g.ldim[L][0] - 1);
+        const long long y = clampll(b[1] * M - 1 + ly, 0, g.ldim[L][1] - 1);
+        const long long z = clampll(b[2] * M - 1 + lz, 0, g.ldim[L][2] - 1);
+        uint16_t v[VS];
+#pragma unroll
+        for (int c = 0; c < VS; ++c) v[c] = 0;
+        if (L == 0) {
+            const uint16_t* src = a.block + (((z - a.org[2]) * a.ext[1] + (y - a.org[1])) * a.ext[0] + (x - a.org[0])) * C;
+#pragma unroll
+            for (int c = 0; c < C; ++c) v[c] = src[c];
+        } else {
+            const long long cx = 2 * x, cy = 2 * y, cz = 2 * z;
+            const bool hx = cx + 1 < g.ldim[L - 1][0], hy = cy + 1 < g.ldim[L - 1][1], hz = cz + 1 < g.ldim[L - 1][2];
+            const long long cbx = cx / M, cby = cy / M, cbz = cz / M;
+            const long long cnid = g.noff[L - 1] + (cbz * g.nb[L - 1][1] + cby) * g.nb[L - 1][0] + cbx;
+            const int cs = a.rn[cnid].slot;
+            const unsigned k = (1u + hx) * (1u + hy) * (1u + hz);
+            if (cs < 0 || cs >= g.n_slots_cap) {
+#pragma unroll
+                for (int c = 0; c < C; ++c) v[c] = g.bg;
+                if (cs >= g.n_slots_cap) atomicOr(a.err, ERR_SLOT_RANGE);
+            } else {
+                const uint16_t* cp = a.pool + (long long)cs * g.slot_elems +
+                                     (((cz - cbz * M + 1) * S + (cy - cby * M + 1)) * S + (cx - cbx * M + 1)) * VS;
+                unsigned long long sum[C];
+#pragma unroll
+                for (int c = 0; c < C; ++c) sum[c] = 0;
+                for (int dz = 0; dz <= (int)hz; ++dz)
+                    for (int dy = 0; dy <= (int)hy; ++dy)
+                        for (int dx = 0; dx <= (int)hx; ++dx) {
+                            const uint16_t* q = cp + (((long long)dz * S + dy) * S + dx) * VS;
+#pragma unroll
+                            for (int c = 0; c < C; ++c) sum[c] += q[c];
+                        }
+#pragma unroll
+                for (int c = 0; c < C; ++c) v[c] = rhu(sum[c], k);
+            }
+        }
+        uint16_t* d = dst + (((long long)lz * S + ly) * S + lx) * VS;
+        if (VS == 4) {
+            uint2 w;
+            w.x = (uint32_t)v[0] | ((uint32_t)v[VS > 1 ? 1 : 0] << 16);
+            w.y = (uint32_t)v[VS > 2 ? 2 : 0] | ((uint32_t)v[VS > 3 ? 3 : 0] << 16);
+            *reinterpret_cast<uint2*>(d) = w;
+        } else if (VS == 2) {
+            *reinterpret_cast<uint32_t*>(d) = (uint32_t)v[0] | ((uint32_t)v[VS > 1 ? 1 : 0] << 16);
+        } else {
+            d[0] = v[0];
+        }
+    }
+    if (!interior) return; // only border copies changed: the node's own statistics did not
+    __syncthreads();
+    // per-plane statistics of the changed interior planes (in-volume voxels only)
+    long long nin[3];
+    for (int d = 0; d < 3; ++d) {
+        long long r = g.ldim[L][d] - b[d] * M;
+        nin[d] = r < M ? r : M;
+    }
+    const int pz0 = l0[2] > 1 ? l0[2] : 1, pz1 = l1[2] < M ? l1[2] : M;
+    for (int lz = pz0; lz <= pz1; ++lz) {
+        if (lz > nin[2]) break; // plane beyond the real extent: unused
+        uint32_t mn[C], mx[C];
+        unsigned long long sm[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            mn[c] = 0xffffu;
+            mx[c] = 0;
+            sm[c] = 0;
+        }
+        const long long np = nin[0] * nin[1];
+        for (long long t = threadIdx.x; t < np; t += blockDim.x) {
+            const int lx = 1 + (int)(t % nin[0]), ly = 1 + (int)(t / nin[0]);
+            const uint16_t* q = dst + (((long long)lz * S + ly) * S + lx) * VS;
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                uint32_t val = q[c];
+                mn[c] = min(mn[c], val);
+                mx[c] = max(mx[c], val);
+                sm[c] += val;
+            }
+        }
+        block_reduce_stats<C>(mn, mx, sm);
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                PStat p;
+                p.mn = (uint16_t)mn[c];
+                p.mx = (uint16_t)mx[c];
+                p.sum = (uint32_t)sm[c];
+                a.ps[((long long)slot * M + (lz - 1)) * C + c] = p;
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    // finalize the node (Sec. "CPU Data Structure": homogeneity, AVG; all channels must be
+    // homogeneous, Sec. "Handling Multi-Channel Data")
+    NStat s;
+    bool bh = true, sh = true;
+    s.count = nin[0] * nin[1] * nin[2];
+    for (int c = 0; c < C; ++c) {
+        uint32_t mn = 0xffffu, mx = 0;
+        unsigned long long sm = 0;
+        for (int lz = 1; lz <= nin[2]; ++lz) {
+            PStat p = a.ps[((long long)slot * M + (lz - 1)) * C + c];
+            mn = min(mn, (uint32_t)p.mn);
+            mx = max(mx, (uint32_t)p.mx);
+            sm += p.sum;
+        }
+        s.bmin[c] = (uint16_t)mn;
+        s.bmax[c] = (uint16_t)mx;
+        s.bsum[c] = sm;
+        uint32_t smn = mn, smx = mx;
+        if (L > 0) {
+            smn = 0xffffu;
+            smx = 0;
+            for (int dz = 0; dz < 2; ++dz)
+                for (int dy = 0; dy < 2; ++dy)
+                    for (int dx = 0; dx < 2; ++dx) {
+                        long long ci = 2 * b[0] + dx, cj = 2 * b[1] + dy, ck = 2 * b[2] + dz;
+                        if (ci >= g.nb[L - 1][0] || cj >= g.nb[L - 1][1] || ck >= g.nb[L - 1][2]) continue;
+                        long long cn = g.noff[L - 1] + (ck * g.nb[L - 1][1] + cj) * g.nb[L - 1][0] + ci;
+                        if (a.rn[cn].flags & F_TOUCHED) {
+                            smn = min(smn, (uint32_t)a.ns[cn].smin[c]);
+                            smx = max(smx, (uint32_t)a.ns[cn].smax[c]);
+                        } else {
+                            smn = min(smn, (uint32_t)g.bg);
+                            smx = max(smx, (uint32_t)g.bg);
+                        }
+                    }
+        }
+        s.smin[c] = (uint16_t)smn;
+        s.smax[c] = (uint16_t)smx;
+        if (!((int)mx - (int)mn < (int)g.tau)) bh = false;
+        if (!((int)smx - (int)smn < (int)g.tau)) sh = false;
+    }
+    for (int c = C; c < MAXC; ++c) {
+        s.bmin[c] = s.bmax[c] = s.smin[c] = s.smax[c] = 0;
+        s.bsum[c] = 0;
+    }
+    a.ns[nid] = s;
+    RNode r;
+    r.slot = slot;
+    r.flags = F_TOUCHED | ((L > 0 && !sh) ? F_CHILDREN : 0u) | (!bh ? F_BRICK : 0u);
+    for (int c = 0; c < 4; ++c)
+        r.avg[c] = (c < C) ? rhu(s.bsum[c], (unsigned long long)s.count) : (uint16_t)0;
+    a.rn[nid] = r;
+}
+
+cudaError_t launch_level_update(const Geo& g, int L, const long long lo[3], const long long hi[3],
+                                const uint16_t* block, const long long org[3], const long long ext[3], uint16_t* pool,
+                                RNode* rn, NStat* ns, PStat* ps, int* err, cudaStream_t st) {
+    LevelArgs a;
+    a.g = g;
+    a.L = L;
+    long long nblocks = 1;
+    for (int d = 0; d < 3; ++d) {
+        a.lo[d] = lo[d];
+        a.hi[d] = hi[d];
+        // bricks whose clamped slot range [b M - 1, b M + M] meets [lo, hi]
+        long long b0 = (lo[d] + g.M - 1) / g.M - 1; // ceil(lo / M) - 1
+        long long b1 = (hi[d] + 1) / g.M;
+        if (b0 < 0) b0 = 0;
+        if (b1 > g.nb[L][d] - 1) b1 = g.nb[L][d] - 1;
+        a.blo[d] = b0;
+        a.bn[d] = b1 - b0 + 1;
+        nblocks *= a.bn[d];
+        a.org[d] = org ? org[d] : 0;
+        a.ext[d] = ext ? ext[d] : 0;
+    }
+    a.block = block;
+    a.pool = pool;
+    a.rn = rn;
+    a.ns = ns;
+    a.ps = ps;
+    a.err = err;
+    if (nblocks <= 0) return cudaSuccess;
+    if (nblocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    switch (g.C) {
+        case 1: level_update_kernel<1, 1><<<(unsigned)nblocks, 256, 0, st>>>(a); break;
+        case 2: level_update_kernel<2, 2><<<(unsigned)nblocks, 256, 0, st>>>(a); break;
+        case 3: level_update_kernel<3, 4><<<(unsigned)nblocks, 256, 0, st>>>(a); break;
+        default: level_update_kernel<4, 4><<<(unsigned)nblocks, 256, 0, st>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+__global__ void read_level_kernel(Geo g, int L, const uint16_t* __restrict__ pool, const RNode* __restrict__ rn,
+                                  uint16_t* __restrict__ out) {
+    const long long X = g.ldim[L][0], Y = g.ldim[L][1], Z = g.ldim[L][2];
+    const long long n = X * Y * Z;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        long long x = i % X, y = (i / X) % Y, z = i / (X * Y);
+        long long bx = x / g.M, by = y / g.M, bz = z / g.M;
+        int slot = rn[g.noff[L] + (bz * g.nb[L][1] + by) * g.nb[L][0] + bx].slot;
+        for (int c = 0; c < g.C; ++c) {
+            uint16_t v = g.bg;
+            if (slot >= 0 && slot < g.n_slots_cap)
+                v = pool[(long long)slot * g.slot_elems +
+                         (((z - bz * g.M + 1) * g.S + (y - by * g.M + 1)) * g.S + (x - bx * g.M + 1)) * g.VS + c];
+            out[i * g.C + c] = v;
+        }
+    }
+}
+
+cudaError_t launch_read_level(const Geo& g, int L, const uint16_t* pool, const RNode* rn, uint16_t* out,
+                              cudaStream_t st) {
+    long long n = g.ldim[L][0] * g.ldim[L][1] * g.ldim[L][2];
+    long long blocks = (n + 255) / 256;
+    if (blocks > 148 * 32) blocks = 148 * 32;
+    if (blocks < 1) blocks = 1;
+    read_level_kernel<<<(unsigned)blocks, 256, 0, st>>>(g, L, pool, rn, out);
+    return cudaGetLastError();
+}
+
+__global__ void read_voxels_kernel(Geo g, int L, const uint16_t* __restrict__ pool, const RNode* __restrict__ rn,
+                                   const long long* __restrict__ xyz, long long n, uint16_t* __restrict__ out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+        const long long bx = x / g.M, by = y / g.M, bz = z / g.M;
+        const int slot = rn[g.noff[L] + (bz * g.nb[L][1] + by) * g.nb[L][0] + bx].slot;
+        for (int c = 0; c < g.C; ++c) {
+            uint16_t v = g.bg;
+            if (slot >= 0 && slot < g.n_slots_cap)
+                v = pool[(long long)slot * g.slot_elems +
+                         (((z - bz * g.M + 1) * g.S + (y - by * g.M + 1)) * g.S + (x - bx * g.M + 1)) * g.VS + c];
+            out[i * g.C + c] = v;
+        }
+    }
+}
+
+cudaError_t launch_read_voxels(const Geo& g, int L, const uint16_t* pool, const RNode* rn, const long long* xyz,
+                               long long n, uint16_t* out, cudaStream_t st) {
+    long long blocks = (n + 255) / 256;
+    if (blocks > 1024) blocks = 1024;
+    if (blocks < 1) return cudaSuccess;
+    read_voxels_kernel<<<(unsigned)blocks, 256, 0, st>>>(g, L, pool, rn, xyz, n, out);
+    return cudaGetLastError();
+}
+
+__global__ void prepare_tf_kernel(int C, const float* __restrict__ tf, const float* __restrict__ scale,
+                                  float4* __restrict__ tf2, float* __restrict__ scl) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < C * 256) {
+        int e = i & 255;
+        float4 v = make_float4(tf[4 * i], tf[4 * i + 1], tf[4 * i + 2], tf[4 * i + 3]);
+        float4 w = v;
+        if (e < 255) w = make_float4(tf[4 * i + 4], tf[4 * i + 5], tf[4 * i + 6], tf[4 * i + 7]);
+        tf2[2 * i] = v;
+        tf2[2 * i + 1] = make_float4(w.x - v.x, w.y - v.y, w.z - v.z, w.w - v.w);
+    }
+    if (i < C) scl[i] = scale[i] / 65535.0f;
+}
+
+cudaError_t launch_prepare_tf(int C, const float* tf, const float* scale, float4* tf2, float* scl, cudaStream_t st) {
+    prepare_tf_kernel<<<(C * 256 + 255) / 256, 256, 0, st>>>(C, tf, scale, tf2, scl);
+    return cudaGetLastError();
+}
+
+} // namespace vrk

@@ -1,0 +1,216 @@
+"""Render parity: every GPU pixel is within RGBA max-abs 2e-3 of an admissible oracle result
+(the FP64-natural one, or one of the stopping states an FP32 opacity may reach near the
+early-termination threshold)."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from synth import synth as S
+from tests.helpers import RGBA_TOL, admissible_error, oracle_dense
+
+pytestmark = pytest.mark.gpu
+
+
+def _build(vol, M, bg=0, tau=0, z_hi=None, precision="fp32"):
+    import torch
+    import paper_1407_2074_b300 as vr
+
+    Z, Y, X, C = vol.shape
+    r = vr.Renderer((X, Y, Z), C, M, background=bg, tau=tau, precision=precision)
+    dev = torch.from_numpy(vol.view(np.int16)).cuda()
+    for z in range(Z if z_hi is None else z_hi):
+        r.insert_slice(z, dev[z])
+    return r
+
+
+def _render(r, cams, tf, scale, mode=0):
+    import torch
+
+    r.set_transfer_functions(torch.from_numpy(tf), torch.tensor(scale, dtype=torch.float32))
+    imgs = r.render(cams, mode=mode)
+    torch.cuda.synchronize()
+    return [im.cpu().numpy() for im in imgs]
+
+
+def _check_full(img, ov, cam, tf, scale, mode=0, tol=RGBA_TOL):
+    nc, cand, _ = O.render(ov, cam, tf, scale, None, mode)
+    err = admissible_error(img.reshape(-1, 4), nc, cand)
+    assert err.max() <= tol, f"max err {err.max():.3e} at pixel {np.unravel_index(err.argmax(), img.shape[:2])}"
+    return err
+
+
+def _check_pixels(img, ov, cam, tf, scale, px, py, mode=0, tol=RGBA_TOL):
+    nc, cand, _ = O.render(ov, cam, tf, scale, (px, py), mode)
+    err = admissible_error(img[py, px], nc, cand)
+    assert err.max() <= tol, f"max err {err.max():.3e}"
+    return err
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    w = S.tiny()
+    vol = w.spec().volume()
+    return w, vol, oracle_dense(vol, 16)
+
+
+def test_tiny_full_image(tiny):
+    w, vol, ov = tiny
+    r = _build(vol, 16)
+    tf, sc = w.tf(), [1.0, 1.0, 1.0]
+    img = _render(r, w.cameras, tf, sc)[0]
+    err = _check_full(img, ov, w.cameras[0], tf, sc)
+    assert err.mean() < 1e-5
+    st = r.stats()
+    _, _, samples = O.render(ov, w.cameras[0], tf, sc, None, 0)
+    assert st.last_render_samples == int(samples.sum())
+
+
+def test_tiny_opaque_tf_clip_planes_and_scales(tiny):
+    w, vol, ov = tiny
+    r = _build(vol, 16)
+    tf = w.tf()
+    tf[..., 3] = np.minimum(1.0, tf[..., 3] * 12.0)  # most rays terminate early
+    sc = [1.7, 0.6, 2.5]
+    cam = dict(w.cameras[0])
+    cam["clip"] = [S.centre_plane(w.dims, (1.0, 0.5, 0.25), 3.0), (0.0, 1.0, 0.0, -10.0)]
+    img = _render(r, [cam], tf, sc)[0]
+    _check_full(img, ov, cam, tf, sc)
+
+
+def test_tiny_mip(tiny):
+    w, vol, ov = tiny
+    r = _build(vol, 16)
+    tf, sc = w.tf(), [1.0, 1.0, 1.0]
+    img = _render(r, w.cameras, tf, sc, mode=1)[0]
+    _check_full(img, ov, w.cameras[0], tf, sc, mode=1)
+
+
+def test_context_clip_planes_apply_to_cameras_without_their_own(tiny):
+    w, vol, ov = tiny
+    r = _build(vol, 16)
+    plane = (0.0, 0.0, -1.0, 40.0)
+    r.set_clip_planes([plane])
+    cam = dict(w.cameras[0])
+    cam["clip"] = None  # n_clip = -1: the context's planes
+    tf, sc = w.tf(), [1.0, 1.0, 1.0]
+    img = _render(r, [cam], tf, sc)[0]
+    ref_cam = dict(w.cameras[0])
+    ref_cam["clip"] = [plane]
+    _check_full(img, ov, ref_cam, tf, sc)
+
+
+@pytest.mark.parametrize("eye,target", [((20.0, 30.0, 25.0), (40.0, 35.0, 60.0)),   # inside the volume
+                                        ((32.0, 32.0, -96.0), (32.0, 32.0, 32.0)),   # axis-aligned centre rays
+                                        ((200.0, 200.0, 200.0), (400.0, 400.0, 400.0))])  # looking away
+def test_tiny_camera_placements(tiny, eye, target):
+    w, vol, ov = tiny
+    r = _build(vol, 16)
+    cam = S.camera(eye, target, (0.0, 1.0, 0.0), 64, 63, fov_y_deg=70.0)
+    tf, sc = w.tf(), [1.0, 1.0, 1.0]
+    img = _render(r, [cam], tf, sc)[0]
+    _check_full(img, ov, cam, tf, sc)
+
+
+@pytest.mark.parametrize("C,M,dims,tau", [(1, 6, (45, 38, 29), 300), (2, 4, (33, 40, 21), 0), (4, 8, (48, 32, 40), 900)])
+def test_channels_and_brick_sizes(C, M, dims, tau):
+    spec = S.VolumeSpec(S.KIND_SPIM, dims, C, 40, seed=6)
+    vol = spec.volume()
+    ov = oracle_dense(vol, M, bg=30, tau=tau)
+    r = _build(vol, M, bg=30, tau=tau)
+    d = max(dims)
+    cam = S.orbit_camera(dims, 1.6 * d, 37.0, 25.0, 96, 80, lod_error_px=0.35)
+    tf = S.make_tf([21 + c for c in range(C)])
+    tf[..., 3] *= 4.0
+    sc = [1.0 + 0.3 * c for c in range(C)]
+    img = _render(r, [cam], tf, sc)[0]
+    _check_full(img, ov, cam, tf, sc)
+
+
+def test_medium_spim_homogeneity_partial_insert_and_lod():
+    # A reduced streamed workload: SPIM-like volume, tau = 3277, half of the slices inserted,
+    # oblique clip plane, LOD thresholds inside the volume (levels 0..2 sampled).
+    dims = (192, 160, 96)
+    spec = S.VolumeSpec(S.KIND_SPIM, dims, 3, 160, seed=2)
+    vol = spec.volume()
+    ov = oracle_dense(vol, 16, tau=3277, z_hi=60)
+    r = _build(vol, 16, tau=3277, z_hi=60)
+    cam = S.orbit_camera(dims, 2.0 * 192, 20.0, 20.0, 480, 270, lod_error_px=2.5,
+                         clip=[S.centre_plane(dims, (1.0, 0.5, 0.25))])
+    tl = O.lod_thresholds(ov, cam)
+    assert 0 < tl[1] < 2.0 * 192 + 200
+    tf, sc = S.make_tf([11, 12, 13]), [1.0, 1.0, 1.0]
+    tf[..., 3] *= 3.0
+    img = _render(r, [cam], tf, sc)[0]
+    _check_full(img, ov, cam, tf, sc)
+
+
+def test_batched_cameras_one_launch(tiny):
+    import torch
+
+    w, vol, ov = tiny
+    r = _build(vol, 16)
+    cams = S.batch_cameras(w.dims)
+    tf, sc = w.tf(), [1.0, 1.0, 1.0]
+    imgs = _render(r, cams, tf, sc)
+    rng = np.random.default_rng(5)
+    for i in range(0, 64, 3):
+        cam = cams[i]
+        px = rng.integers(0, cam["width"], size=96).astype(np.int32)
+        py = rng.integers(0, cam["height"], size=96).astype(np.int32)
+        _check_pixels(imgs[i], ov, cam, tf, sc, px, py)
+    alone = _render(r, [cams[7]], tf, sc)[0]
+    assert np.array_equal(alone, imgs[7])  # a ray does not depend on the other views of the launch
+
+
+def test_render_is_deterministic(tiny):
+    w, vol, ov = tiny
+    r = _build(vol, 16)
+    tf, sc = w.tf(), [1.0, 1.0, 1.0]
+    a = _render(r, w.cameras, tf, sc)[0]
+    b = _render(r, w.cameras, tf, sc)[0]
+    assert np.array_equal(a, b)
+
+
+def test_tile_shapes_give_identical_images(tiny):
+    w, vol, ov = tiny
+    r = _build(vol, 16)
+    tf, sc = w.tf(), [1.0, 1.0, 1.0]
+    ref = _render(r, w.cameras, tf, sc)[0]
+    for tw, th in ((32, 1), (16, 2), (4, 8)):
+        r.set_tile_shape(tw, th)
+        assert np.array_equal(_render(r, w.cameras, tf, sc)[0], ref)
+
+
+def _full_size_render(w, frames, tau, n_px, seed):
+    import torch
+    import paper_1407_2074_b300 as vr
+
+    spec = w.spec()
+    X, Y, Z = w.dims
+    r = vr.Renderer(w.dims, 3, w.brick, tau=tau)
+    buf = torch.empty((8, Y, X, 3), dtype=torch.int16, device="cuda")
+    st = torch.cuda.current_stream().cuda_stream
+    for z0 in range(0, Z, 8):
+        spec.generate_device(buf.data_ptr(), z0, min(Z, z0 + 8), st)
+        r.insert_block((0, 0, z0), buf[: min(Z, z0 + 8) - z0])
+    del buf
+    tf, sc = w.tf(), [1.0, 1.0, 1.0]
+    imgs = _render(r, w.cameras, tf, sc)
+    lazy = O.LazyVolume(w.dims, 3, w.brick, spec.voxel_fn, spec.handle, 0, Z, tau=0)
+    rng = np.random.default_rng(seed)
+    for cam, img in zip(w.cameras, imgs):
+        hit = np.argwhere(img[..., 3] > 0.05)
+        pick = hit[rng.choice(len(hit), size=min(n_px, len(hit)), replace=False)]
+        _check_pixels(img, lazy, cam, tf, sc, pick[:, 1].astype(np.int32), pick[:, 0].astype(np.int32))
+    r.close()
+
+
+def test_streamed_full_size_sampled_pixels():
+    """1024x1024x512 at 1920x1080 with the oblique clip plane (tau = 0: the lazy oracle needs no
+    node scans), sampled pixels against the lazy oracle."""
+    _full_size_render(S.streamed(tau=0), None, 0, 48, 1)
+
+
+def test_large_full_size_sampled_pixels():
+    """The 24 GiB 2048x2048x1024 volume at 1920x1080 (orbit frame 0), sampled pixels."""
+    _full_size_render(S.large(tau=0), None, 0, 24, 2)
