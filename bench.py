@@ -161,7 +161,7 @@ def main():
     ap.add_argument("--steps", type=int, default=120)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-rays", type=int, default=1536)
+    ap.add_argument("--cpu-rays", type=int, default=6144)
     ap.add_argument("--workload", default="large", choices=["large", "streamed", "medium"],
                     help="large = the 24 GiB volume (default); medium = 1024x1024x256 (profiling size)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
