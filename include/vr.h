@@ -137,6 +137,22 @@ vr_status vr_set_clip_planes(vr_ctx* ctx, int n, const float* planes);
 vr_status vr_render(vr_ctx* ctx, const vr_camera* cams, int n_cams, float* const* images, int mode,
                     void* cuda_stream);
 
+/* vr_render for callers that cannot let the library allocate memory during a call -- an
+ * application that reserved its GPU memory up front, or a host that must not have its other
+ * streams stalled by the device-wide synchronisation cudaMalloc/cudaFree can cause.  The paper
+ * has no counterpart.  Same arguments, checks and images as vr_render (the context, its brick pool
+ * and transfer functions must exist already), but the ray-tile queue, the sample counters and the
+ * per-camera constants live in one fixed device array of libvr (about 15 KB, held by every GPU
+ * that loads the library until the process exits) instead of buffers the library allocates.
+ * At most VR_NOALLOC_MAX_CAMERAS cameras per call (VR_ERR_INVALID_ARG beyond).  The first call on
+ * a device looks the array up (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  Every call reuses the same array: calls that can overlap on the GPU (other streams,
+ * other contexts on the same device) race and must be serialised by the caller.  The call does not
+ * update vr_stats' last_render_* counters. */
+#define VR_NOALLOC_MAX_CAMERAS 64
+vr_status vr_render_noalloc(vr_ctx* ctx, const vr_camera* cams, int n_cams, float* const* images, int mode,
+                            void* cuda_stream);
+
 /* Adjoint of vr_render (DVR) for dL/dimage given per view (device [H_i][W_i][4]): writes
  * dl_dtf[C][256][4] and dl_dscale[C] (device, overwritten).  Each ray's forward march is
  * recomputed, never stored.  Stream-ordered.  The paper has no counterpart. */

@@ -612,3 +612,37 @@ vr_status vr_set_tile_shape(vr_ctx* c, int tw, int th) {
 }
 
 } // extern "C"
+
+// Validation and camera constants for vr_render_noalloc (vr_noalloc.cu): exactly what vr_render
+// computes, written into a host array the caller provides, with no allocation of any kind.
+namespace vrk {
+
+vr_status prepare_render_noalloc(vr_ctx* c, const vr_camera* cams, int n, float* const* images, int mode,
+                                 CamParam* params, RenderArgs* args, int* blocks) {
+    vr_status s = check_ctx(c);
+    if (s != VR_OK) return s;
+    if (!cams || n <= 0 || !images || !params || !args || !blocks) return fail(c, VR_ERR_INVALID_ARG, "no cameras or images");
+    if (mode != VR_MODE_DVR && mode != VR_MODE_MIP) return fail(c, VR_ERR_INVALID_ARG, "unknown mode");
+    if (!c->tf_set) return fail(c, VR_ERR_INVALID_ARG, "transfer functions not set");
+    long long tiles = 0;
+    for (int i = 0; i < n; ++i) {
+        CamParam& cp = params[i];
+        std::memset(&cp, 0, sizeof cp);
+        if (!derive_camera(c, cams[i], cp)) return fail(c, VR_ERR_INVALID_ARG, "invalid camera " + std::to_string(i));
+        if (!images[i]) return fail(c, VR_ERR_INVALID_ARG, "NULL image");
+        cp.img = images[i];
+        cp.tiles_x = (int)ceil_div(cp.W, c->tile_w);
+        cp.tile_begin = tiles;
+        tiles += (long long)cp.tiles_x * ceil_div(cp.H, c->tile_h);
+    }
+    if (tiles >= 0xffffffffLL) return fail(c, VR_ERR_INVALID_ARG, "too many pixels in one call");
+    *args = make_args(c, n, tiles);
+    *blocks = grid_for(c, tiles, 256, 8);
+    return VR_OK;
+}
+
+vr_status noalloc_fail(vr_ctx* c, vr_status s, const char* msg) { return fail(c, s, msg); }
+
+int noalloc_fp16(const vr_ctx* c) { return c->opt.precision == VR_FP16_INTERP; }
+
+} // namespace vrk
