@@ -155,6 +155,88 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def batched_leg(torch, vr, S, reps=20):
+    """The tiny volume seen by 64 mixed-resolution cameras (16 each at 256^2, 640x480, 1280x720,
+    1920x1080, one clip plane each): one persistent launch per batch, captured in a CUDA graph,
+    launch shape from the autotuner.  FP32 and FP16 interpolation."""
+    from paper_1407_2074_b300 import autotune
+
+    w = S.batched()
+    vol = w.spec().volume()
+    r = vr.Renderer(w.dims, 3, w.brick, tau=w.tau)
+    r.insert_block((0, 0, 0), torch.from_numpy(vol.view(np.int16)).cuda())
+    r.set_transfer_functions(torch.from_numpy(w.tf()).cuda(), torch.ones(3, device="cuda"))
+    rays = sum(c["width"] * c["height"] for c in w.cameras)
+    out = {"workload": w.name, "cameras": len(w.cameras), "rays_per_batch": rays}
+    for name, mode in (("fp32", 0), ("fp16", vr.vr.VR_RENDER_FP16)):
+        shape, timings = autotune.autotune(r, w.cameras, w.name, mode=mode)
+        plan = r.plan(w.cameras, mode=mode)
+        ms = autotune.time_plan(plan, reps)
+        samples, _ = plan.samples()
+        plan.close()
+        out[name] = {"ms_per_batch": ms, "rays_per_s": rays / (ms / 1e3), "samples_per_s": samples / (ms / 1e3),
+                     "launch_shape": list(shape), "gpu_launches_per_batch": 1}
+    r.close()
+    return out
+
+
+def adjoint_leg(torch, vr, S, steps=200):
+    """512^3 x 3 SPIM-like volume, 512x512 view: fit TF tables [3,256,4] + scales [3] to a target
+    rendered with other tables (seeds 201-203) and scales (0.8, 1, 1.25); mean-L2 loss, Adam lr 1e-2,
+    hand-written adjoint with per-ray recompute."""
+    w = S.differentiable()
+    spec = w.spec()
+    X, Y, Z = w.dims
+    r = vr.Renderer(w.dims, 3, w.brick, tau=w.tau)
+    buf = torch.empty((16, Y, X, 3), dtype=torch.int16, device="cuda")
+    st = torch.cuda.current_stream().cuda_stream
+    for z0 in range(0, Z, 16):
+        spec.generate_device(buf.data_ptr(), z0, z0 + 16, st)
+        r.insert_block((0, 0, z0), buf)
+    del buf
+    cams = w.cameras
+    with torch.no_grad():
+        target = vr.render(r, cams, torch.from_numpy(S.make_tf(S.TARGET_TF_SEEDS)).cuda(),
+                           torch.tensor(S.TARGET_SCALES, device="cuda"))[0].clone()
+    tf = torch.from_numpy(w.tf()).cuda().requires_grad_(True)
+    sc = torch.ones(3, device="cuda", requires_grad=True)
+    opt = torch.optim.Adam([tf, sc], lr=1e-2)
+
+    def step():
+        opt.zero_grad(set_to_none=True)
+        img = vr.render(r, cams, tf, sc)[0]
+        loss = ((img - target) ** 2).mean()
+        loss.backward()
+        opt.step()
+        with torch.no_grad():
+            tf.clamp_(0.0, 1.0)
+        return loss
+
+    first = float(step().item())
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        loss = step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    # forward / backward split of one step
+    f0, f1, f2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    f0.record()
+    img = vr.render(r, cams, tf, sc)[0]
+    f1.record()
+    ((img - target) ** 2).mean().backward()
+    f2.record()
+    torch.cuda.synchronize()
+    r.close()
+    return {"workload": w.name, "image": [cams[0]["width"], cams[0]["height"]], "adam_steps": steps,
+            "ms_per_step": ms, "forward_ms": f0.elapsed_time(f1), "backward_ms": f1.elapsed_time(f2),
+            "loss_first": first, "loss_last": float(loss.item())}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -166,6 +248,8 @@ def main():
                     help="large = the 24 GiB volume (default); medium = 1024x1024x256 (profiling size)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--fp16", type=int, default=1, help="also time the FP16-interpolation render")
+    ap.add_argument("--suite", type=int, default=1, help="also run the batched and differentiable legs")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -198,6 +282,7 @@ def main():
         w = S.large(tau=3277, frames=frames, dims=(1024, 1024, 256), nuclei=10000)
     r = vr.Renderer(w.dims, 3, w.brick, tau=w.tau)
     build_s, spec = build_volume(w, r, torch)
+    pool_gb = r.stats().pool_bytes / 1e9
     tf = torch.from_numpy(w.tf()).cuda()
     sc = torch.ones(3, device="cuda")
     r.set_transfer_functions(tf, sc)
@@ -296,6 +381,26 @@ def main():
                "h2d_bytes_per_step": int(SLICES_PER_STEP * X * Y * 3 * 2), "d2h_bytes_per_step": int(H * W * 16),
                "ms_per_step": e2e_ms / args.steps}
 
+    # FP16 sample interpolation + TF lookup (FP32 compositing) on the same frames: render only
+    fp16 = None
+    if args.fp16:
+        f16 = [torch.empty((H, W, 4), dtype=torch.float32, device="cuda") for _ in range(2)]
+        r.render([w.cameras[frame_of[0]]], [f16[0]], mode=vr.vr.VR_MODE_DVR | vr.vr.VR_RENDER_FP16)
+        torch.cuda.synchronize()
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        h0.record()
+        for i in range(args.warmup, nsteps):
+            r.render([w.cameras[frame_of[i]]], [f16[i % 2]], mode=vr.vr.VR_MODE_DVR | vr.vr.VR_RENDER_FP16)
+        h1.record()
+        torch.cuda.synchronize()
+        ms16 = h0.elapsed_time(h1) / args.steps
+        last = nsteps - 1
+        r.render([w.cameras[frame_of[last]]], [images[0]])
+        r.render([w.cameras[frame_of[last]]], [f16[0]], mode=vr.vr.VR_MODE_DVR | vr.vr.VR_RENDER_FP16)
+        d = (f16[0] - images[0]).abs()
+        fp16 = {"ms_per_frame": ms16, "samples_per_s": samples / args.steps / (ms16 / 1000.0),
+                "max_abs_diff_vs_fp32": float(d.max().item()), "mean_abs_diff_vs_fp32": float(d.mean().item())}
+
     # algorithmic footprint of the render (frame 0): distinct voxels x C x 2 B + node entries x 16 B
     # + transfer-function tables + image
     vox, nodes = r.footprint([w.cameras[frame_of[args.warmup]]])
@@ -311,6 +416,14 @@ def main():
         if d.get("source_hash") == source_hash():
             roof["traffic"] = d.get("traffic_bytes_per_launch")
 
+    batched = adjoint = None
+    if args.suite and rank == 0:
+        del blocks
+        r.close()
+        torch.cuda.empty_cache()
+        batched = batched_leg(torch, vr, S)
+        adjoint = adjoint_leg(torch, vr, S)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         s, t, cores = cpu_baseline(w, spec, args.cpu_rays)
@@ -324,10 +437,11 @@ def main():
                 "config": {"workload": w.name + ": insert 8 slices + render one 1920x1080 orbit frame per step",
                            "dims": list(w.dims), "channels": 3, "brick": w.brick, "tau": w.tau, "step_voxels": 0.5,
                            "lod_error_px": 1.0, "ert_alpha": 0.99, "l2": "inputs larger than L2 (brick pool "
-                           f"{r.stats().pool_bytes / 1e9:.1f} GB)", "parallelism": f"replicas x{ws}"},
+                           f"{pool_gb:.1f} GB)", "parallelism": f"replicas x{ws}"},
                 "ms_per_frame": render_ms, "insert_ms_per_8_slices": insert_ms,
                 "samples_per_frame": samples / args.steps / ws, "build_s_full_volume": build_s,
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp16": fp16,
+                "batched": batched, "adjoint": adjoint,
                 "gpu_launches": launches_per_step * args.steps, "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     if dist:

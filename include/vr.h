@@ -44,6 +44,9 @@ typedef enum {
 
 enum { VR_FP32 = 0, VR_FP16_INTERP = 1 };
 enum { VR_MODE_DVR = 0, VR_MODE_MIP = 1 };
+/* OR-ed into vr_render's mode: this call interpolates samples and reads the transfer functions in
+ * FP16 (normalised intensities), compositing in FP32 -- as if the context had VR_FP16_INTERP. */
+#define VR_RENDER_FP16 0x10
 #define VR_MAX_CHANNELS 4
 #define VR_MAX_LEVELS 16
 #define VR_MAX_CLIP 3
@@ -61,7 +64,8 @@ typedef struct {
     uint16_t homog_threshold;   /* tau: a brick is homogeneous if max - min < tau in every channel
                                    (Sec. "CPU Data Structure"); 0 disables pruning */
     size_t pool_capacity_bytes; /* brick pool size; 0 = room for every brick of the full tree */
-    int precision;              /* VR_FP32 or VR_FP16_INTERP (samples interpolated in FP16) */
+    int precision;              /* VR_FP32 or VR_FP16_INTERP: default precision of vr_render's DVR
+                                   (FP16 sample interpolation and TF lookup, FP32 compositing) */
 } vr_options;
 
 /* One view.  The camera looks from eye at target; up fixes the roll.  fov_y_deg is the vertical
@@ -131,7 +135,8 @@ vr_status vr_set_transfer_functions(vr_ctx* ctx, const float* tf, const float* s
 vr_status vr_set_clip_planes(vr_ctx* ctx, int n, const float* planes);
 
 /* Render n_cams views in one launch.  images[i] is a device buffer [H_i][W_i][4] of
- * premultiplied RGBA FP32 (caller-owned); mode VR_MODE_DVR (Algorithm 1) or VR_MODE_MIP.
+ * premultiplied RGBA FP32 (caller-owned); mode VR_MODE_DVR (Algorithm 1) or VR_MODE_MIP, optionally
+ * | VR_RENDER_FP16 (DVR only; MIP always interpolates in FP32).
  * Stream-ordered.  Errors: VR_ERR_INVALID_ARG (bad camera, NULL image, no transfer functions
  * set), VR_ERR_STATE, VR_ERR_CUDA. */
 vr_status vr_render(vr_ctx* ctx, const vr_camera* cams, int n_cams, float* const* images, int mode,
@@ -181,6 +186,24 @@ vr_status vr_read_node(vr_ctx* ctx, int level, int64_t i, int64_t j, int64_t k, 
                        void* cuda_stream);
 
 vr_status vr_stats(vr_ctx* ctx, vr_stats_t* out);
+
+/* Render plan: a fixed batch of views of uneven resolution rendered by ONE persistent launch,
+ * captured once into a CUDA graph (queue reset + kernel) and replayed by vr_plan_launch.  The
+ * plan owns the per-camera constants; images, the context's brick pool and its transfer
+ * functions are read at replay time, so inserts and vr_set_transfer_functions between replays
+ * take effect.  mode as in vr_render (| VR_RENDER_FP16).  The launch shape (vr_set_launch_shape)
+ * is fixed at creation.  An addition of this library; the paper has no counterpart. */
+typedef struct vr_render_plan vr_render_plan;
+vr_status vr_plan_create(vr_ctx* ctx, const vr_camera* cams, int n_cams, float* const* images, int mode,
+                         vr_render_plan** out);
+vr_status vr_plan_launch(vr_render_plan* plan, void* cuda_stream);
+/* Samples composited and rays of the last replay (synchronises). */
+vr_status vr_plan_samples(vr_render_plan* plan, int64_t* samples, int64_t* rays);
+vr_status vr_plan_destroy(vr_render_plan* plan);
+
+/* Launch shape of the ray caster: warp tile tile_w x tile_h (product 32), threads per CTA (64, 128
+ * or 256) and CTAs per SM of the persistent grid.  Defaults 8 x 4, 256, 8. */
+vr_status vr_set_launch_shape(vr_ctx* ctx, int tile_w, int tile_h, int threads_per_cta, int ctas_per_sm);
 
 /* Ray-tile shape of the render queue: each warp renders tile_w x tile_h pixels (tile_w * tile_h
  * must be 32).  Default 8 x 4.  Chosen per workload by the autotuner of the Python package. */

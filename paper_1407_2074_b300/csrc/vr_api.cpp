@@ -50,6 +50,7 @@ struct vr_ctx {
     int n_clip_default = 0;
     float clip_default[VR_MAX_CLIP][4] = {};
     int tile_w = 8, tile_h = 4;
+    int threads = 256, ctas_per_sm = 8; // render launch shape (autotuned per workload)
     bool failed = false;
     std::string msg;
 };
@@ -456,6 +457,8 @@ vr_status vr_render(vr_ctx* c, const vr_camera* cams, int n, float* const* image
     vr_status s = check_ctx(c);
     if (s != VR_OK) return s;
     if (!cams || n <= 0 || !images) return fail(c, VR_ERR_INVALID_ARG, "no cameras or images");
+    const int fp16 = (mode & VR_RENDER_FP16) || c->opt.precision == VR_FP16_INTERP;
+    mode &= ~VR_RENDER_FP16;
     if (mode != VR_MODE_DVR && mode != VR_MODE_MIP) return fail(c, VR_ERR_INVALID_ARG, "unknown mode");
     if (!c->tf_set) return fail(c, VR_ERR_INVALID_ARG, "transfer functions not set");
     cudaStream_t st = (cudaStream_t)stream;
@@ -465,7 +468,8 @@ vr_status vr_render(vr_ctx* c, const vr_camera* cams, int n, float* const* image
     CK(c, cudaMemsetAsync(c->counter, 0, sizeof(unsigned int), st));
     CK(c, cudaMemsetAsync(c->stats, 0, 2 * sizeof(unsigned long long), st));
     RenderArgs a = make_args(c, n, tiles);
-    CK(c, launch_render(a, mode, c->opt.precision == VR_FP16_INTERP, grid_for(c, tiles, 256, 8), 256, st));
+    CK(c, launch_render(a, mode, fp16 && mode == VR_MODE_DVR, grid_for(c, tiles, c->threads, c->ctas_per_sm),
+                        c->threads, st));
     return VR_OK;
 }
 
@@ -608,6 +612,117 @@ vr_status vr_set_tile_shape(vr_ctx* c, int tw, int th) {
     if (!c || tw <= 0 || th <= 0 || tw * th != 32) return VR_ERR_INVALID_ARG;
     c->tile_w = tw;
     c->tile_h = th;
+    return VR_OK;
+}
+
+vr_status vr_set_launch_shape(vr_ctx* c, int tw, int th, int threads, int ctas_per_sm) {
+    if (!c || tw <= 0 || th <= 0 || tw * th != 32 || (threads != 64 && threads != 128 && threads != 256) ||
+        ctas_per_sm < 1 || ctas_per_sm > 32)
+        return VR_ERR_INVALID_ARG;
+    c->tile_w = tw;
+    c->tile_h = th;
+    c->threads = threads;
+    c->ctas_per_sm = ctas_per_sm;
+    return VR_OK;
+}
+
+struct vr_render_plan {
+    vr_ctx* c = nullptr;
+    CamParam* d_cams = nullptr;
+    unsigned int* counter = nullptr;
+    unsigned long long* stats = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+static void plan_free(vr_render_plan* p) {
+    if (!p) return;
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    dfree(p->c, p->d_cams);
+    dfree(p->c, p->counter);
+    dfree(p->c, p->stats);
+    delete p;
+}
+
+vr_status vr_plan_create(vr_ctx* c, const vr_camera* cams, int n, float* const* images, int mode,
+                         vr_render_plan** out) {
+    vr_status s = check_ctx(c);
+    if (s != VR_OK) return s;
+    if (!out || !cams || n <= 0 || !images) return fail(c, VR_ERR_INVALID_ARG, "no cameras or images");
+    *out = nullptr;
+    const int fp16 = (mode & VR_RENDER_FP16) || c->opt.precision == VR_FP16_INTERP;
+    mode &= ~VR_RENDER_FP16;
+    if (mode != VR_MODE_DVR && mode != VR_MODE_MIP) return fail(c, VR_ERR_INVALID_ARG, "unknown mode");
+    if (!c->tf_set) return fail(c, VR_ERR_INVALID_ARG, "transfer functions not set");
+    std::vector<CamParam> h((size_t)n);
+    long long tiles = 0;
+    for (int i = 0; i < n; ++i) {
+        CamParam& cp = h[(size_t)i];
+        std::memset(&cp, 0, sizeof cp);
+        if (!derive_camera(c, cams[i], cp)) return fail(c, VR_ERR_INVALID_ARG, "invalid camera " + std::to_string(i));
+        if (!images[i]) return fail(c, VR_ERR_INVALID_ARG, "NULL image");
+        cp.img = images[i];
+        cp.tiles_x = (int)ceil_div(cp.W, c->tile_w);
+        cp.tile_begin = tiles;
+        tiles += (long long)cp.tiles_x * ceil_div(cp.H, c->tile_h);
+    }
+    if (tiles >= 0xffffffffLL) return fail(c, VR_ERR_INVALID_ARG, "too many pixels in one plan");
+    vr_render_plan* p = new vr_render_plan();
+    p->c = c;
+    p->d_cams = (CamParam*)dalloc(c, sizeof(CamParam) * (size_t)n);
+    p->counter = (unsigned int*)dalloc(c, sizeof(unsigned int) * 4);
+    p->stats = (unsigned long long*)dalloc(c, sizeof(unsigned long long) * 4);
+    if (!p->d_cams || !p->counter || !p->stats) {
+        plan_free(p);
+        return fail(c, VR_ERR_OUT_OF_MEMORY, "plan allocation failed");
+    }
+    cudaError_t e = cudaMemcpy(p->d_cams, h.data(), sizeof(CamParam) * (size_t)n, cudaMemcpyHostToDevice);
+    RenderArgs a = make_args(c, n, tiles);
+    a.cams = p->d_cams;
+    a.counter = p->counter;
+    a.stats = p->stats;
+    cudaStream_t cs = nullptr;
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+        cudaMemsetAsync(p->counter, 0, sizeof(unsigned int), cs);
+        cudaMemsetAsync(p->stats, 0, 2 * sizeof(unsigned long long), cs);
+        launch_render(a, mode, fp16 && mode == VR_MODE_DVR, grid_for(c, tiles, c->threads, c->ctas_per_sm), c->threads, cs);
+        e = cudaStreamEndCapture(cs, &p->graph);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&p->exec, p->graph, 0);
+    if (cs) cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        plan_free(p);
+        return cuda_fail(c, e, "plan capture");
+    }
+    *out = p;
+    return VR_OK;
+}
+
+vr_status vr_plan_launch(vr_render_plan* p, void* stream) {
+    if (!p) return VR_ERR_INVALID_ARG;
+    vr_status s = check_ctx(p->c);
+    if (s != VR_OK) return s;
+    CK(p->c, cudaGraphLaunch(p->exec, (cudaStream_t)stream));
+    return VR_OK;
+}
+
+vr_status vr_plan_samples(vr_render_plan* p, int64_t* samples, int64_t* rays) {
+    if (!p) return VR_ERR_INVALID_ARG;
+    unsigned long long h[2] = {0, 0};
+    CK(p->c, cudaMemcpy(h, p->stats, sizeof h, cudaMemcpyDeviceToHost));
+    if (samples) *samples = (int64_t)h[0];
+    if (rays) *rays = (int64_t)h[1];
+    return VR_OK;
+}
+
+vr_status vr_plan_destroy(vr_render_plan* p) {
+    if (!p) return VR_ERR_INVALID_ARG;
+    cudaSetDevice(p->c->dev);
+    cudaDeviceSynchronize();
+    plan_free(p);
     return VR_OK;
 }
 

@@ -19,6 +19,7 @@
 // correctly rounded single-precision operations (_rn intrinsics, never contracted) in a fixed
 // order, so these integer-valued decisions are reproducible off the GPU; interpolation, TF and
 // compositing are ordinary FP32 with FMA.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
@@ -111,7 +112,9 @@ struct TFLookup {
 };
 
 // Marches one ray; calls f.sample(I[C], ell) for every sample until it returns true.
-template <int C, int VS, bool POW2, class F>
+// H = false: I in raw uint16 units, FP32 interpolation.  H = true: the eight corners are cached as
+// normalised FP16 channel pairs (value / 65535), interpolated in half2; I is that FP16 result.
+template <int C, int VS, bool POW2, bool H, class F>
 __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restrict__ pool,
                                            const RNode* __restrict__ rn, const CamParam& cp, const float d[3], float t0,
                                            float t1, F& f) {
@@ -133,6 +136,8 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
     // cell cache
     const uint16_t* cell = nullptr;
     float cv[8][C];
+    constexpr int CP = (C + 1) / 2;
+    __half2 hv[8][CP];
     long long k = 0;
     for (;; ++k) {
         const float tk = __fadd_rn(t0, __fmul_rn((float)k, dt));
@@ -230,21 +235,102 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
                     } else {
                         cv[q][0] = (float)__ldg(reinterpret_cast<const unsigned short*>(v));
                     }
+                    if (H) {
+                        constexpr float inv = 1.0f / 65535.0f;
+#pragma unroll
+                        for (int j = 0; j < CP; ++j)
+                            hv[q][j] = __floats2half2_rn(cv[q][2 * j] * inv, (2 * j + 1 < C) ? cv[q][2 * j + 1] * inv : 0.0f);
+                    }
                 }
             }
+            if (H) {
+                const __half2 fx = __float2half2_rn(fr[0]), fy = __float2half2_rn(fr[1]), fz = __float2half2_rn(fr[2]);
 #pragma unroll
-            for (int c = 0; c < C; ++c) {
-                const float c00 = fmaf(fr[0], cv[1][c] - cv[0][c], cv[0][c]);
-                const float c10 = fmaf(fr[0], cv[3][c] - cv[2][c], cv[2][c]);
-                const float c01 = fmaf(fr[0], cv[5][c] - cv[4][c], cv[4][c]);
-                const float c11 = fmaf(fr[0], cv[7][c] - cv[6][c], cv[6][c]);
-                const float c0 = fmaf(fr[1], c10 - c00, c00);
-                const float c1 = fmaf(fr[1], c11 - c01, c01);
-                I[c] = fmaf(fr[2], c1 - c0, c0);
+                for (int j = 0; j < CP; ++j) {
+                    const __half2 c00 = __hfma2(fx, __hsub2(hv[1][j], hv[0][j]), hv[0][j]);
+                    const __half2 c10 = __hfma2(fx, __hsub2(hv[3][j], hv[2][j]), hv[2][j]);
+                    const __half2 c01 = __hfma2(fx, __hsub2(hv[5][j], hv[4][j]), hv[4][j]);
+                    const __half2 c11 = __hfma2(fx, __hsub2(hv[7][j], hv[6][j]), hv[6][j]);
+                    const __half2 c0 = __hfma2(fy, __hsub2(c10, c00), c00);
+                    const __half2 c1 = __hfma2(fy, __hsub2(c11, c01), c01);
+                    const float2 r = __half22float2(__hfma2(fz, __hsub2(c1, c0), c0));
+                    I[2 * j] = r.x;
+                    if (2 * j + 1 < C) I[2 * j + 1] = r.y;
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    const float c00 = fmaf(fr[0], cv[1][c] - cv[0][c], cv[0][c]);
+                    const float c10 = fmaf(fr[0], cv[3][c] - cv[2][c], cv[2][c]);
+                    const float c01 = fmaf(fr[0], cv[5][c] - cv[4][c], cv[4][c]);
+                    const float c11 = fmaf(fr[0], cv[7][c] - cv[6][c], cv[6][c]);
+                    const float c0 = fmaf(fr[1], c10 - c00, c00);
+                    const float c1 = fmaf(fr[1], c11 - c01, c01);
+                    I[c] = fmaf(fr[2], c1 - c0, c0);
+                }
             }
         } else {
 #pragma unroll
-            for (int c = 0; c < C; ++c) I[c] = avg[c];
+            for (int c = 0; c < C; ++c) I[c] = H ? __half2float(__float2half_rn(avg[c] * (1.0f / 65535.0f))) : avg[c];
+            if constexpr (F::kRuns) if (ell == dt) {
+                // A brick-less node gives every sample the same intensity: find the run of samples
+                // k..k+n-1 that stay in this node with a full segment, using the same per-sample
+                // single-precision tests as above (monotone in k), and composite it in one step.
+                auto in_run = [&](long long kk) -> bool {
+                    if (kk >= MAX_SAMPLES) return false;
+                    const float t = __fadd_rn(t0, __fmul_rn((float)kk, dt));
+                    if (!(t < t1) || !(t < tl_limit) || !(__fsub_rn(t1, t) >= dt)) return false;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        const float pa = __fadd_rn(cp.eye[a], __fmul_rn(t, d[a]));
+                        if (POW2) {
+                            if (!(pa >= lo[a] && pa < hi[a])) return false;
+                        } else {
+                            long long q = (long long)floorf(__fdiv_rn(pa, (float)(M << nlev)));
+                            q = q < 0 ? 0 : (q > g.nb[nlev][a] - 1 ? g.nb[nlev][a] - 1 : q);
+                            if (q != cidx[a]) return false;
+                        }
+                    }
+                    return true;
+                };
+                float te = fminf(tl_limit, t1 - dt);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    if (d[a] > 0.0f) te = fminf(te, (hi[a] - cp.eye[a]) / d[a]);
+                    else if (d[a] < 0.0f) te = fminf(te, (lo[a] - cp.eye[a]) / d[a]);
+                }
+                const float steps = floorf((te - tk) / dt);
+                long long ke = k + (steps > 0.0f ? (long long)fminf(steps, 16777216.0f) : 0);
+                long long aa = k, bb;
+                if (ke > k && in_run(ke)) {
+                    aa = ke;
+                    long long st = 1;
+                    bb = ke + 1;
+                    while (in_run(bb)) {
+                        aa = bb;
+                        st *= 2;
+                        bb = aa + st;
+                    }
+                } else {
+                    bb = ke > k ? ke : k + 1;
+                }
+                while (bb - aa > 1) {
+                    const long long m = aa + (bb - aa) / 2;
+                    if (in_run(m)) aa = m;
+                    else bb = m;
+                }
+                const long long n = aa - k + 1;
+                if (n >= 2) {
+                    bool stop = false;
+                    const long long used = f.run(I, n, dt, stop);
+                    k += used - 1;
+                    if (stop) {
+                        ++k;
+                        break;
+                    }
+                    continue;
+                }
+            }
         }
         if (f.sample(I, ell)) {
             ++k;
@@ -255,16 +341,61 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
 }
 
 struct NoHooks {
+    static constexpr bool kRuns = false; // composites runs of equal samples in closed form
     __device__ __forceinline__ void on_node(long long) {}
     __device__ __forceinline__ void on_cell(const Geo&, int, const long long*, const int*) {}
 };
 
-template <int C>
+// n samples of one constant intensity, each a per-sample transfer T' = T q, C' = C + T K:
+// after j samples T_j = T q^j and C_j = C + T K (1 - q^j) / (1 - q).  Early termination at the
+// first j with 1 - T q^j >= ert.  ln q and 1 - q^j come from log1p/expm1 (no cancellation).
+__device__ __forceinline__ long long composite_run(float lnq, const float K[3], long long n, float ert, float& A,
+                                                   float& Cr, float& Cg, float& Cb, bool& stop) {
+    const float T = 1.0f - A;
+    long long j = n;
+    stop = false;
+    if (lnq < 0.0f && ert <= 1.0f) {
+        const float target = (1.0f - ert) / T;
+        float jj = (target >= 1.0f) ? 1.0f : ceilf(logf(target) / lnq);
+        if (jj < 1.0f) jj = 1.0f;
+        if (jj <= (float)n) {
+            j = (long long)jj;
+            stop = true;
+        }
+    }
+    const float S = (lnq < 0.0f) ? expm1f((float)j * lnq) / expm1f(lnq) : (float)j;
+    Cr = fmaf(T * K[0], S, Cr);
+    Cg = fmaf(T * K[1], S, Cg);
+    Cb = fmaf(T * K[2], S, Cb);
+    A = 1.0f - T * expf((float)j * lnq);
+    return j;
+}
+
+template <int C, bool RUNS = true>
 struct DVRComposite : NoHooks {
+    static constexpr bool kRuns = RUNS;
     const float4* s_tf;
     const float* s_scl;
     float ert;
     float A = 0.0f, Cr = 0.0f, Cg = 0.0f, Cb = 0.0f;
+    __device__ __forceinline__ long long run(const float (&I)[C], long long n, float ell, bool& stop) {
+        float lnq = 0.0f, qpre = 1.0f, K[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            TFLookup<C> t;
+            t.eval(s_tf, s_scl, c, I[c]);
+            const float al = fminf(fmaxf(t.al, 0.0f), ALPHA_MAX);
+            float a, oma;
+            opacity(al, ell, a, oma);
+            const float w = qpre * a;
+            K[0] = fmaf(w, t.r, K[0]);
+            K[1] = fmaf(w, t.g, K[1]);
+            K[2] = fmaf(w, t.b, K[2]);
+            qpre *= oma;
+            lnq += ell * log1pf(-al);
+        }
+        return composite_run(lnq, K, n, ert, A, Cr, Cg, Cb, stop);
+    }
     __device__ __forceinline__ bool sample(const float (&I)[C], float ell) {
 #pragma unroll
         for (int c = 0; c < C; ++c) {
@@ -278,6 +409,65 @@ struct DVRComposite : NoHooks {
             Cg = fmaf(w, t.g, Cg);
             Cb = fmaf(w, t.b, Cb);
             A += w;
+        }
+        return A >= ert;
+    }
+};
+
+// FP16 variant of the DVR functor: I is the FP16-interpolated normalised intensity; the
+// transfer-function lookup reads a half table (entry, next - entry) and interpolates in half2;
+// opacity correction and compositing stay FP32.
+struct __align__(16) HalfEntry {
+    __half2 rg, ba, drg, dba;
+};
+
+template <int C>
+struct DVRCompositeH : NoHooks {
+    static constexpr bool kRuns = true;
+    const HalfEntry* s_tfh;
+    const __half* s_sh; // per-channel scale s (normalised intensities)
+    float ert;
+    float A = 0.0f, Cr = 0.0f, Cg = 0.0f, Cb = 0.0f;
+    __device__ __forceinline__ void lookup(int c, float I, float2& rg, float2& ba) const {
+        const __half x = __hmul_sat(__float2half_rn(I), s_sh[c]);
+        const float w = __half2float(x) * 255.0f;
+        const int i = min((int)w, 254);
+        const __half2 lam = __float2half2_rn(w - (float)i);
+        const HalfEntry e = s_tfh[c * 256 + i];
+        rg = __half22float2(__hfma2(lam, e.drg, e.rg));
+        ba = __half22float2(__hfma2(lam, e.dba, e.ba));
+    }
+    __device__ __forceinline__ long long run(const float (&I)[C], long long n, float ell, bool& stop) {
+        float lnq = 0.0f, qpre = 1.0f, K[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            float2 rg, ba;
+            lookup(c, I[c], rg, ba);
+            const float al = fminf(fmaxf(ba.y, 0.0f), ALPHA_MAX);
+            float a, oma;
+            opacity(al, ell, a, oma);
+            const float w = qpre * a;
+            K[0] = fmaf(w, rg.x, K[0]);
+            K[1] = fmaf(w, rg.y, K[1]);
+            K[2] = fmaf(w, ba.x, K[2]);
+            qpre *= oma;
+            lnq += ell * log1pf(-al);
+        }
+        return composite_run(lnq, K, n, ert, A, Cr, Cg, Cb, stop);
+    }
+    __device__ __forceinline__ bool sample(const float (&I)[C], float ell) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            float2 rg, ba;
+            lookup(c, I[c], rg, ba);
+            const float al = fminf(fmaxf(ba.y, 0.0f), ALPHA_MAX);
+            float a, oma;
+            opacity(al, ell, a, oma);
+            const float wgt = (1.0f - A) * a;
+            Cr = fmaf(wgt, rg.x, Cr);
+            Cg = fmaf(wgt, rg.y, Cg);
+            Cb = fmaf(wgt, ba.x, Cb);
+            A += wgt;
         }
         return A >= ert;
     }
@@ -307,7 +497,14 @@ struct DVRFootprint : DVRComposite<C> {
 
 template <int C>
 struct MIPMax : NoHooks {
+    static constexpr bool kRuns = true;
     float mx[C];
+    __device__ __forceinline__ long long run(const float (&I)[C], long long n, float, bool& stop) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) mx[c] = fmaxf(mx[c], I[c]);
+        stop = false;
+        return n;
+    }
     __device__ __forceinline__ MIPMax() {
 #pragma unroll
         for (int c = 0; c < C; ++c) mx[c] = -1.0f;
@@ -337,11 +534,26 @@ __device__ __forceinline__ void load_tables(const RenderArgs& a, int C, float4* 
     __syncthreads();
 }
 
-template <int C, int VS, int MODE, bool POW2>
+template <int C, int VS, int MODE, bool POW2, bool H>
 __global__ void __launch_bounds__(256) render_kernel(RenderArgs a) {
     extern __shared__ float4 s_tf[];
     __shared__ float s_scl[MAXC];
+    __shared__ __half s_sh[MAXC];
+    HalfEntry* s_tfh = reinterpret_cast<HalfEntry*>(s_tf + C * 512);
     load_tables(a, C, s_tf, s_scl);
+    if (H) {
+        for (int i = threadIdx.x; i < C * 256; i += blockDim.x) {
+            const float4 T = s_tf[2 * i], D = s_tf[2 * i + 1];
+            HalfEntry e;
+            e.rg = __floats2half2_rn(T.x, T.y);
+            e.ba = __floats2half2_rn(T.z, T.w);
+            e.drg = __floats2half2_rn(D.x, D.y);
+            e.dba = __floats2half2_rn(D.z, D.w);
+            s_tfh[i] = e;
+        }
+        if (threadIdx.x < C) s_sh[threadIdx.x] = __float2half_rn(s_scl[threadIdx.x] * 65535.0f);
+        __syncthreads();
+    }
     const int lane = threadIdx.x & 31;
     unsigned long long my_samples = 0, my_rays = 0;
     for (;;) {
@@ -359,9 +571,13 @@ __global__ void __launch_bounds__(256) render_kernel(RenderArgs a) {
         float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
         if (ray_setup(cp, a.g, px, py, d, t0, t1)) {
             ++my_rays;
-            if (MODE == 0) {
+            if (MODE == 0 && H) {
+                DVRCompositeH<C> f{{}, s_tfh, s_sh, cp.ert};
+                my_samples += march<C, VS, POW2, true>(a.g, a.pool, a.rnodes, cp, d, t0, t1, f);
+                out = make_float4(f.Cr, f.Cg, f.Cb, f.A);
+            } else if (MODE == 0) {
                 DVRComposite<C> f{{}, s_tf, s_scl, cp.ert};
-                my_samples += march<C, VS, POW2>(a.g, a.pool, a.rnodes, cp, d, t0, t1, f);
+                my_samples += march<C, VS, POW2, false>(a.g, a.pool, a.rnodes, cp, d, t0, t1, f);
                 out = make_float4(f.Cr, f.Cg, f.Cb, f.A);
             } else if (MODE == 2) {
                 DVRFootprint<C> f;
@@ -370,11 +586,11 @@ __global__ void __launch_bounds__(256) render_kernel(RenderArgs a) {
                 f.ert = cp.ert;
                 f.vmark = a.vmark;
                 f.nmark = a.nmark;
-                my_samples += march<C, VS, POW2>(a.g, a.pool, a.rnodes, cp, d, t0, t1, f);
+                my_samples += march<C, VS, POW2, false>(a.g, a.pool, a.rnodes, cp, d, t0, t1, f);
                 out = make_float4(f.Cr, f.Cg, f.Cb, f.A);
             } else {
                 MIPMax<C> f;
-                const long long n = march<C, VS, POW2>(a.g, a.pool, a.rnodes, cp, d, t0, t1, f);
+                const long long n = march<C, VS, POW2, false>(a.g, a.pool, a.rnodes, cp, d, t0, t1, f);
                 my_samples += n;
                 if (n > 0) {
                     float A = 0.f, Cr = 0.f, Cg = 0.f, Cb = 0.f;
@@ -481,8 +697,8 @@ __global__ void __launch_bounds__(256) render_backward_kernel(RenderArgs a) {
         if (!ray_setup(cp, a.g, px, py, d, t0, t1)) continue;
         const float4 gl = reinterpret_cast<const float4*>(cp.dimg)[(long long)py * cp.W + px];
         if (gl.x == 0.0f && gl.y == 0.0f && gl.z == 0.0f && gl.w == 0.0f) continue;
-        DVRComposite<C> fw{{}, s_tf, s_scl, cp.ert};
-        march<C, VS, POW2>(a.g, a.pool, a.rnodes, cp, d, t0, t1, fw);
+        DVRComposite<C, false> fw{{}, s_tf, s_scl, cp.ert}; // sample by sample, like the adjoint sweep
+        march<C, VS, POW2, false>(a.g, a.pool, a.rnodes, cp, d, t0, t1, fw);
         DVRAdjoint<C> bw;
         bw.s_tf = s_tf;
         bw.s_scl = s_scl;
@@ -498,7 +714,7 @@ __global__ void __launch_bounds__(256) render_backward_kernel(RenderArgs a) {
         bw.Af = fw.A;
 #pragma unroll
         for (int c = 0; c < C; ++c) bw.dsc[c] = 0.0f;
-        march<C, VS, POW2>(a.g, a.pool, a.rnodes, cp, d, t0, t1, bw);
+        march<C, VS, POW2, false>(a.g, a.pool, a.rnodes, cp, d, t0, t1, bw);
 #pragma unroll
         for (int c = 0; c < C; ++c) dsc[c] += bw.dsc[c];
     }
@@ -513,35 +729,38 @@ __global__ void __launch_bounds__(256) render_backward_kernel(RenderArgs a) {
         if (s_dtf[i] != 0.0f) atomicAdd(&a.dtf[i], s_dtf[i]);
 }
 
+template <int C, int VS, int MODE, bool POW2, bool H>
+static void launch_one(const RenderArgs& a, int blocks, int threads, cudaStream_t st) {
+    const size_t smem = (size_t)C * 512 * sizeof(float4) + (H ? (size_t)C * 256 * sizeof(HalfEntry) : 0);
+    cudaFuncSetAttribute(render_kernel<C, VS, MODE, POW2, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    render_kernel<C, VS, MODE, POW2, H><<<blocks, threads, smem, st>>>(a);
+}
+
 template <int C, int VS>
-static cudaError_t launch_fwd_c(const RenderArgs& a, int mode, int blocks, int threads, cudaStream_t st) {
-    const size_t smem = (size_t)C * 512 * sizeof(float4);
-    if (mode == 0) {
-        if (a.g.pow2)
-            render_kernel<C, VS, 0, true><<<blocks, threads, smem, st>>>(a);
-        else
-            render_kernel<C, VS, 0, false><<<blocks, threads, smem, st>>>(a);
+static cudaError_t launch_fwd_c(const RenderArgs& a, int mode, int fp16, int blocks, int threads, cudaStream_t st) {
+    const bool p2 = a.g.pow2 != 0;
+    if (mode == 0 && fp16) {
+        if (p2) launch_one<C, VS, 0, true, true>(a, blocks, threads, st);
+        else launch_one<C, VS, 0, false, true>(a, blocks, threads, st);
+    } else if (mode == 0) {
+        if (p2) launch_one<C, VS, 0, true, false>(a, blocks, threads, st);
+        else launch_one<C, VS, 0, false, false>(a, blocks, threads, st);
     } else if (mode == 2) {
-        if (a.g.pow2)
-            render_kernel<C, VS, 2, true><<<blocks, threads, smem, st>>>(a);
-        else
-            render_kernel<C, VS, 2, false><<<blocks, threads, smem, st>>>(a);
+        if (p2) launch_one<C, VS, 2, true, false>(a, blocks, threads, st);
+        else launch_one<C, VS, 2, false, false>(a, blocks, threads, st);
     } else {
-        if (a.g.pow2)
-            render_kernel<C, VS, 1, true><<<blocks, threads, smem, st>>>(a);
-        else
-            render_kernel<C, VS, 1, false><<<blocks, threads, smem, st>>>(a);
+        if (p2) launch_one<C, VS, 1, true, false>(a, blocks, threads, st);
+        else launch_one<C, VS, 1, false, false>(a, blocks, threads, st);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_render(const RenderArgs& a, int mode, int fp16, int blocks, int threads, cudaStream_t st) {
-    (void)fp16;
     switch (a.g.C) {
-        case 1: return launch_fwd_c<1, 1>(a, mode, blocks, threads, st);
-        case 2: return launch_fwd_c<2, 2>(a, mode, blocks, threads, st);
-        case 3: return launch_fwd_c<3, 4>(a, mode, blocks, threads, st);
-        default: return launch_fwd_c<4, 4>(a, mode, blocks, threads, st);
+        case 1: return launch_fwd_c<1, 1>(a, mode, fp16, blocks, threads, st);
+        case 2: return launch_fwd_c<2, 2>(a, mode, fp16, blocks, threads, st);
+        case 3: return launch_fwd_c<3, 4>(a, mode, fp16, blocks, threads, st);
+        default: return launch_fwd_c<4, 4>(a, mode, fp16, blocks, threads, st);
     }
 }
 

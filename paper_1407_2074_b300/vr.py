@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libvr.so")
 VR_OK, VR_ERR_INVALID_ARG, VR_ERR_OUT_OF_MEMORY, VR_ERR_CUDA, VR_ERR_STATE, VR_ERR_TIMEOUT, VR_ERR_DEVICE_ASSERT = range(7)
 VR_FP32, VR_FP16_INTERP = 0, 1
 VR_MODE_DVR, VR_MODE_MIP = 0, 1
+VR_RENDER_FP16 = 0x10
 F_CHILDREN, F_BRICK, F_TOUCHED = 1, 2, 4
 
 
@@ -72,9 +73,16 @@ def lib():
         L.vr_last_error.restype = ctypes.c_char_p
         L.vr_last_error.argtypes = [vp]
         L.vr_set_tile_shape.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+        L.vr_set_launch_shape.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L.vr_plan_create.argtypes = [vp, ctypes.POINTER(Camera), ctypes.c_int, ctypes.POINTER(vp), ctypes.c_int,
+                                     ctypes.POINTER(vp)]
+        L.vr_plan_launch.argtypes = [vp, vp]
+        L.vr_plan_samples.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+        L.vr_plan_destroy.argtypes = [vp]
         for f in ("vr_create", "vr_destroy", "vr_insert_block", "vr_insert_slice", "vr_set_transfer_functions",
                   "vr_set_clip_planes", "vr_render", "vr_render_backward", "vr_read_level", "vr_read_voxels", "vr_read_node", "vr_render_footprint",
-                  "vr_stats", "vr_set_tile_shape"):
+                  "vr_stats", "vr_set_tile_shape", "vr_set_launch_shape", "vr_plan_create", "vr_plan_launch",
+                  "vr_plan_samples", "vr_plan_destroy"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -203,6 +211,13 @@ class Renderer:
     def set_tile_shape(self, tw, th):
         self._check(lib().vr_set_tile_shape(self._ctx, tw, th))
 
+    def set_launch_shape(self, tw, th, threads=256, ctas_per_sm=8):
+        self._check(lib().vr_set_launch_shape(self._ctx, tw, th, threads, ctas_per_sm))
+
+    def plan(self, cams, images=None, mode=VR_MODE_DVR):
+        """A graph-captured single launch over all ``cams``; returns a RenderPlan."""
+        return RenderPlan(self, cams, images, mode)
+
     # ---- render ----
     def render(self, cams, images=None, mode=VR_MODE_DVR, stream=None):
         import torch
@@ -291,6 +306,44 @@ class Renderer:
         s = Stats()
         self._check(lib().vr_stats(self._ctx, ctypes.byref(s)))
         return s
+
+
+class RenderPlan:
+    """vr_render_plan: one persistent launch over a fixed camera batch, replayed as a CUDA graph."""
+
+    def __init__(self, renderer, cams, images=None, mode=VR_MODE_DVR):
+        import torch
+
+        self.r = renderer
+        n = len(cams)
+        self.cams = cams
+        self.images = images if images is not None else [
+            torch.empty((c["height"], c["width"], 4), dtype=torch.float32, device=renderer.device) for c in cams]
+        cs = (Camera * n)(*[camera_struct(c) for c in cams])
+        ptrs = (ctypes.c_void_p * n)(*[im.data_ptr() for im in self.images])
+        h = ctypes.c_void_p()
+        renderer._check(lib().vr_plan_create(renderer.handle, cs, n, ptrs, mode, ctypes.byref(h)))
+        self._p = h.value
+
+    def launch(self, stream=None):
+        self.r._check(lib().vr_plan_launch(self._p, ctypes.c_void_p(_stream_ptr(stream))))
+        return self.images
+
+    def samples(self):
+        s, r = ctypes.c_int64(), ctypes.c_int64()
+        self.r._check(lib().vr_plan_samples(self._p, ctypes.byref(s), ctypes.byref(r)))
+        return s.value, r.value
+
+    def close(self):
+        if self._p:
+            lib().vr_plan_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _torch_fn():

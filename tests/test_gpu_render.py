@@ -214,3 +214,102 @@ def test_streamed_full_size_sampled_pixels():
 def test_large_full_size_sampled_pixels():
     """The 24 GiB 2048x2048x1024 volume at 1920x1080 (orbit frame 0), sampled pixels."""
     _full_size_render(S.large(tau=0), None, 0, 24, 2)
+
+
+def test_homogeneous_runs_with_early_termination():
+    # tau = 3277 makes the background outside the tissue one homogeneous subtree: long runs of
+    # equal samples composited in closed form.  Constant alpha 0.03 per voxel makes most rays
+    # terminate inside such runs; the oracle composites sample by sample.
+    dims = (160, 128, 96)
+    spec = S.VolumeSpec(S.KIND_SPIM, dims, 3, 120, seed=12)
+    vol = spec.volume()
+    ov = oracle_dense(vol, 16, tau=3277)
+    r = _build(vol, 16, tau=3277)
+    tf = S.make_tf([31, 32, 33])
+    tf[..., 3] = 0.03
+    sc = [1.0, 1.0, 1.0]
+    for eps, ert in ((1.0, 0.99), (0.3, 0.7), (4.0, 2.0)):
+        cam = S.orbit_camera(dims, 1.7 * 160, 50.0, 30.0, 200, 150, lod_error_px=eps, ert_alpha=ert)
+        img = _render(r, [cam], tf, sc)[0]
+        _check_full(img, ov, cam, tf, sc)
+
+
+def _fp16_errors(img, ov, cam, tf, sc):
+    nc, cand, _ = O.render(ov, cam, tf, sc, None, 0)
+    return admissible_error(img.reshape(-1, 4), nc, cand)
+
+
+def test_fp16_interpolation_error_against_the_oracle(tiny):
+    import paper_1407_2074_b300 as vr
+    from paper_1407_2074_b300 import vr as V
+
+    w, vol, ov = tiny
+    r = _build(vol, 16)
+    tf, sc = w.tf(), [1.0, 1.0, 1.0]
+    img = _render(r, w.cameras, tf, sc, mode=V.VR_MODE_DVR | V.VR_RENDER_FP16)[0]
+    err = _fp16_errors(img, ov, w.cameras[0], tf, sc)
+    print(f"FP16 tiny: max {err.max():.2e} mean {err.mean():.2e}")
+    assert err.max() <= 2e-2 and err.mean() <= 2e-3
+    r16 = _build(vol, 16, precision="fp16")  # the context-wide setting gives the same image
+    assert np.array_equal(_render(r16, w.cameras, tf, sc)[0], img)
+
+
+def test_fp16_medium_spim_error():
+    from paper_1407_2074_b300 import vr as V
+
+    dims = (192, 160, 96)
+    spec = S.VolumeSpec(S.KIND_SPIM, dims, 3, 160, seed=2)
+    vol = spec.volume()
+    ov = oracle_dense(vol, 16, tau=3277)
+    r = _build(vol, 16, tau=3277)
+    cam = S.orbit_camera(dims, 2.0 * 192, 20.0, 20.0, 320, 180, lod_error_px=2.5)
+    tf, sc = S.make_tf([11, 12, 13]), [1.0, 1.0, 1.0]
+    tf[..., 3] *= 3.0
+    img32 = _render(r, [cam], tf, sc)[0]
+    img16 = _render(r, [cam], tf, sc, mode=V.VR_MODE_DVR | V.VR_RENDER_FP16)[0]
+    e32 = _fp16_errors(img32, ov, cam, tf, sc)
+    e16 = _fp16_errors(img16, ov, cam, tf, sc)
+    print(f"medium SPIM: FP32 max {e32.max():.2e}; FP16 max {e16.max():.2e} mean {e16.mean():.2e}")
+    assert e32.max() <= RGBA_TOL and e16.max() <= 2e-2 and e16.mean() <= 2e-3
+
+
+def test_graph_plan_matches_render_and_sees_updates(tiny, tmp_path, monkeypatch):
+    import torch
+    from paper_1407_2074_b300 import autotune
+    from paper_1407_2074_b300 import vr as V
+
+    w, vol, ov = tiny
+    r = _build(vol, 16)
+    cams = S.batch_cameras(w.dims)
+    tf, sc = w.tf(), [1.0, 1.0, 1.0]
+    ref = _render(r, cams, tf, sc)
+    plan = r.plan(cams)
+    plan.launch()
+    torch.cuda.synchronize()
+    for a, b in zip(plan.images, ref):
+        assert np.array_equal(a.cpu().numpy(), b)
+    s_plan, rays = plan.samples()
+    r.render(cams)
+    assert s_plan == r.stats().last_render_samples and rays > 0
+    tf2 = tf.copy()
+    tf2[..., 3] *= 0.5
+    r.set_transfer_functions(torch.from_numpy(tf2), torch.ones(3))
+    plan.launch()
+    again = _render(r, cams, tf2, sc)
+    torch.cuda.synchronize()
+    for a, b in zip(plan.images, again):
+        assert np.array_equal(a.cpu().numpy(), b)
+    plan.close()
+    monkeypatch.setenv("VR_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    shape, timings = autotune.autotune(r, cams, "tiny-64cams", reps=2,
+                                       candidates=[(8, 4, 256, 8), (16, 2, 128, 16), (32, 1, 64, 32)])
+    assert len(timings) == 3 and (tmp_path / "tune.json").exists()
+    tuned = _render(r, cams, tf2, sc)
+    for a, b in zip(tuned, again):
+        assert np.array_equal(a, b)
+    shape2, _ = autotune.autotune(r, cams, "tiny-64cams")  # cached
+    assert shape2 == shape
+    p16 = r.plan(cams[:4], mode=V.VR_MODE_DVR | V.VR_RENDER_FP16)
+    p16.launch()
+    torch.cuda.synchronize()
+    p16.close()
