@@ -76,8 +76,9 @@ __device__ __forceinline__ bool ray_setup(const CamParam& cp, const Geo& g, int 
 // alpha (no 1 - (1 - x) cancellation).
 __device__ __forceinline__ void opacity(float al, float ell, float& a, float& oma) {
     if (ell == 0.5f) {
-        const float s = sqrtf(1.0f - al);
-        a = al / (1.0f + s);
+        const float om = 1.0f - al; // >= 1e-6
+        const float s = om * rsqrtf(om);
+        a = __fdividef(al, 1.0f + s);
         oma = s;
     } else if (ell == 1.0f) {
         a = al;
@@ -90,7 +91,7 @@ __device__ __forceinline__ void opacity(float al, float ell, float& a, float& om
 }
 
 constexpr float ALPHA_MAX = 1.0f - 1e-6f;
-constexpr long long MAX_SAMPLES = 1LL << 24; // (float)k stays exact; bounds every ray
+constexpr int MAX_SAMPLES = 1 << 24; // (float)k stays exact; bounds every ray
 
 template <int C>
 struct TFLookup {
@@ -127,7 +128,7 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
     int nlev = -1;
     float tl_limit = 0.0f; // t at which L* would exceed the cached node's level
     float lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
-    long long cidx[3] = {0, 0, 0};
+    int cidx[3] = {0, 0, 0};
     bool brick = false;
     const uint16_t* sbase = nullptr;
     float avg[C];
@@ -138,7 +139,7 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
     float cv[8][C];
     constexpr int CP = (C + 1) / 2;
     __half2 hv[8][CP];
-    long long k = 0;
+    int k = 0;
     for (;; ++k) {
         const float tk = __fadd_rn(t0, __fmul_rn((float)k, dt));
         if (!(tk < t1) || k >= MAX_SAMPLES) break;
@@ -159,8 +160,9 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
                 const float size = (float)(M << nlev);
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    long long q = (long long)floorf(__fdiv_rn(p[a], size));
-                    q = q < 0 ? 0 : (q > g.nb[nlev][a] - 1 ? g.nb[nlev][a] - 1 : q);
+                    int q = (int)floorf(__fdiv_rn(p[a], size));
+                    const int qm = (int)g.nb[nlev][a] - 1;
+                    q = q < 0 ? 0 : (q > qm ? qm : q);
                     valid = valid && (q == cidx[a]);
                 }
             }
@@ -168,7 +170,7 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
         if (!valid) {
             // getNodeAtPosition: descend from the root towards L*
             int lev = N;
-            long long idx[3] = {0, 0, 0};
+            int idx[3] = {0, 0, 0};
             RNode nd = rn[g.noff[N]];
             f.on_node(g.noff[N]);
             while (lev > Lstar && (nd.flags & F_CHILDREN)) {
@@ -177,13 +179,14 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
                 const float inv = 1.0f / size;
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    long long q = POW2 ? (long long)floorf(__fmul_rn(p[a], inv)) : (long long)floorf(__fdiv_rn(p[a], size));
-                    const long long c0 = 2 * idx[a];
-                    q = q < c0 ? c0 : (q > c0 + 1 ? c0 + 1 : q);
-                    if (q > g.nb[lev][a] - 1) q = g.nb[lev][a] - 1;
+                    const float qf = POW2 ? floorf(__fmul_rn(p[a], inv)) : floorf(__fdiv_rn(p[a], size));
+                    const int c0 = 2 * idx[a];
+                    int q = qf < (float)c0 ? c0 : (qf > (float)(c0 + 1) ? c0 + 1 : (int)qf);
+                    const int qm = (int)g.nb[lev][a] - 1;
+                    if (q > qm) q = qm;
                     idx[a] = q;
                 }
-                const long long nid = g.noff[lev] + (idx[2] * g.nb[lev][1] + idx[1]) * g.nb[lev][0] + idx[0];
+                const long long nid = g.noff[lev] + ((long long)idx[2] * g.nb[lev][1] + idx[1]) * g.nb[lev][0] + idx[0];
                 nd = rn[nid];
                 f.on_node(nid);
             }
@@ -194,7 +197,7 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
             for (int a = 0; a < 3; ++a) {
                 cidx[a] = idx[a];
                 lo[a] = (idx[a] == 0) ? -CUDART_INF_F : (float)idx[a] * size;
-                hi[a] = (idx[a] == g.nb[lev][a] - 1) ? CUDART_INF_F : (float)(idx[a] + 1) * size;
+                hi[a] = (idx[a] == (int)g.nb[lev][a] - 1) ? CUDART_INF_F : (float)(idx[a] + 1) * size;
                 off[a] = (float)(idx[a] * M) - 0.5f;
             }
             inv_vox = 1.0f / (float)(1 << lev);
@@ -242,6 +245,23 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
                             hv[q][j] = __floats2half2_rn(cv[q][2 * j] * inv, (2 * j + 1 < C) ? cv[q][2 * j + 1] * inv : 0.0f);
                     }
                 }
+                if (!H) {
+                    // trilinear as a polynomial in (fx, fy, fz); integer corners make every
+                    // coefficient exact: I = k0 + kx fx + ky fy + kz fz + kxy fx fy + kxz fx fz
+                    //                        + kyz fy fz + kxyz fx fy fz
+#pragma unroll
+                    for (int c = 0; c < C; ++c) {
+                        const float v0 = cv[0][c], v1 = cv[1][c], v2 = cv[2][c], v3 = cv[3][c];
+                        const float v4 = cv[4][c], v5 = cv[5][c], v6 = cv[6][c], v7 = cv[7][c];
+                        cv[1][c] = v1 - v0;
+                        cv[2][c] = v2 - v0;
+                        cv[4][c] = v4 - v0;
+                        cv[3][c] = (v3 - v2) - (v1 - v0);
+                        cv[5][c] = (v5 - v4) - (v1 - v0);
+                        cv[6][c] = (v6 - v4) - (v2 - v0);
+                        cv[7][c] = ((v7 - v6) - (v5 - v4)) - ((v3 - v2) - (v1 - v0));
+                    }
+                }
             }
             if (H) {
                 const __half2 fx = __float2half2_rn(fr[0]), fy = __float2half2_rn(fr[1]), fz = __float2half2_rn(fr[2]);
@@ -258,15 +278,16 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
                     if (2 * j + 1 < C) I[2 * j + 1] = r.y;
                 }
             } else {
+                const float fxy = fr[0] * fr[1], fxz = fr[0] * fr[2], fyz = fr[1] * fr[2], fxyz = fxy * fr[2];
 #pragma unroll
                 for (int c = 0; c < C; ++c) {
-                    const float c00 = fmaf(fr[0], cv[1][c] - cv[0][c], cv[0][c]);
-                    const float c10 = fmaf(fr[0], cv[3][c] - cv[2][c], cv[2][c]);
-                    const float c01 = fmaf(fr[0], cv[5][c] - cv[4][c], cv[4][c]);
-                    const float c11 = fmaf(fr[0], cv[7][c] - cv[6][c], cv[6][c]);
-                    const float c0 = fmaf(fr[1], c10 - c00, c00);
-                    const float c1 = fmaf(fr[1], c11 - c01, c01);
-                    I[c] = fmaf(fr[2], c1 - c0, c0);
+                    float v = fmaf(fr[0], cv[1][c], cv[0][c]);
+                    v = fmaf(fr[1], cv[2][c], v);
+                    v = fmaf(fr[2], cv[4][c], v);
+                    v = fmaf(fxy, cv[3][c], v);
+                    v = fmaf(fxz, cv[5][c], v);
+                    v = fmaf(fyz, cv[6][c], v);
+                    I[c] = fmaf(fxyz, cv[7][c], v);
                 }
             }
         } else {
@@ -276,7 +297,7 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
                 // A brick-less node gives every sample the same intensity: find the run of samples
                 // k..k+n-1 that stay in this node with a full segment, using the same per-sample
                 // single-precision tests as above (monotone in k), and composite it in one step.
-                auto in_run = [&](long long kk) -> bool {
+                auto in_run = [&](int kk) -> bool {
                     if (kk >= MAX_SAMPLES) return false;
                     const float t = __fadd_rn(t0, __fmul_rn((float)kk, dt));
                     if (!(t < t1) || !(t < tl_limit) || !(__fsub_rn(t1, t) >= dt)) return false;
@@ -286,8 +307,9 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
                         if (POW2) {
                             if (!(pa >= lo[a] && pa < hi[a])) return false;
                         } else {
-                            long long q = (long long)floorf(__fdiv_rn(pa, (float)(M << nlev)));
-                            q = q < 0 ? 0 : (q > g.nb[nlev][a] - 1 ? g.nb[nlev][a] - 1 : q);
+                            int q = (int)floorf(__fdiv_rn(pa, (float)(M << nlev)));
+                            const int qm = (int)g.nb[nlev][a] - 1;
+                            q = q < 0 ? 0 : (q > qm ? qm : q);
                             if (q != cidx[a]) return false;
                         }
                     }
@@ -300,11 +322,11 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
                     else if (d[a] < 0.0f) te = fminf(te, (lo[a] - cp.eye[a]) / d[a]);
                 }
                 const float steps = floorf((te - tk) / dt);
-                long long ke = k + (steps > 0.0f ? (long long)fminf(steps, 16777216.0f) : 0);
-                long long aa = k, bb;
+                int ke = k + (steps > 0.0f ? (int)fminf(steps, 16777216.0f) : 0);
+                int aa = k, bb;
                 if (ke > k && in_run(ke)) {
                     aa = ke;
-                    long long st = 1;
+                    int st = 1;
                     bb = ke + 1;
                     while (in_run(bb)) {
                         aa = bb;
@@ -315,14 +337,14 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
                     bb = ke > k ? ke : k + 1;
                 }
                 while (bb - aa > 1) {
-                    const long long m = aa + (bb - aa) / 2;
+                    const int m = aa + (bb - aa) / 2;
                     if (in_run(m)) aa = m;
                     else bb = m;
                 }
-                const long long n = aa - k + 1;
+                const int n = aa - k + 1;
                 if (n >= 2) {
                     bool stop = false;
-                    const long long used = f.run(I, n, dt, stop);
+                    const int used = (int)f.run(I, n, dt, stop);
                     k += used - 1;
                     if (stop) {
                         ++k;
@@ -343,7 +365,7 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
 struct NoHooks {
     static constexpr bool kRuns = false; // composites runs of equal samples in closed form
     __device__ __forceinline__ void on_node(long long) {}
-    __device__ __forceinline__ void on_cell(const Geo&, int, const long long*, const int*) {}
+    __device__ __forceinline__ void on_cell(const Geo&, int, const int*, const int*) {}
 };
 
 // n samples of one constant intensity, each a per-sample transfer T' = T q, C' = C + T K:
@@ -482,11 +504,11 @@ struct DVRFootprint : DVRComposite<C> {
     __device__ __forceinline__ void on_node(long long nid) {
         atomicOr(&nmark[nid >> 5], 1u << (nid & 31));
     }
-    __device__ __forceinline__ void on_cell(const Geo& g, int L, const long long* idx, const int* i0) {
+    __device__ __forceinline__ void on_cell(const Geo& g, int L, const int* idx, const int* i0) {
         for (int q = 0; q < 8; ++q) {
             long long v[3];
             for (int a = 0; a < 3; ++a) {
-                long long x = idx[a] * g.M - 1 + i0[a] + ((q >> a) & 1);
+                long long x = (long long)idx[a] * g.M - 1 + i0[a] + ((q >> a) & 1);
                 v[a] = x < 0 ? 0 : (x > g.ldim[L][a] - 1 ? g.ldim[L][a] - 1 : x);
             }
             const long long bit = (v[2] * g.ldim[L][1] + v[1]) * g.ldim[L][0] + v[0];
@@ -534,8 +556,12 @@ __device__ __forceinline__ void load_tables(const RenderArgs& a, int C, float4* 
     __syncthreads();
 }
 
+#ifndef VR_RENDER_MIN_CTAS
+#define VR_RENDER_MIN_CTAS 3 // resident 256-thread CTAs per SM the register budget is sized for
+#endif
+
 template <int C, int VS, int MODE, bool POW2, bool H>
-__global__ void __launch_bounds__(256) render_kernel(RenderArgs a) {
+__global__ void __launch_bounds__(256, VR_RENDER_MIN_CTAS) render_kernel(RenderArgs a) {
     extern __shared__ float4 s_tf[];
     __shared__ float s_scl[MAXC];
     __shared__ __half s_sh[MAXC];

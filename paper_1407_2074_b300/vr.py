@@ -11,7 +11,7 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libvr.so")
+LIB_PATH = os.environ.get("VR_LIBRARY", os.path.join(_HERE, "libvr.so"))
 
 VR_OK, VR_ERR_INVALID_ARG, VR_ERR_OUT_OF_MEMORY, VR_ERR_CUDA, VR_ERR_STATE, VR_ERR_TIMEOUT, VR_ERR_DEVICE_ASSERT = range(7)
 VR_FP32, VR_FP16_INTERP = 0, 1
