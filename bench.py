@@ -155,6 +155,21 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def insert_algorithmic_bytes(dims, C, n, levels):
+    """Bytes an insert of n whole z-slices must move: read the block, write level 0, and for every
+    level L >= 1 read the changed level-(L-1) planes and write the changed level-L planes
+    (C channels x 2 bytes per voxel; border copies and padding are layout, not counted)."""
+    X, Y, _ = dims
+    plane = lambda L: -(-X // 2 ** L) * -(-Y // 2 ** L) * C * 2
+    tot = 2 * n * plane(0)
+    planes = n
+    for L in range(1, levels):
+        tot += planes * plane(L - 1)
+        planes = max(1, planes // 2)
+        tot += planes * plane(L)
+    return tot
+
+
 def batched_leg(torch, vr, S, reps=20):
     """The tiny volume seen by 64 mixed-resolution cameras (16 each at 256^2, 640x480, 1280x720,
     1920x1080, one clip plane each): one persistent launch per batch, captured in a CUDA graph,
@@ -283,6 +298,7 @@ def main():
     r = vr.Renderer(w.dims, 3, w.brick, tau=w.tau)
     build_s, spec = build_volume(w, r, torch)
     pool_gb = r.stats().pool_bytes / 1e9
+    levels = r.levels
     tf = torch.from_numpy(w.tf()).cuda()
     sc = torch.ones(3, device="cuda")
     r.set_transfer_functions(tf, sc)
@@ -406,6 +422,7 @@ def main():
     vox, nodes = r.footprint([w.cameras[frame_of[args.warmup]]])
     U = sum(vox) * 3 * 2 + nodes * 16 + 3 * 256 * 16 + H * W * 16
     peak, peak_kind = peaks()
+    ins_bytes = insert_algorithmic_bytes(w.dims, 3, SLICES_PER_STEP, levels)
     achieved = U / (render_ms / 1000.0) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": None, "kernel": "render_kernel<3,4,DVR>", "algorithmic_bytes_per_launch": U,
@@ -439,6 +456,9 @@ def main():
                            "lod_error_px": 1.0, "ert_alpha": 0.99, "l2": "inputs larger than L2 (brick pool "
                            f"{pool_gb:.1f} GB)", "parallelism": f"replicas x{ws}"},
                 "ms_per_frame": render_ms, "insert_ms_per_8_slices": insert_ms,
+                "insert_roofline": {"bound": "hbm", "algorithmic_bytes": ins_bytes,
+                                    "achieved": ins_bytes / (insert_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                                    "frac": ins_bytes / (insert_ms / 1e3) / 1e9 / peak},
                 "samples_per_frame": samples / args.steps / ws, "build_s_full_volume": build_s,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp16": fp16,
                 "batched": batched, "adjoint": adjoint,

@@ -465,7 +465,7 @@ vr_status vr_render(vr_ctx* c, const vr_camera* cams, int n, float* const* image
     long long tiles = 0;
     s = prepare_cams(c, cams, n, images, nullptr, st, &tiles);
     if (s != VR_OK) return s;
-    CK(c, cudaMemsetAsync(c->counter, 0, sizeof(unsigned int), st));
+    CK(c, cudaMemsetAsync(c->counter, 0, sizeof(unsigned long long), st));
     CK(c, cudaMemsetAsync(c->stats, 0, 2 * sizeof(unsigned long long), st));
     RenderArgs a = make_args(c, n, tiles);
     CK(c, launch_render(a, mode, fp16 && mode == VR_MODE_DVR, grid_for(c, tiles, c->threads, c->ctas_per_sm),
@@ -485,12 +485,12 @@ vr_status vr_render_backward(vr_ctx* c, const vr_camera* cams, int n, const floa
     if (s != VR_OK) return s;
     CK(c, cudaMemsetAsync(dtf, 0, sizeof(float) * 1024 * c->g.C, st));
     CK(c, cudaMemsetAsync(dscale, 0, sizeof(float) * c->g.C, st));
-    CK(c, cudaMemsetAsync(c->counter, 0, sizeof(unsigned int), st));
+    CK(c, cudaMemsetAsync(c->counter, 0, sizeof(unsigned long long), st));
     RenderArgs a = make_args(c, n, tiles);
     a.stats = nullptr;
     a.dtf = dtf;
     a.dscale = dscale;
-    CK(c, launch_render_backward(a, grid_for(c, tiles, 256, 4), 256, st));
+    CK(c, launch_render_backward(a, grid_for(c, tiles, 128, 3), 128, st));
     return VR_OK;
 }
 
@@ -506,7 +506,7 @@ vr_status vr_render_footprint(vr_ctx* c, const vr_camera* cams, int n, float* co
     long long tiles = 0;
     s = prepare_cams(c, cams, n, images, nullptr, st, &tiles);
     if (s != VR_OK) return s;
-    CK(c, cudaMemsetAsync(c->counter, 0, sizeof(unsigned int), st));
+    CK(c, cudaMemsetAsync(c->counter, 0, sizeof(unsigned long long), st));
     CK(c, cudaMemsetAsync(c->stats, 0, 2 * sizeof(unsigned long long), st));
     RenderArgs a = make_args(c, n, tiles);
     for (int L = 0; L <= c->g.N; ++L) a.vmark[L] = voxel_marks[L];
@@ -686,7 +686,7 @@ vr_status vr_plan_create(vr_ctx* c, const vr_camera* cams, int n, float* const* 
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
     if (e == cudaSuccess) {
-        cudaMemsetAsync(p->counter, 0, sizeof(unsigned int), cs);
+        cudaMemsetAsync(p->counter, 0, sizeof(unsigned long long), cs);
         cudaMemsetAsync(p->stats, 0, 2 * sizeof(unsigned long long), cs);
         launch_render(a, mode, fp16 && mode == VR_MODE_DVR, grid_for(c, tiles, c->threads, c->ctas_per_sm), c->threads, cs);
         e = cudaStreamEndCapture(cs, &p->graph);

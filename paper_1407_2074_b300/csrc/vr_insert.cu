@@ -285,46 +285,64 @@ __global__ void __launch_bounds__(256) level_update_kernel(LevelArgs a) {
         }
     }
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    // finalize the node (Sec. "CPU Data Structure": homogeneity, AVG; all channels must be
-    // homogeneous, Sec. "Handling Multi-Channel Data")
+    if (threadIdx.x >= 32) return;
+    // finalize the node in warp 0 (Sec. "CPU Data Structure": homogeneity, AVG; all channels must
+    // be homogeneous, Sec. "Handling Multi-Channel Data").  Lane l reads the plane statistics of
+    // planes l, l+32, ... and lane l < 8 the subtree statistics of child l; warp reductions.
+    const int lane = threadIdx.x;
+    uint32_t bmn[C], bmx[C], cmn[C], cmx[C];
+    unsigned long long bsm[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        bmn[c] = cmn[c] = 0xffffu;
+        bmx[c] = cmx[c] = 0u;
+        bsm[c] = 0ull;
+    }
+    for (int lz = 1 + lane; lz <= nin[2]; lz += 32) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const PStat p = a.ps[((long long)slot * M + (lz - 1)) * C + c];
+            bmn[c] = min(bmn[c], (uint32_t)p.mn);
+            bmx[c] = max(bmx[c], (uint32_t)p.mx);
+            bsm[c] += p.sum;
+        }
+    }
+    if (L > 0 && lane < 8) {
+        const long long ci = 2 * b[0] + (lane & 1), cj = 2 * b[1] + ((lane >> 1) & 1), ck = 2 * b[2] + (lane >> 2);
+        if (ci < g.nb[L - 1][0] && cj < g.nb[L - 1][1] && ck < g.nb[L - 1][2]) {
+            const long long cn = g.noff[L - 1] + (ck * g.nb[L - 1][1] + cj) * g.nb[L - 1][0] + ci;
+            const bool t = (a.rn[cn].flags & F_TOUCHED) != 0;
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                cmn[c] = t ? (uint32_t)a.ns[cn].smin[c] : (uint32_t)g.bg;
+                cmx[c] = t ? (uint32_t)a.ns[cn].smax[c] : (uint32_t)g.bg;
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        for (int o = 16; o > 0; o >>= 1) {
+            bmn[c] = min(bmn[c], __shfl_xor_sync(0xffffffffu, bmn[c], o));
+            bmx[c] = max(bmx[c], __shfl_xor_sync(0xffffffffu, bmx[c], o));
+            bsm[c] += __shfl_xor_sync(0xffffffffu, bsm[c], o);
+            cmn[c] = min(cmn[c], __shfl_xor_sync(0xffffffffu, cmn[c], o));
+            cmx[c] = max(cmx[c], __shfl_xor_sync(0xffffffffu, cmx[c], o));
+        }
+    }
+    if (lane != 0) return;
     NStat s;
     bool bh = true, sh = true;
     s.count = nin[0] * nin[1] * nin[2];
+#pragma unroll
     for (int c = 0; c < C; ++c) {
-        uint32_t mn = 0xffffu, mx = 0;
-        unsigned long long sm = 0;
-        for (int lz = 1; lz <= nin[2]; ++lz) {
-            PStat p = a.ps[((long long)slot * M + (lz - 1)) * C + c];
-            mn = min(mn, (uint32_t)p.mn);
-            mx = max(mx, (uint32_t)p.mx);
-            sm += p.sum;
-        }
-        s.bmin[c] = (uint16_t)mn;
-        s.bmax[c] = (uint16_t)mx;
-        s.bsum[c] = sm;
-        uint32_t smn = mn, smx = mx;
-        if (L > 0) {
-            smn = 0xffffu;
-            smx = 0;
-            for (int dz = 0; dz < 2; ++dz)
-                for (int dy = 0; dy < 2; ++dy)
-                    for (int dx = 0; dx < 2; ++dx) {
-                        long long ci = 2 * b[0] + dx, cj = 2 * b[1] + dy, ck = 2 * b[2] + dz;
-                        if (ci >= g.nb[L - 1][0] || cj >= g.nb[L - 1][1] || ck >= g.nb[L - 1][2]) continue;
-                        long long cn = g.noff[L - 1] + (ck * g.nb[L - 1][1] + cj) * g.nb[L - 1][0] + ci;
-                        if (a.rn[cn].flags & F_TOUCHED) {
-                            smn = min(smn, (uint32_t)a.ns[cn].smin[c]);
-                            smx = max(smx, (uint32_t)a.ns[cn].smax[c]);
-                        } else {
-                            smn = min(smn, (uint32_t)g.bg);
-                            smx = max(smx, (uint32_t)g.bg);
-                        }
-                    }
-        }
+        s.bmin[c] = (uint16_t)bmn[c];
+        s.bmax[c] = (uint16_t)bmx[c];
+        s.bsum[c] = bsm[c];
+        const uint32_t smn = (L > 0) ? cmn[c] : bmn[c];
+        const uint32_t smx = (L > 0) ? cmx[c] : bmx[c];
         s.smin[c] = (uint16_t)smn;
         s.smax[c] = (uint16_t)smx;
-        if (!((int)mx - (int)mn < (int)g.tau)) bh = false;
+        if (!((int)bmx[c] - (int)bmn[c] < (int)g.tau)) bh = false;
         if (!((int)smx - (int)smn < (int)g.tau)) sh = false;
     }
     for (int c = C; c < MAXC; ++c) {

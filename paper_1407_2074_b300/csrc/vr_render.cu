@@ -23,6 +23,8 @@
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
+#include <type_traits>
+
 #include "vr_internal.h"
 
 namespace vrk {
@@ -580,44 +582,47 @@ __global__ void __launch_bounds__(256, VR_RENDER_MIN_CTAS) render_kernel(RenderA
         if (threadIdx.x < C) s_sh[threadIdx.x] = __float2half_rn(s_scl[threadIdx.x] * 65535.0f);
         __syncthreads();
     }
+    // Warp tiles: a warp takes one tile_w x tile_h pixel tile at a time and its lanes march their
+    // rays in lockstep.  Neighbouring rays at the same depth read the same cache lines; refilling
+    // lanes with new rays as soon as theirs end (tried) loses that coherence and is ~3.6x slower.
+    using F = std::conditional_t<MODE == 1, MIPMax<C>,
+                                 std::conditional_t<MODE == 2, DVRFootprint<C>,
+                                                    std::conditional_t<H, DVRCompositeH<C>, DVRComposite<C>>>>;
     const int lane = threadIdx.x & 31;
+    unsigned long long* counter = reinterpret_cast<unsigned long long*>(a.counter);
     unsigned long long my_samples = 0, my_rays = 0;
     for (;;) {
-        unsigned int tile = 0;
-        if (lane == 0) tile = atomicAdd(a.counter, 1u);
+        unsigned long long tile = 0;
+        if (lane == 0) tile = atomicAdd(counter, 1ull);
         tile = __shfl_sync(0xffffffffu, tile, 0);
         if ((long long)tile >= a.total_tiles) break;
-        const int ci = find_camera(a.cams, a.n_cams, tile);
-        const CamParam& cp = a.cams[ci];
-        const long long lt = (long long)tile - cp.tile_begin;
-        const int px = (int)(lt % cp.tiles_x) * a.tile_w + lane % a.tile_w;
-        const int py = (int)(lt / cp.tiles_x) * a.tile_h + lane / a.tile_w;
-        if (px >= cp.W || py >= cp.H) continue;
-        float d[3], t0, t1;
+        const int ci = find_camera(a.cams, a.n_cams, (long long)tile);
+        const CamParam* cp = &a.cams[ci];
+        const long long lt = (long long)tile - cp->tile_begin;
+        const int px = (int)(lt % cp->tiles_x) * a.tile_w + lane % a.tile_w;
+        const int py = (int)(lt / cp->tiles_x) * a.tile_h + lane / a.tile_w;
+        if (px >= cp->W || py >= cp->H) continue;
+        float dd[3], r0, r1;
         float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (ray_setup(cp, a.g, px, py, d, t0, t1)) {
+        if (ray_setup(*cp, a.g, px, py, dd, r0, r1)) {
             ++my_rays;
-            if (MODE == 0 && H) {
-                DVRCompositeH<C> f{{}, s_tfh, s_sh, cp.ert};
-                my_samples += march<C, VS, POW2, true>(a.g, a.pool, a.rnodes, cp, d, t0, t1, f);
-                out = make_float4(f.Cr, f.Cg, f.Cb, f.A);
-            } else if (MODE == 0) {
-                DVRComposite<C> f{{}, s_tf, s_scl, cp.ert};
-                my_samples += march<C, VS, POW2, false>(a.g, a.pool, a.rnodes, cp, d, t0, t1, f);
-                out = make_float4(f.Cr, f.Cg, f.Cb, f.A);
-            } else if (MODE == 2) {
-                DVRFootprint<C> f;
+            F f;
+            if constexpr (MODE == 1) {
+                f = MIPMax<C>();
+            } else if constexpr (MODE == 2) {
                 f.s_tf = s_tf;
                 f.s_scl = s_scl;
-                f.ert = cp.ert;
+                f.ert = cp->ert;
                 f.vmark = a.vmark;
                 f.nmark = a.nmark;
-                my_samples += march<C, VS, POW2, false>(a.g, a.pool, a.rnodes, cp, d, t0, t1, f);
-                out = make_float4(f.Cr, f.Cg, f.Cb, f.A);
+            } else if constexpr (H) {
+                f = DVRCompositeH<C>{{}, s_tfh, s_sh, cp->ert};
             } else {
-                MIPMax<C> f;
-                const long long n = march<C, VS, POW2, false>(a.g, a.pool, a.rnodes, cp, d, t0, t1, f);
-                my_samples += n;
+                f = DVRComposite<C>{{}, s_tf, s_scl, cp->ert};
+            }
+            const long long n = march<C, VS, POW2, H>(a.g, a.pool, a.rnodes, *cp, dd, r0, r1, f);
+            my_samples += (unsigned long long)n;
+            if constexpr (MODE == 1) {
                 if (n > 0) {
                     float A = 0.f, Cr = 0.f, Cg = 0.f, Cb = 0.f;
 #pragma unroll
@@ -633,9 +638,11 @@ __global__ void __launch_bounds__(256, VR_RENDER_MIN_CTAS) render_kernel(RenderA
                     }
                     out = make_float4(Cr, Cg, Cb, A);
                 }
+            } else {
+                out = make_float4(f.Cr, f.Cg, f.Cb, f.A);
             }
         }
-        reinterpret_cast<float4*>(cp.img)[(long long)py * cp.W + px] = out;
+        reinterpret_cast<float4*>(cp->img)[(long long)py * cp->W + px] = out;
     }
     for (int o = 16; o > 0; o >>= 1) {
         my_samples += __shfl_xor_sync(0xffffffffu, my_samples, o);
@@ -662,6 +669,35 @@ struct DVRAdjoint : NoHooks {
     float gC[3], gAf, Cf[3], Af;
     float A = 0.0f, Cp[3] = {0.0f, 0.0f, 0.0f};
     float dsc[C];
+    // Per channel, the table-entry pair (i, i+1) this lane is accumulating into and the pending
+    // sums S = sum g and L = sum lam g (entry i receives S - L, entry i+1 receives L).  Samples
+    // of one ray mostly stay on one pair, so shared-memory atomics happen once per change of
+    // pair instead of once per sample (32 lanes hitting one entry serialise).
+    int pk[C];
+    float pS[C][4], pL[C][4];
+    __device__ __forceinline__ void reset() {
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            pk[c] = -1;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) pS[c][q] = pL[c][q] = 0.0f;
+        }
+    }
+    __device__ __forceinline__ void flush(int c) {
+        if (pk[c] < 0) return;
+        float* e0 = s_dtf + (c * 256 + pk[c]) * 4;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float lo = pS[c][q] - pL[c][q];
+            if (lo != 0.0f) atomicAdd(e0 + q, lo);
+            if (pL[c][q] != 0.0f) atomicAdd(e0 + 4 + q, pL[c][q]);
+            pS[c][q] = pL[c][q] = 0.0f;
+        }
+    }
+    __device__ __forceinline__ void flush_all() {
+#pragma unroll
+        for (int c = 0; c < C; ++c) flush(c);
+    }
     __device__ __forceinline__ bool sample(const float (&I)[C], float ell) {
 #pragma unroll
         for (int c = 0; c < C; ++c) {
@@ -681,15 +717,16 @@ struct DVRAdjoint : NoHooks {
                                  gAf * (1.0f - Af);
             const float ga = T * (gC[0] * t.r + gC[1] * t.g + gC[2] * t.b) + suffix / oma;
             const float gq[4] = {gC[0] * w, gC[1] * w, gC[2] * w, clamped ? 0.0f : ga * ell * oma / (1.0f - al)};
-            float* e0 = s_dtf + (c * 256 + t.i) * 4;
             const float4 D = s_tf[(c * 256 + t.i) * 2 + 1];
             const float glam = gq[0] * D.x + gq[1] * D.y + gq[2] * D.z + gq[3] * D.w;
+            if (t.i != pk[c]) {
+                flush(c);
+                pk[c] = t.i;
+            }
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                if (gq[q] != 0.0f) {
-                    atomicAdd(e0 + q, (1.0f - t.lam) * gq[q]);
-                    atomicAdd(e0 + 4 + q, t.lam * gq[q]);
-                }
+                pS[c][q] += gq[q];
+                pL[c][q] = fmaf(t.lam, gq[q], pL[c][q]);
             }
             if (t.xr > 0.0f && t.xr < 1.0f) dsc[c] += glam * 255.0f * I[c] * (1.0f / 65535.0f);
         }
@@ -698,7 +735,7 @@ struct DVRAdjoint : NoHooks {
 };
 
 template <int C, int VS, bool POW2>
-__global__ void __launch_bounds__(256) render_backward_kernel(RenderArgs a) {
+__global__ void __launch_bounds__(128, 3) render_backward_kernel(RenderArgs a) {
     extern __shared__ float4 s_tf[];
     __shared__ float s_scl[MAXC];
     float* s_dtf = reinterpret_cast<float*>(s_tf + C * 512);
@@ -740,7 +777,9 @@ __global__ void __launch_bounds__(256) render_backward_kernel(RenderArgs a) {
         bw.Af = fw.A;
 #pragma unroll
         for (int c = 0; c < C; ++c) bw.dsc[c] = 0.0f;
+        bw.reset();
         march<C, VS, POW2, false>(a.g, a.pool, a.rnodes, cp, d, t0, t1, bw);
+        bw.flush_all();
 #pragma unroll
         for (int c = 0; c < C; ++c) dsc[c] += bw.dsc[c];
     }
