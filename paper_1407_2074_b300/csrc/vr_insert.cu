@@ -25,6 +25,8 @@ __device__ __forceinline__ long long clampll(long long v, long long lo, long lon
     return v < lo ? lo : (v > hi ? hi : v);
 }
 
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
 __device__ __forceinline__ uint16_t rhu(unsigned long long S, unsigned long long k) {
     return (uint16_t)((2ull * S + k) / (2ull * k));
 }
@@ -118,6 +120,7 @@ struct LevelArgs {
     long long blo[3], bn[3]; // brick range of the grid
     const uint16_t* block;   // L = 0 input
     long long org[3], ext[3];
+    int mshift; // log2(M) when M is a power of two, else -1
     uint16_t* pool;
     RNode* rn;
     NStat* ns;
@@ -187,71 +190,22 @@ __global__ void __launch_bounds__(256) level_update_kernel(LevelArgs a) {
         interior = interior && (b[d] * M <= a.hi[d]) && (b[d] * M + M - 1 >= a.lo[d]);
     }
     uint16_t* dst = a.pool + (long long)slot * g.slot_elems;
-    const int nx = l1[0] - l0[0] + 1, ny = l1[1] - l0[1] + 1, nz = l1[2] - l0[2] + 1;
-    const long long n = (long long)nx * ny * nz;
-    for (long long t = threadIdx.x; t < n; t += blockDim.x) {
-        const int lx = l0[0] + (int)(t % nx), ly = l0[1] + (int)((t / nx) % ny), lz = l0[2] + (int)(t / ((long long)nx * ny));
-        const long long x = clampll(b[0] * M - 1 + lx, 0, g.ldim[L][0] - 1);
-        const long long y = clampll(b[1] * M - 1 + ly, 0, g.ldim[L][1] - 1);
-        const long long z = clampll(b[2] * M - 1 + lz, 0, g.ldim[L][2] - 1);
-        uint16_t v[VS];
-#pragma unroll
-        for (int c = 0; c < VS; ++c) v[c] = 0;
-        if (L == 0) {
-            const uint16_t* src = a.block + (((z - a.org[2]) * a.ext[1] + (y - a.org[1])) * a.ext[0] + (x - a.org[0])) * C;
-#pragma unroll
-            for (int c = 0; c < C; ++c) v[c] = src[c];
-        } else {
-            const long long cx = 2 * x, cy = 2 * y, cz = 2 * z;
-            const bool hx = cx + 1 < g.ldim[L - 1][0], hy = cy + 1 < g.ldim[L - 1][1], hz = cz + 1 < g.ldim[L - 1][2];
-            const long long cbx = cx / M, cby = cy / M, cbz = cz / M;
-            const long long cnid = g.noff[L - 1] + (cbz * g.nb[L - 1][1] + cby) * g.nb[L - 1][0] + cbx;
-            const int cs = a.rn[cnid].slot;
-            const unsigned k = (1u + hx) * (1u + hy) * (1u + hz);
-            if (cs < 0 || cs >= g.n_slots_cap) {
-#pragma unroll
-                for (int c = 0; c < C; ++c) v[c] = g.bg;
-                if (cs >= g.n_slots_cap) atomicOr(a.err, ERR_SLOT_RANGE);
-            } else {
-                const uint16_t* cp = a.pool + (long long)cs * g.slot_elems +
-                                     (((cz - cbz * M + 1) * S + (cy - cby * M + 1)) * S + (cx - cbx * M + 1)) * VS;
-                unsigned long long sum[C];
-#pragma unroll
-                for (int c = 0; c < C; ++c) sum[c] = 0;
-                for (int dz = 0; dz <= (int)hz; ++dz)
-                    for (int dy = 0; dy <= (int)hy; ++dy)
-                        for (int dx = 0; dx <= (int)hx; ++dx) {
-                            const uint16_t* q = cp + (((long long)dz * S + dy) * S + dx) * VS;
-#pragma unroll
-                            for (int c = 0; c < C; ++c) sum[c] += q[c];
-                        }
-#pragma unroll
-                for (int c = 0; c < C; ++c) v[c] = rhu(sum[c], k);
-            }
-        }
-        uint16_t* d = dst + (((long long)lz * S + ly) * S + lx) * VS;
-        if (VS == 4) {
-            uint2 w;
-            w.x = (uint32_t)v[0] | ((uint32_t)v[VS > 1 ? 1 : 0] << 16);
-            w.y = (uint32_t)v[VS > 2 ? 2 : 0] | ((uint32_t)v[VS > 3 ? 3 : 0] << 16);
-            *reinterpret_cast<uint2*>(d) = w;
-        } else if (VS == 2) {
-            *reinterpret_cast<uint32_t*>(d) = (uint32_t)v[0] | ((uint32_t)v[VS > 1 ? 1 : 0] << 16);
-        } else {
-            d[0] = v[0];
-        }
-    }
-    if (!interior) return; // only border copies changed: the node's own statistics did not
-    __syncthreads();
-    // per-plane statistics of the changed interior planes (in-volume voxels only)
-    long long nin[3];
+    const int nx = l1[0] - l0[0] + 1, ny = l1[1] - l0[1] + 1;
+    const int np = nx * ny;
+    int nin[3]; // in-volume interior extent of this brick
     for (int d = 0; d < 3; ++d) {
-        long long r = g.ldim[L][d] - b[d] * M;
-        nin[d] = r < M ? r : M;
+        const long long r = g.ldim[L][d] - b[d] * M;
+        nin[d] = (int)(r < M ? r : M);
     }
-    const int pz0 = l0[2] > 1 ? l0[2] : 1, pz1 = l1[2] < M ? l1[2] : M;
-    for (int lz = pz0; lz <= pz1; ++lz) {
-        if (lz > nin[2]) break; // plane beyond the real extent: unused
+    // When the change covers every interior in-volume position of a plane (always for whole
+    // slices) the plane statistics are gathered while writing; otherwise re-read afterwards.
+    const bool full_xy = l0[0] <= 1 && l1[0] >= nin[0] && l0[1] <= 1 && l1[1] >= nin[1];
+    const int bx0 = (int)(b[0] * M) - 1, by0 = (int)(b[1] * M) - 1, bz0 = (int)(b[2] * M) - 1;
+    const int X = (int)g.ldim[L][0], Y = (int)g.ldim[L][1], Z = (int)g.ldim[L][2];
+    const int msh = a.mshift; // log2(M) when M is a power of two, else -1
+    for (int lz = l0[2]; lz <= l1[2]; ++lz) {
+        const int z = clampi(bz0 + lz, 0, Z - 1);
+        const bool stats_here = interior && full_xy && lz >= 1 && lz <= nin[2]; // uniform in the CTA
         uint32_t mn[C], mx[C];
         unsigned long long sm[C];
 #pragma unroll
@@ -260,27 +214,120 @@ __global__ void __launch_bounds__(256) level_update_kernel(LevelArgs a) {
             mx[c] = 0;
             sm[c] = 0;
         }
-        const long long np = nin[0] * nin[1];
-        for (long long t = threadIdx.x; t < np; t += blockDim.x) {
-            const int lx = 1 + (int)(t % nin[0]), ly = 1 + (int)(t / nin[0]);
-            const uint16_t* q = dst + (((long long)lz * S + ly) * S + lx) * VS;
+        for (int t = threadIdx.x; t < np; t += blockDim.x) {
+            const int ty = t / nx;
+            const int lx = l0[0] + (t - ty * nx), ly = l0[1] + ty;
+            const int x = clampi(bx0 + lx, 0, X - 1), y = clampi(by0 + ly, 0, Y - 1);
+            uint16_t v[VS];
 #pragma unroll
-            for (int c = 0; c < C; ++c) {
-                uint32_t val = q[c];
-                mn[c] = min(mn[c], val);
-                mx[c] = max(mx[c], val);
-                sm[c] += val;
+            for (int c = 0; c < VS; ++c) v[c] = 0;
+            if (L == 0) {
+                const uint16_t* src =
+                    a.block + ((((long long)(z - a.org[2]) * a.ext[1]) + (y - a.org[1])) * a.ext[0] + (x - a.org[0])) * C;
+#pragma unroll
+                for (int c = 0; c < C; ++c) v[c] = src[c];
+            } else {
+                const int cx = 2 * x, cy = 2 * y, cz = 2 * z;
+                const bool hx = cx + 1 < (int)g.ldim[L - 1][0], hy = cy + 1 < (int)g.ldim[L - 1][1],
+                           hz = cz + 1 < (int)g.ldim[L - 1][2];
+                const int cbx = msh >= 0 ? cx >> msh : cx / M, cby = msh >= 0 ? cy >> msh : cy / M,
+                          cbz = msh >= 0 ? cz >> msh : cz / M;
+                const long long cnid = g.noff[L - 1] + ((long long)cbz * g.nb[L - 1][1] + cby) * g.nb[L - 1][0] + cbx;
+                const int cs = a.rn[cnid].slot;
+                const unsigned k = (1u + hx) * (1u + hy) * (1u + hz);
+                if (cs < 0 || cs >= g.n_slots_cap) {
+#pragma unroll
+                    for (int c = 0; c < C; ++c) v[c] = g.bg;
+                    if (cs >= g.n_slots_cap) atomicOr(a.err, ERR_SLOT_RANGE);
+                } else {
+                    const uint16_t* cp = a.pool + (long long)cs * g.slot_elems +
+                                         (((cz - cbz * M + 1) * S + (cy - cby * M + 1)) * S + (cx - cbx * M + 1)) * VS;
+                    uint32_t sum[C];
+#pragma unroll
+                    for (int c = 0; c < C; ++c) sum[c] = 0;
+                    for (int dz = 0; dz <= (int)hz; ++dz)
+                        for (int dy = 0; dy <= (int)hy; ++dy)
+                            for (int dx = 0; dx <= (int)hx; ++dx) {
+                                const uint16_t* q = cp + ((dz * S + dy) * S + dx) * VS;
+#pragma unroll
+                                for (int c = 0; c < C; ++c) sum[c] += q[c];
+                            }
+#pragma unroll
+                    for (int c = 0; c < C; ++c) v[c] = rhu(sum[c], k);
+                }
+            }
+            uint16_t* d = dst + ((lz * S + ly) * S + lx) * VS;
+            if (VS == 4) {
+                uint2 w;
+                w.x = (uint32_t)v[0] | ((uint32_t)v[VS > 1 ? 1 : 0] << 16);
+                w.y = (uint32_t)v[VS > 2 ? 2 : 0] | ((uint32_t)v[VS > 3 ? 3 : 0] << 16);
+                *reinterpret_cast<uint2*>(d) = w;
+            } else if (VS == 2) {
+                *reinterpret_cast<uint32_t*>(d) = (uint32_t)v[0] | ((uint32_t)v[VS > 1 ? 1 : 0] << 16);
+            } else {
+                d[0] = v[0];
+            }
+            if (stats_here && lx >= 1 && lx <= nin[0] && ly >= 1 && ly <= nin[1]) {
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    mn[c] = min(mn[c], (uint32_t)v[c]);
+                    mx[c] = max(mx[c], (uint32_t)v[c]);
+                    sm[c] += v[c];
+                }
             }
         }
-        block_reduce_stats<C>(mn, mx, sm);
-        if (threadIdx.x == 0) {
+        if (stats_here) {
+            block_reduce_stats<C>(mn, mx, sm);
+            if (threadIdx.x == 0) {
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    PStat p;
+                    p.mn = (uint16_t)mn[c];
+                    p.mx = (uint16_t)mx[c];
+                    p.sum = (uint32_t)sm[c];
+                    a.ps[((long long)slot * M + (lz - 1)) * C + c] = p;
+                }
+            }
+        }
+    }
+    if (!interior) return; // only border copies changed: the node's own statistics did not
+    if (!full_xy) {
+        __syncthreads();
+        // per-plane statistics of the changed interior planes, re-read (in-volume voxels only)
+        const int pz0 = l0[2] > 1 ? l0[2] : 1, pz1 = l1[2] < M ? l1[2] : M;
+        for (int lz = pz0; lz <= pz1; ++lz) {
+            if (lz > nin[2]) break; // plane beyond the real extent: unused
+            uint32_t mn[C], mx[C];
+            unsigned long long sm[C];
 #pragma unroll
             for (int c = 0; c < C; ++c) {
-                PStat p;
-                p.mn = (uint16_t)mn[c];
-                p.mx = (uint16_t)mx[c];
-                p.sum = (uint32_t)sm[c];
-                a.ps[((long long)slot * M + (lz - 1)) * C + c] = p;
+                mn[c] = 0xffffu;
+                mx[c] = 0;
+                sm[c] = 0;
+            }
+            const int npl = nin[0] * nin[1];
+            for (int t = threadIdx.x; t < npl; t += blockDim.x) {
+                const int ty = t / nin[0];
+                const int lx = 1 + (t - ty * nin[0]), ly = 1 + ty;
+                const uint16_t* q = dst + ((lz * S + ly) * S + lx) * VS;
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    const uint32_t val = q[c];
+                    mn[c] = min(mn[c], val);
+                    mx[c] = max(mx[c], val);
+                    sm[c] += val;
+                }
+            }
+            block_reduce_stats<C>(mn, mx, sm);
+            if (threadIdx.x == 0) {
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    PStat p;
+                    p.mn = (uint16_t)mn[c];
+                    p.mx = (uint16_t)mx[c];
+                    p.sum = (uint32_t)sm[c];
+                    a.ps[((long long)slot * M + (lz - 1)) * C + c] = p;
+                }
             }
         }
     }
@@ -380,6 +427,10 @@ cudaError_t launch_level_update(const Geo& g, int L, const long long lo[3], cons
         a.ext[d] = ext ? ext[d] : 0;
     }
     a.block = block;
+    a.mshift = -1;
+    if (g.pow2)
+        for (int sft = 0; sft < 31; ++sft)
+            if ((1 << sft) == g.M) a.mshift = sft;
     a.pool = pool;
     a.rn = rn;
     a.ns = ns;
