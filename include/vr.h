@@ -129,6 +129,14 @@ vr_status vr_insert_slice(vr_ctx* ctx, int64_t z, const uint16_t* slice, int on_
  * stream.  Errors: VR_ERR_INVALID_ARG (NULL pointers). */
 vr_status vr_set_transfer_functions(vr_ctx* ctx, const float* tf, const float* scale, void* cuda_stream);
 
+/* Per-channel affine sample transforms (Sec. "Correction of Chromatic Aberration": each sampling
+ * point is multiplied by the channel's matrix before the volume is sampled).  m is a host array
+ * [C][3][4] (row-major 3x4: rotation/scale and translation, level-0 voxel units), copied; NULL
+ * or all-identity restores the untransformed path.  With transforms, each channel descends the
+ * octree from its own point (FP32 interpolation; VR_RENDER_FP16 is ignored).  Used by vr_render,
+ * plans and vr_render_backward.  Errors: VR_ERR_INVALID_ARG (non-finite entries). */
+vr_status vr_set_channel_transforms(vr_ctx* ctx, const float* m);
+
 /* Context-wide clip planes (up to three half-spaces n.p + d >= 0, Sec. "Integration into
  * Voreen"), used by every camera whose n_clip is -1.  planes[n][4] is a host array, copied.
  * Errors: VR_ERR_INVALID_ARG (n outside 0..3, NULL planes with n > 0). */

@@ -116,6 +116,14 @@ typedef struct {
 int or_render(or_volume* v, const or_camera* cam, const float* tf, const float* scale, int mode, int64_t n,
               const int32_t* px, const int32_t* py, or_pixel* out, int threads);
 
+/* As or_render, with a per-channel affine sample transform (Sec. "Correction of Chromatic
+ * Aberration"): channel c samples the volume at xf[c] * p, xf [C][3][4] (NULL = identity). */
+int or_render_xf(or_volume* v, const or_camera* cam, const float* tf, const float* scale, const float* xf, int mode,
+                 int64_t n, const int32_t* px, const int32_t* py, or_pixel* out, int threads);
+int or_render_grad_xf(or_volume* v, const or_camera* cam, const float* tf, const float* scale, const float* xf,
+                      int64_t n, const int32_t* px, const int32_t* py, const double* dl, double* dtf, double* dscale,
+                      int threads);
+
 /* Gradient of sum_pixels sum_k dl[p][k] * I[p][k] with respect to tf and scale (FP64, natural
  * decisions).  dl: [n][4].  Outputs are overwritten. */
 int or_render_grad(or_volume* v, const or_camera* cam, const float* tf, const float* scale, int64_t n,

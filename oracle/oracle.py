@@ -79,6 +79,12 @@ def lib():
         L.or_render_grad.argtypes = [ctypes.c_void_p, ctypes.POINTER(Camera), ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+        L.or_render_xf.argtypes = [ctypes.c_void_p, ctypes.POINTER(Camera), ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_int]
+        L.or_render_grad_xf.argtypes = [ctypes.c_void_p, ctypes.POINTER(Camera), ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
         L.or_ray.argtypes = [ctypes.POINTER(Geom), ctypes.POINTER(Camera), ctypes.c_int, ctypes.c_int,
                              ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
                              ctypes.POINTER(ctypes.c_float)]
@@ -191,8 +197,9 @@ def image_pixels(width, height):
     return px.ravel().copy(), py.ravel().copy()
 
 
-def render(vol: Volume, cam: dict, tf: np.ndarray, scale, pixels=None, mode=0, threads=0):
-    """Returns (n_cand [n], cand [n][MAXCAND][4], samples [n]); pixels = (px, py) arrays or None (all)."""
+def render(vol: Volume, cam: dict, tf: np.ndarray, scale, pixels=None, mode=0, threads=0, xf=None):
+    """Returns (n_cand [n], cand [n][MAXCAND][4], samples [n]); pixels = (px, py) arrays or None (all).
+    xf: optional per-channel affine sample transforms [C][3][4]."""
     if pixels is None:
         px, py = image_pixels(cam["width"], cam["height"])
     else:
@@ -203,8 +210,10 @@ def render(vol: Volume, cam: dict, tf: np.ndarray, scale, pixels=None, mode=0, t
     sc = np.ascontiguousarray(scale, dtype=np.float32)
     out = (Pixel * max(n, 1))()
     cs = camera_struct(cam)
-    rc = lib().or_render(vol.handle, ctypes.byref(cs), tf.ctypes.data, sc.ctypes.data, mode, n, px.ctypes.data,
-                         py.ctypes.data, ctypes.addressof(out), threads)
+    xfa = None if xf is None else np.ascontiguousarray(xf, dtype=np.float32).reshape(-1, 3, 4)
+    rc = lib().or_render_xf(vol.handle, ctypes.byref(cs), tf.ctypes.data, sc.ctypes.data,
+                            None if xfa is None else xfa.ctypes.data, mode, n, px.ctypes.data, py.ctypes.data,
+                            ctypes.addressof(out), threads)
     if rc != 0:
         raise ValueError("oracle render: invalid arguments")
     arr = np.ctypeslib.as_array(ctypes.cast(out, ctypes.POINTER(ctypes.c_uint8)),
@@ -216,14 +225,14 @@ def render(vol: Volume, cam: dict, tf: np.ndarray, scale, pixels=None, mode=0, t
     return rec["n_cand"].copy(), rec["rgba"].copy(), rec["samples"].copy()
 
 
-def render_image(vol, cam, tf, scale, mode=0, threads=0):
+def render_image(vol, cam, tf, scale, mode=0, threads=0, xf=None):
     """Natural-decision image [H][W][4] (float64) plus the candidate arrays."""
-    nc, cand, samples = render(vol, cam, tf, scale, None, mode, threads)
+    nc, cand, samples = render(vol, cam, tf, scale, None, mode, threads, xf)
     H, W = cam["height"], cam["width"]
     return cand[:, 0, :].reshape(H, W, 4), nc.reshape(H, W), cand.reshape(H, W, MAXCAND, 4), samples.reshape(H, W)
 
 
-def render_grad(vol, cam, tf, scale, pixels, dl, threads=0):
+def render_grad(vol, cam, tf, scale, pixels, dl, threads=0, xf=None):
     """d(sum dl * I)/d(tf, scale) over the listed pixels; dl [n][4]."""
     px = np.ascontiguousarray(pixels[0], dtype=np.int32)
     py = np.ascontiguousarray(pixels[1], dtype=np.int32)
@@ -235,8 +244,10 @@ def render_grad(vol, cam, tf, scale, pixels, dl, threads=0):
     dtf = np.zeros((C, 256, 4), dtype=np.float64)
     dsc = np.zeros(C, dtype=np.float64)
     cs = camera_struct(cam)
-    rc = lib().or_render_grad(vol.handle, ctypes.byref(cs), tf.ctypes.data, sc.ctypes.data, n, px.ctypes.data,
-                              py.ctypes.data, dl.ctypes.data, dtf.ctypes.data, dsc.ctypes.data, threads)
+    xfa = None if xf is None else np.ascontiguousarray(xf, dtype=np.float32).reshape(-1, 3, 4)
+    rc = lib().or_render_grad_xf(vol.handle, ctypes.byref(cs), tf.ctypes.data, sc.ctypes.data,
+                                 None if xfa is None else xfa.ctypes.data, n, px.ctypes.data, py.ctypes.data,
+                                 dl.ctypes.data, dtf.ctypes.data, dsc.ctypes.data, threads)
     if rc != 0:
         raise ValueError("oracle render_grad: invalid arguments")
     return dtf, dsc

@@ -221,8 +221,15 @@ static void rec_push(recbuf* b, const rec_t* r) {
 
 /* One ray.  mode 0: emission-absorption with ERT candidates; mode 1: MIP.
  * rec != NULL records the natural-decision forward for the adjoint. */
+/* Per-channel affine sample transform (Sec. "Correction of Chromatic Aberration": each sampling
+ * point is multiplied by the matrix of the current channel).  m is [3][4] (rows x, y, z; last
+ * column the translation), evaluated in single precision in this order. */
+static void channel_point(const float* m, const float p[3], float q[3]) {
+    for (int i = 0; i < 3; ++i) q[i] = ((m[4 * i] * p[0] + m[4 * i + 1] * p[1]) + m[4 * i + 2] * p[2]) + m[4 * i + 3];
+}
+
 static void march(or_volume* v, const or_camera* cam, const cam_derived* cd, const float* tf, const float* scale,
-                  int mode, int px, int py, or_pixel* out, recbuf* rec) {
+                  const float* xf, int mode, int px, int py, or_pixel* out, recbuf* rec) {
     const or_geom* g = or_volume_geom(v);
     int C = g->C;
     memset(out, 0, sizeof(*out));
@@ -249,9 +256,21 @@ static void march(or_volume* v, const or_camera* cam, const cam_derived* cd, con
             if (tk >= cd->tl[L]) Lstar = L;
         or_node nd;
         int lev = descend(v, p, Lstar, &nd);
+        or_node ndc[OR_MAXC];
+        int levc[OR_MAXC];
+        float pc[OR_MAXC][3];
+        if (xf) /* every channel descends from its own transformed point */
+            for (int c = 0; c < C; ++c) {
+                channel_point(xf + 12 * c, p, pc[c]);
+                levc[c] = descend(v, pc[c], Lstar, &ndc[c]);
+            }
         if (!have_nat || mode == 1) ++nsamp;
         for (int c = 0; c < C; ++c) {
-            double I = nd.has_brick ? trilinear(v, lev, p, c) : (double)nd.avg[c];
+            double I;
+            if (xf)
+                I = ndc[c].has_brick ? trilinear(v, levc[c], pc[c], c) : (double)ndc[c].avg[c];
+            else
+                I = nd.has_brick ? trilinear(v, lev, p, c) : (double)nd.avg[c];
             if (mode == 1) {
                 if (I > mip[c]) mip[c] = I;
                 continue;
@@ -342,6 +361,7 @@ typedef struct {
     cam_derived cd;
     const float* tf;
     const float* scale;
+    const float* xf; /* NULL or [C][3][4] per-channel transforms */
     int mode;
     const int32_t* px;
     const int32_t* py;
@@ -350,7 +370,8 @@ typedef struct {
 
 static void render_range(void* p, int64_t b, int64_t e) {
     render_job* j = (render_job*)p;
-    for (int64_t i = b; i < e; ++i) march(j->v, j->cam, &j->cd, j->tf, j->scale, j->mode, j->px[i], j->py[i], &j->out[i], NULL);
+    for (int64_t i = b; i < e; ++i)
+        march(j->v, j->cam, &j->cd, j->tf, j->scale, j->xf, j->mode, j->px[i], j->py[i], &j->out[i], NULL);
 }
 
 static int cam_valid(const or_camera* cam) {
@@ -360,8 +381,8 @@ static int cam_valid(const or_camera* cam) {
     return 1;
 }
 
-int or_render(or_volume* v, const or_camera* cam, const float* tf, const float* scale, int mode, int64_t n,
-              const int32_t* px, const int32_t* py, or_pixel* out, int threads) {
+int or_render_xf(or_volume* v, const or_camera* cam, const float* tf, const float* scale, const float* xf, int mode,
+                 int64_t n, const int32_t* px, const int32_t* py, or_pixel* out, int threads) {
     if (!v || !cam_valid(cam) || !tf || !scale || !px || !py || !out || (mode != 0 && mode != 1)) return -1;
     render_job j;
     j.v = v;
@@ -369,12 +390,18 @@ int or_render(or_volume* v, const or_camera* cam, const float* tf, const float* 
     cam_setup(or_volume_geom(v), cam, &j.cd);
     j.tf = tf;
     j.scale = scale;
+    j.xf = xf;
     j.mode = mode;
     j.px = px;
     j.py = py;
     j.out = out;
     or_parallel_for(n, 16, threads, render_range, &j);
     return 0;
+}
+
+int or_render(or_volume* v, const or_camera* cam, const float* tf, const float* scale, int mode, int64_t n,
+              const int32_t* px, const int32_t* py, or_pixel* out, int threads) {
+    return or_render_xf(v, cam, tf, scale, NULL, mode, n, px, py, out, threads);
 }
 
 /* ---- adjoint ---- */
@@ -436,15 +463,16 @@ static void* grad_worker(void* p) {
         if (i >= j->n) break;
         rb.n = 0;
         or_pixel px;
-        march(j->rj.v, j->rj.cam, &j->rj.cd, j->rj.tf, j->rj.scale, 0, j->rj.px[i], j->rj.py[i], &px, &rb);
+        march(j->rj.v, j->rj.cam, &j->rj.cd, j->rj.tf, j->rj.scale, j->rj.xf, 0, j->rj.px[i], j->rj.py[i], &px, &rb);
         ray_grad(g, j->rj.tf, &rb, j->dl + 4 * i, dtf, dsc);
     }
     free(rb.r);
     return NULL;
 }
 
-int or_render_grad(or_volume* v, const or_camera* cam, const float* tf, const float* scale, int64_t n,
-                   const int32_t* px, const int32_t* py, const double* dl, double* dtf, double* dscale, int threads) {
+int or_render_grad_xf(or_volume* v, const or_camera* cam, const float* tf, const float* scale, const float* xf,
+                      int64_t n, const int32_t* px, const int32_t* py, const double* dl, double* dtf, double* dscale,
+                      int threads) {
     if (!v || !cam_valid(cam) || !tf || !scale || !px || !py || !dl || !dtf || !dscale) return -1;
     const or_geom* g = or_volume_geom(v);
     int C = g->C;
@@ -456,6 +484,7 @@ int or_render_grad(or_volume* v, const or_camera* cam, const float* tf, const fl
     cam_setup(g, cam, &j.rj.cd);
     j.rj.tf = tf;
     j.rj.scale = scale;
+    j.rj.xf = xf;
     j.rj.px = px;
     j.rj.py = py;
     j.n = n;
@@ -480,4 +509,9 @@ int or_render_grad(or_volume* v, const or_camera* cam, const float* tf, const fl
     free(j.dtf);
     free(j.dscale);
     return 0;
+}
+
+int or_render_grad(or_volume* v, const or_camera* cam, const float* tf, const float* scale, int64_t n,
+                   const int32_t* px, const int32_t* py, const double* dl, double* dtf, double* dscale, int threads) {
+    return or_render_grad_xf(v, cam, tf, scale, NULL, n, px, py, dl, dtf, dscale, threads);
 }

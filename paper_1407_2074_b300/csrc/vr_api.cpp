@@ -51,6 +51,8 @@ struct vr_ctx {
     float clip_default[VR_MAX_CLIP][4] = {};
     int tile_w = 8, tile_h = 4;
     int threads = 256, ctas_per_sm = 8; // render launch shape (autotuned per workload)
+    int has_xf = 0;                     // per-channel sample transforms (identity when 0)
+    float xf[VR_MAX_CHANNELS][12] = {};
     bool failed = false;
     std::string msg;
 };
@@ -327,6 +329,26 @@ vr_status vr_set_transfer_functions(vr_ctx* c, const float* tf, const float* sca
     return VR_OK;
 }
 
+vr_status vr_set_channel_transforms(vr_ctx* c, const float* m) {
+    vr_status s = check_ctx(c);
+    if (s != VR_OK) return s;
+    if (!m) {
+        c->has_xf = 0;
+        return VR_OK;
+    }
+    bool identity = true;
+    for (int ch = 0; ch < c->g.C; ++ch)
+        for (int q = 0; q < 12; ++q) {
+            const float v = m[12 * ch + q];
+            if (!std::isfinite(v)) return fail(c, VR_ERR_INVALID_ARG, "non-finite transform");
+            c->xf[ch][q] = v;
+            const float id = (q == 0 || q == 5 || q == 10) ? 1.0f : 0.0f;
+            if (v != id) identity = false;
+        }
+    c->has_xf = identity ? 0 : 1;
+    return VR_OK;
+}
+
 vr_status vr_set_clip_planes(vr_ctx* c, int n, const float* planes) {
     vr_status s = check_ctx(c);
     if (s != VR_OK) return s;
@@ -442,6 +464,8 @@ static RenderArgs make_args(vr_ctx* c, int n, long long tiles) {
     a.counter = c->counter;
     a.stats = c->stats;
     a.err = c->err;
+    a.has_xf = c->has_xf;
+    std::memcpy(a.xf, c->xf, sizeof a.xf);
     return a;
 }
 

@@ -86,6 +86,8 @@ struct RenderArgs {
     int tile_w, tile_h;
     unsigned int* counter;              // tile queue head (reset before each launch)
     unsigned long long* stats;          // [0] samples, [1] rays
+    int has_xf;                         // per-channel sample transforms active
+    float xf[MAXC][12];                 // channel c samples at xf[c] (3x4, row-major) applied to p
     unsigned int* vmark[MAXL];          // footprint mode: one bit per level-L voxel
     unsigned int* nmark;                // footprint mode: one bit per node
     float* dtf;                         // backward: [C][256][4]

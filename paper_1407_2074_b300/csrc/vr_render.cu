@@ -106,7 +106,7 @@ struct TFLookup {
         const float w = x * 255.0f;
         i = min((int)w, 254);
         lam = w - (float)i;
-        const float4 T = s_tf[(c * 256 + i) * 2], D = s_tf[(c * 256 + i) * 2 + 1];
+        const float4 T = s_tf[c * 256 + i], D = s_tf[(C + c) * 256 + i];
         r = fmaf(lam, D.x, T.x);
         g = fmaf(lam, D.y, T.y);
         b = fmaf(lam, D.z, T.z);
@@ -129,21 +129,23 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
     // node cache
     int nlev = -1;
     float tl_limit = 0.0f; // t at which L* would exceed the cached node's level
-    float lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    float bnd[3] = {0, 0, 0}; // the node-box face each axis is heading for (+-inf at the grid ends)
+    const bool neg[3] = {!(d[0] > 0.0f), !(d[1] > 0.0f), !(d[2] > 0.0f)};
     int cidx[3] = {0, 0, 0};
     bool brick = false;
     const uint16_t* sbase = nullptr;
     float avg[C];
     float off[3] = {0, 0, 0};
     float inv_vox = 1.0f;
-    // cell cache
-    const uint16_t* cell = nullptr;
+    // cell cache (offset of the cached cell's first corner inside the slot, -1 = none)
+    int cell = -1;
     float cv[8][C];
     constexpr int CP = (C + 1) / 2;
     __half2 hv[8][CP];
     int k = 0;
-    for (;; ++k) {
-        const float tk = __fadd_rn(t0, __fmul_rn((float)k, dt));
+    float kf = 0.0f; // == (float)k, exact below 2^24
+    for (;; ++k, kf += 1.0f) {
+        const float tk = __fadd_rn(t0, __fmul_rn(kf, dt));
         if (!(tk < t1) || k >= MAX_SAMPLES) break;
         const float ell = fminf(dt, __fsub_rn(t1, tk));
         float p[3];
@@ -156,8 +158,10 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
         bool valid = nlev >= 0 && tk < tl_limit;
         if (valid) {
             if (POW2) {
+                // positions move monotonically along each axis, so only the face the ray is heading
+                // for can be crossed: (p < hi) for d > 0, (p >= lo) otherwise
 #pragma unroll
-                for (int a = 0; a < 3; ++a) valid = valid && (p[a] >= lo[a]) && (p[a] < hi[a]);
+                for (int a = 0; a < 3; ++a) valid = valid && ((p[a] < bnd[a]) != neg[a]);
             } else {
                 const float size = (float)(M << nlev);
 #pragma unroll
@@ -198,8 +202,10 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 cidx[a] = idx[a];
-                lo[a] = (idx[a] == 0) ? -CUDART_INF_F : (float)idx[a] * size;
-                hi[a] = (idx[a] == (int)g.nb[lev][a] - 1) ? CUDART_INF_F : (float)(idx[a] + 1) * size;
+                if (d[a] > 0.0f)
+                    bnd[a] = (idx[a] == (int)g.nb[lev][a] - 1) ? CUDART_INF_F : (float)(idx[a] + 1) * size;
+                else
+                    bnd[a] = (idx[a] == 0) ? -CUDART_INF_F : (float)idx[a] * size;
                 off[a] = (float)(idx[a] * M) - 0.5f;
             }
             inv_vox = 1.0f / (float)(1 << lev);
@@ -207,7 +213,7 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
             sbase = brick ? pool + (long long)nd.slot * g.slot_elems : nullptr;
 #pragma unroll
             for (int c = 0; c < C; ++c) avg[c] = (float)nd.avg[c];
-            cell = nullptr;
+            cell = -1;
         }
         float I[C];
         if (brick) {
@@ -221,9 +227,10 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
                 fr[a] = __fsub_rn(u, fl);
                 i0[a] = ii < 0 ? 0 : (ii > M ? M : ii);
             }
-            const uint16_t* cp0 = sbase + ((long long)(i0[2] * S + i0[1]) * S + i0[0]) * VS;
-            if (cp0 != cell) {
-                cell = cp0;
+            const int coff = ((i0[2] * S + i0[1]) * S + i0[0]) * VS;
+            if (coff != cell) {
+                cell = coff;
+                const uint16_t* cp0 = sbase + coff;
                 f.on_cell(g, nlev, cidx, i0);
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
@@ -307,7 +314,7 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
                     for (int a = 0; a < 3; ++a) {
                         const float pa = __fadd_rn(cp.eye[a], __fmul_rn(t, d[a]));
                         if (POW2) {
-                            if (!(pa >= lo[a] && pa < hi[a])) return false;
+                            if ((pa < bnd[a]) == neg[a]) return false;
                         } else {
                             int q = (int)floorf(__fdiv_rn(pa, (float)(M << nlev)));
                             const int qm = (int)g.nb[nlev][a] - 1;
@@ -320,8 +327,7 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
                 float te = fminf(tl_limit, t1 - dt);
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    if (d[a] > 0.0f) te = fminf(te, (hi[a] - cp.eye[a]) / d[a]);
-                    else if (d[a] < 0.0f) te = fminf(te, (lo[a] - cp.eye[a]) / d[a]);
+                    if (d[a] != 0.0f) te = fminf(te, (bnd[a] - cp.eye[a]) / d[a]);
                 }
                 const float steps = floorf((te - tk) / dt);
                 int ke = k + (steps > 0.0f ? (int)fminf(steps, 16777216.0f) : 0);
@@ -348,12 +354,159 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
                     bool stop = false;
                     const int used = (int)f.run(I, n, dt, stop);
                     k += used - 1;
+                    kf = (float)k;
                     if (stop) {
                         ++k;
                         break;
                     }
                     continue;
                 }
+            }
+        }
+        if (f.sample(I, ell)) {
+            ++k;
+            break;
+        }
+    }
+    return k;
+}
+
+// March with a per-channel affine sample transform (Sec. "Correction of Chromatic Aberration"):
+// channel c samples at q_c = X_c p, X_c a 3x4 matrix applied in single precision in a fixed order
+// (((m0 p0 + m1 p1) + m2 p2) + m3).  Each channel descends from its own point and keeps its own
+// node and cell cache; the node test checks both faces because rounded transformed positions
+// need not be monotone.  Samples are composited one by one (no closed-form runs).
+template <int C, int VS, bool POW2, class F>
+__device__ __forceinline__ long long march_xf(const Geo& g, const uint16_t* __restrict__ pool,
+                                              const RNode* __restrict__ rn, const CamParam& cp, const float d[3],
+                                              float t0, float t1, const float (*xf)[12], F& f) {
+    const float dt = cp.dt;
+    const int N = g.N, M = g.M, S = g.S;
+    int Lstar = 0;
+    float tnext = (N >= 1) ? cp.tl[1] : CUDART_INF_F;
+    int nlev[C], cell[C];
+    float tl_limit[C], lo[C][3], hi[C][3], off[C][3], inv_vox[C], avg[C], cv[C][8];
+    const uint16_t* sbase[C];
+    bool brick[C];
+    int cidx[C][3];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        nlev[c] = -1;
+        cell[c] = -1;
+        tl_limit[c] = 0.0f;
+        brick[c] = false;
+        sbase[c] = nullptr;
+    }
+    int k = 0;
+    float kf = 0.0f;
+    for (;; ++k, kf += 1.0f) {
+        const float tk = __fadd_rn(t0, __fmul_rn(kf, dt));
+        if (!(tk < t1) || k >= MAX_SAMPLES) break;
+        const float ell = fminf(dt, __fsub_rn(t1, tk));
+        float p[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) p[a] = __fadd_rn(cp.eye[a], __fmul_rn(tk, d[a]));
+        while (tk >= tnext) {
+            ++Lstar;
+            tnext = (Lstar < N) ? cp.tl[Lstar + 1] : CUDART_INF_F;
+        }
+        float I[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const float* m = xf[c];
+            float q[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+                q[i] = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(m[4 * i], p[0]), __fmul_rn(m[4 * i + 1], p[1])),
+                                           __fmul_rn(m[4 * i + 2], p[2])),
+                                 m[4 * i + 3]);
+            bool valid = nlev[c] >= 0 && tk < tl_limit[c];
+            if (valid) {
+                if (POW2) {
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) valid = valid && (q[a] >= lo[c][a]) && (q[a] < hi[c][a]);
+                } else {
+                    const float size = (float)(M << nlev[c]);
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        int qq = (int)floorf(__fdiv_rn(q[a], size));
+                        const int qm = (int)g.nb[nlev[c]][a] - 1;
+                        qq = qq < 0 ? 0 : (qq > qm ? qm : qq);
+                        valid = valid && (qq == cidx[c][a]);
+                    }
+                }
+            }
+            if (!valid) {
+                int lev = N;
+                int idx[3] = {0, 0, 0};
+                RNode nd = rn[g.noff[N]];
+                while (lev > Lstar && (nd.flags & F_CHILDREN)) {
+                    --lev;
+                    const float size = (float)(M << lev);
+                    const float inv = 1.0f / size;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        const float qf = POW2 ? floorf(__fmul_rn(q[a], inv)) : floorf(__fdiv_rn(q[a], size));
+                        const int c0 = 2 * idx[a];
+                        int qq = qf < (float)c0 ? c0 : (qf > (float)(c0 + 1) ? c0 + 1 : (int)qf);
+                        const int qm = (int)g.nb[lev][a] - 1;
+                        if (qq > qm) qq = qm;
+                        idx[a] = qq;
+                    }
+                    nd = rn[g.noff[lev] + ((long long)idx[2] * g.nb[lev][1] + idx[1]) * g.nb[lev][0] + idx[0]];
+                }
+                nlev[c] = lev;
+                tl_limit[c] = (lev < N) ? cp.tl[lev + 1] : CUDART_INF_F;
+                const float size = (float)(M << lev);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    cidx[c][a] = idx[a];
+                    lo[c][a] = (idx[a] == 0) ? -CUDART_INF_F : (float)idx[a] * size;
+                    hi[c][a] = (idx[a] == (int)g.nb[lev][a] - 1) ? CUDART_INF_F : (float)(idx[a] + 1) * size;
+                    off[c][a] = (float)(idx[a] * M) - 0.5f;
+                }
+                inv_vox[c] = 1.0f / (float)(1 << lev);
+                brick[c] = (nd.flags & F_BRICK) && nd.slot >= 0 && nd.slot < g.n_slots_cap;
+                sbase[c] = brick[c] ? pool + (long long)nd.slot * g.slot_elems : nullptr;
+                avg[c] = (float)nd.avg[c];
+                cell[c] = -1;
+            }
+            if (brick[c]) {
+                float fr[3];
+                int i0[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const float u = __fsub_rn(__fmul_rn(q[a], inv_vox[c]), off[c][a]);
+                    const float fl = floorf(u);
+                    const int ii = (int)fl;
+                    fr[a] = __fsub_rn(u, fl);
+                    i0[a] = ii < 0 ? 0 : (ii > M ? M : ii);
+                }
+                const int coff = ((i0[2] * S + i0[1]) * S + i0[0]) * VS;
+                if (coff != cell[c]) {
+                    cell[c] = coff;
+                    float v[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e)
+                        v[e] = (float)__ldg(sbase[c] + coff + ((((e >> 2) & 1) * S + ((e >> 1) & 1)) * S + (e & 1)) * VS + c);
+                    cv[c][0] = v[0];
+                    cv[c][1] = v[1] - v[0];
+                    cv[c][2] = v[2] - v[0];
+                    cv[c][4] = v[4] - v[0];
+                    cv[c][3] = (v[3] - v[2]) - (v[1] - v[0]);
+                    cv[c][5] = (v[5] - v[4]) - (v[1] - v[0]);
+                    cv[c][6] = (v[6] - v[4]) - (v[2] - v[0]);
+                    cv[c][7] = ((v[7] - v[6]) - (v[5] - v[4])) - ((v[3] - v[2]) - (v[1] - v[0]));
+                }
+                float r = fmaf(fr[0], cv[c][1], cv[c][0]);
+                r = fmaf(fr[1], cv[c][2], r);
+                r = fmaf(fr[2], cv[c][4], r);
+                r = fmaf(fr[0] * fr[1], cv[c][3], r);
+                r = fmaf(fr[0] * fr[2], cv[c][5], r);
+                r = fmaf(fr[1] * fr[2], cv[c][6], r);
+                I[c] = fmaf(fr[0] * fr[1] * fr[2], cv[c][7], r);
+            } else {
+                I[c] = avg[c];
             }
         }
         if (f.sample(I, ell)) {
@@ -421,6 +574,7 @@ struct DVRComposite : NoHooks {
         return composite_run(lnq, K, n, ert, A, Cr, Cg, Cb, stop);
     }
     __device__ __forceinline__ bool sample(const float (&I)[C], float ell) {
+        float T = 1.0f - A; // transmittance: w = T a, T <- T (1 - a)
 #pragma unroll
         for (int c = 0; c < C; ++c) {
             TFLookup<C> t;
@@ -428,12 +582,13 @@ struct DVRComposite : NoHooks {
             const float al = fminf(fmaxf(t.al, 0.0f), ALPHA_MAX);
             float a, oma;
             opacity(al, ell, a, oma);
-            const float w = (1.0f - A) * a;
+            const float w = T * a;
             Cr = fmaf(w, t.r, Cr);
             Cg = fmaf(w, t.g, Cg);
             Cb = fmaf(w, t.b, Cb);
-            A += w;
+            T *= oma;
         }
+        A = 1.0f - T;
         return A >= ert;
     }
 };
@@ -553,7 +708,9 @@ __device__ __forceinline__ int find_camera(const CamParam* __restrict__ cams, in
 }
 
 __device__ __forceinline__ void load_tables(const RenderArgs& a, int C, float4* s_tf, float* s_scl) {
-    for (int i = threadIdx.x; i < C * 512; i += blockDim.x) s_tf[i] = a.tf[i];
+    // entries in s_tf[0, C*256), differences in s_tf[C*256, 2*C*256): 16-byte strides keep lanes
+    // with different entries on different banks
+    for (int i = threadIdx.x; i < C * 512; i += blockDim.x) s_tf[(i & 1) * C * 256 + (i >> 1)] = a.tf[i];
     if (threadIdx.x < C) s_scl[threadIdx.x] = a.scl[threadIdx.x];
     __syncthreads();
 }
@@ -562,7 +719,7 @@ __device__ __forceinline__ void load_tables(const RenderArgs& a, int C, float4* 
 #define VR_RENDER_MIN_CTAS 3 // resident 256-thread CTAs per SM the register budget is sized for
 #endif
 
-template <int C, int VS, int MODE, bool POW2, bool H>
+template <int C, int VS, int MODE, bool POW2, bool H, bool XF = false>
 __global__ void __launch_bounds__(256, VR_RENDER_MIN_CTAS) render_kernel(RenderArgs a) {
     extern __shared__ float4 s_tf[];
     __shared__ float s_scl[MAXC];
@@ -571,7 +728,7 @@ __global__ void __launch_bounds__(256, VR_RENDER_MIN_CTAS) render_kernel(RenderA
     load_tables(a, C, s_tf, s_scl);
     if (H) {
         for (int i = threadIdx.x; i < C * 256; i += blockDim.x) {
-            const float4 T = s_tf[2 * i], D = s_tf[2 * i + 1];
+            const float4 T = s_tf[i], D = s_tf[C * 256 + i];
             HalfEntry e;
             e.rg = __floats2half2_rn(T.x, T.y);
             e.ba = __floats2half2_rn(T.z, T.w);
@@ -620,7 +777,11 @@ __global__ void __launch_bounds__(256, VR_RENDER_MIN_CTAS) render_kernel(RenderA
             } else {
                 f = DVRComposite<C>{{}, s_tf, s_scl, cp->ert};
             }
-            const long long n = march<C, VS, POW2, H>(a.g, a.pool, a.rnodes, *cp, dd, r0, r1, f);
+            long long n;
+            if constexpr (XF)
+                n = march_xf<C, VS, POW2>(a.g, a.pool, a.rnodes, *cp, dd, r0, r1, a.xf, f);
+            else
+                n = march<C, VS, POW2, H>(a.g, a.pool, a.rnodes, *cp, dd, r0, r1, f);
             my_samples += (unsigned long long)n;
             if constexpr (MODE == 1) {
                 if (n > 0) {
@@ -717,7 +878,7 @@ struct DVRAdjoint : NoHooks {
                                  gAf * (1.0f - Af);
             const float ga = T * (gC[0] * t.r + gC[1] * t.g + gC[2] * t.b) + suffix / oma;
             const float gq[4] = {gC[0] * w, gC[1] * w, gC[2] * w, clamped ? 0.0f : ga * ell * oma / (1.0f - al)};
-            const float4 D = s_tf[(c * 256 + t.i) * 2 + 1];
+            const float4 D = s_tf[(C + c) * 256 + t.i];
             const float glam = gq[0] * D.x + gq[1] * D.y + gq[2] * D.z + gq[3] * D.w;
             if (t.i != pk[c]) {
                 flush(c);
@@ -734,7 +895,7 @@ struct DVRAdjoint : NoHooks {
     }
 };
 
-template <int C, int VS, bool POW2>
+template <int C, int VS, bool POW2, bool XF = false>
 __global__ void __launch_bounds__(128, 3) render_backward_kernel(RenderArgs a) {
     extern __shared__ float4 s_tf[];
     __shared__ float s_scl[MAXC];
@@ -761,7 +922,10 @@ __global__ void __launch_bounds__(128, 3) render_backward_kernel(RenderArgs a) {
         const float4 gl = reinterpret_cast<const float4*>(cp.dimg)[(long long)py * cp.W + px];
         if (gl.x == 0.0f && gl.y == 0.0f && gl.z == 0.0f && gl.w == 0.0f) continue;
         DVRComposite<C, false> fw{{}, s_tf, s_scl, cp.ert}; // sample by sample, like the adjoint sweep
-        march<C, VS, POW2, false>(a.g, a.pool, a.rnodes, cp, d, t0, t1, fw);
+        if constexpr (XF)
+            march_xf<C, VS, POW2>(a.g, a.pool, a.rnodes, cp, d, t0, t1, a.xf, fw);
+        else
+            march<C, VS, POW2, false>(a.g, a.pool, a.rnodes, cp, d, t0, t1, fw);
         DVRAdjoint<C> bw;
         bw.s_tf = s_tf;
         bw.s_scl = s_scl;
@@ -778,7 +942,10 @@ __global__ void __launch_bounds__(128, 3) render_backward_kernel(RenderArgs a) {
 #pragma unroll
         for (int c = 0; c < C; ++c) bw.dsc[c] = 0.0f;
         bw.reset();
-        march<C, VS, POW2, false>(a.g, a.pool, a.rnodes, cp, d, t0, t1, bw);
+        if constexpr (XF)
+            march_xf<C, VS, POW2>(a.g, a.pool, a.rnodes, cp, d, t0, t1, a.xf, bw);
+        else
+            march<C, VS, POW2, false>(a.g, a.pool, a.rnodes, cp, d, t0, t1, bw);
         bw.flush_all();
 #pragma unroll
         for (int c = 0; c < C; ++c) dsc[c] += bw.dsc[c];
@@ -794,16 +961,27 @@ __global__ void __launch_bounds__(128, 3) render_backward_kernel(RenderArgs a) {
         if (s_dtf[i] != 0.0f) atomicAdd(&a.dtf[i], s_dtf[i]);
 }
 
-template <int C, int VS, int MODE, bool POW2, bool H>
+template <int C, int VS, int MODE, bool POW2, bool H, bool XF = false>
 static void launch_one(const RenderArgs& a, int blocks, int threads, cudaStream_t st) {
     const size_t smem = (size_t)C * 512 * sizeof(float4) + (H ? (size_t)C * 256 * sizeof(HalfEntry) : 0);
-    cudaFuncSetAttribute(render_kernel<C, VS, MODE, POW2, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    render_kernel<C, VS, MODE, POW2, H><<<blocks, threads, smem, st>>>(a);
+    cudaFuncSetAttribute(render_kernel<C, VS, MODE, POW2, H, XF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    render_kernel<C, VS, MODE, POW2, H, XF><<<blocks, threads, smem, st>>>(a);
 }
 
 template <int C, int VS>
 static cudaError_t launch_fwd_c(const RenderArgs& a, int mode, int fp16, int blocks, int threads, cudaStream_t st) {
     const bool p2 = a.g.pow2 != 0;
+    if (a.has_xf && (mode == 0 || mode == 1)) { // per-channel transforms: FP32 interpolation
+        if (mode == 0) {
+            if (p2) launch_one<C, VS, 0, true, false, true>(a, blocks, threads, st);
+            else launch_one<C, VS, 0, false, false, true>(a, blocks, threads, st);
+        } else {
+            if (p2) launch_one<C, VS, 1, true, false, true>(a, blocks, threads, st);
+            else launch_one<C, VS, 1, false, false, true>(a, blocks, threads, st);
+        }
+        return cudaGetLastError();
+    }
     if (mode == 0 && fp16) {
         if (p2) launch_one<C, VS, 0, true, true>(a, blocks, threads, st);
         else launch_one<C, VS, 0, false, true>(a, blocks, threads, st);
@@ -829,15 +1007,21 @@ cudaError_t launch_render(const RenderArgs& a, int mode, int fp16, int blocks, i
     }
 }
 
+template <int C, int VS, bool POW2, bool XF>
+static void launch_bwd_one(const RenderArgs& a, int blocks, int threads, cudaStream_t st) {
+    const size_t smem = (size_t)C * 512 * sizeof(float4) + (size_t)C * 1024 * sizeof(float);
+    cudaFuncSetAttribute(render_backward_kernel<C, VS, POW2, XF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    render_backward_kernel<C, VS, POW2, XF><<<blocks, threads, smem, st>>>(a);
+}
+
 template <int C, int VS>
 static cudaError_t launch_bwd_c(const RenderArgs& a, int blocks, int threads, cudaStream_t st) {
-    const size_t smem = (size_t)C * 512 * sizeof(float4) + (size_t)C * 1024 * sizeof(float);
     if (a.g.pow2) {
-        cudaFuncSetAttribute(render_backward_kernel<C, VS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        render_backward_kernel<C, VS, true><<<blocks, threads, smem, st>>>(a);
+        if (a.has_xf) launch_bwd_one<C, VS, true, true>(a, blocks, threads, st);
+        else launch_bwd_one<C, VS, true, false>(a, blocks, threads, st);
     } else {
-        cudaFuncSetAttribute(render_backward_kernel<C, VS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        render_backward_kernel<C, VS, false><<<blocks, threads, smem, st>>>(a);
+        if (a.has_xf) launch_bwd_one<C, VS, false, true>(a, blocks, threads, st);
+        else launch_bwd_one<C, VS, false, false>(a, blocks, threads, st);
     }
     return cudaGetLastError();
 }

@@ -61,6 +61,7 @@ def lib():
         L.vr_insert_slice.argtypes = [vp, ctypes.c_int64, vp, ctypes.c_int, vp]
         L.vr_set_transfer_functions.argtypes = [vp, vp, vp, vp]
         L.vr_set_clip_planes.argtypes = [vp, ctypes.c_int, vp]
+        L.vr_set_channel_transforms.argtypes = [vp, vp]
         L.vr_render.argtypes = [vp, ctypes.POINTER(Camera), ctypes.c_int, ctypes.POINTER(vp), ctypes.c_int, vp]
         L.vr_render_backward.argtypes = [vp, ctypes.POINTER(Camera), ctypes.c_int, ctypes.POINTER(vp), vp, vp, vp]
         L.vr_read_level.argtypes = [vp, ctypes.c_int, vp, vp]
@@ -80,7 +81,7 @@ def lib():
         L.vr_plan_samples.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
         L.vr_plan_destroy.argtypes = [vp]
         for f in ("vr_create", "vr_destroy", "vr_insert_block", "vr_insert_slice", "vr_set_transfer_functions",
-                  "vr_set_clip_planes", "vr_render", "vr_render_backward", "vr_read_level", "vr_read_voxels", "vr_read_node", "vr_render_footprint",
+                  "vr_set_clip_planes", "vr_set_channel_transforms", "vr_render", "vr_render_backward", "vr_read_level", "vr_read_voxels", "vr_read_node", "vr_render_footprint",
                   "vr_stats", "vr_set_tile_shape", "vr_set_launch_shape", "vr_plan_create", "vr_plan_launch",
                   "vr_plan_samples", "vr_plan_destroy"):
             getattr(L, f).restype = ctypes.c_int
@@ -207,6 +208,14 @@ class Renderer:
     def set_clip_planes(self, planes):
         p = np.ascontiguousarray(np.asarray(planes, dtype=np.float32).reshape(-1, 4))
         self._check(lib().vr_set_clip_planes(self._ctx, p.shape[0], p.ctypes.data if p.shape[0] else None))
+
+    def set_channel_transforms(self, xf):
+        """xf: [C][3][4] per-channel affine sample transforms, or None for identity."""
+        if xf is None:
+            self._check(lib().vr_set_channel_transforms(self._ctx, None))
+            return
+        m = np.ascontiguousarray(np.asarray(xf, dtype=np.float32).reshape(self.C, 3, 4))
+        self._check(lib().vr_set_channel_transforms(self._ctx, m.ctypes.data))
 
     def set_tile_shape(self, tw, th):
         self._check(lib().vr_set_tile_shape(self._ctx, tw, th))

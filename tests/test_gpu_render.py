@@ -313,3 +313,74 @@ def test_graph_plan_matches_render_and_sees_updates(tiny, tmp_path, monkeypatch)
     p16.launch()
     torch.cuda.synchronize()
     p16.close()
+
+
+def _random_xf(C, seed, shift=2.5, scale=0.03, rot=0.04, centre=(32.0, 32.0, 32.0)):
+    # small per-channel affine transforms about the volume centre: translation, scaling, rotation
+    rng = np.random.default_rng(seed)
+    out = np.zeros((C, 3, 4), np.float32)
+    c = np.asarray(centre, np.float64)
+    for ch in range(C):
+        ang = rng.uniform(-rot, rot, size=3)
+        cx, cy, cz = np.cos(ang)
+        sx, sy, sz = np.sin(ang)
+        Rx = np.array([[1, 0, 0], [0, cx, -sx], [0, sx, cx]])
+        Ry = np.array([[cy, 0, sy], [0, 1, 0], [-sy, 0, cy]])
+        Rz = np.array([[cz, -sz, 0], [sz, cz, 0], [0, 0, 1]])
+        A = Rz @ Ry @ Rx @ np.diag(1.0 + rng.uniform(-scale, scale, size=3))
+        t = c - A @ c + rng.uniform(-shift, shift, size=3)
+        out[ch, :, :3] = A
+        out[ch, :, 3] = t
+    return out
+
+
+@pytest.mark.parametrize("tau,M", [(0, 16), (2000, 16), (600, 6)])
+def test_channel_transforms_against_oracle(tiny, tau, M):
+    w, vol, _ = tiny
+    ov = oracle_dense(vol, M, tau=tau)
+    r = _build(vol, M, tau=tau)
+    xf = _random_xf(3, seed=tau + M)
+    r.set_channel_transforms(xf)
+    tf, sc = w.tf(), [1.0, 1.0, 1.0]
+    tf[..., 3] *= 3.0
+    cam = dict(w.cameras[0])
+    cam["lod_error_px"] = 0.6
+    import torch
+
+    r.set_transfer_functions(torch.from_numpy(tf), torch.tensor(sc))
+    img = r.render([cam])[0].cpu().numpy()
+    nc, cand, _ = O.render(ov, cam, tf, sc, None, 0, 0, xf=xf)
+    err = admissible_error(img.reshape(-1, 4), nc, cand)
+    assert err.max() <= RGBA_TOL, err.max()
+    # MIP with transforms
+    mip = r.render([cam], mode=1)[0].cpu().numpy()
+    nc, cand, _ = O.render(ov, cam, tf, sc, None, 1, 0, xf=xf)
+    assert admissible_error(mip.reshape(-1, 4), nc, cand).max() <= RGBA_TOL
+    # back to identity: the plain path again
+    r.set_channel_transforms(None)
+    plain = r.render([cam])[0].cpu().numpy()
+    nc, cand, _ = O.render(ov, cam, tf, sc, None, 0)
+    assert admissible_error(plain.reshape(-1, 4), nc, cand).max() <= RGBA_TOL
+
+
+def test_channel_transforms_adjoint():
+    import torch
+    import paper_1407_2074_b300 as vr
+
+    w = S.tiny()
+    vol = w.spec().volume()
+    ov = oracle_dense(vol, 16)
+    r = _build(vol, 16)
+    xf = _random_xf(3, seed=5)
+    r.set_channel_transforms(xf)
+    cam = dict(w.cameras[0])
+    cam["width"] = cam["height"] = 40
+    cam["ert_alpha"] = 2.0
+    tf, sc = w.tf(), np.array([1.0, 0.9, 1.2], np.float32)
+    r.set_transfer_functions(torch.from_numpy(tf), torch.from_numpy(sc))
+    dl = np.random.default_rng(3).normal(size=(40, 40, 4)).astype(np.float32)
+    dtf, dsc = r.render_backward([cam], [torch.from_numpy(dl).cuda()])
+    px, py = O.image_pixels(40, 40)
+    rtf, rsc = O.render_grad(ov, cam, tf, sc, (px, py), dl.reshape(-1, 4).astype(np.float64), xf=xf)
+    assert np.linalg.norm(dtf.cpu().numpy() - rtf) <= 1e-3 * np.linalg.norm(rtf)
+    assert np.linalg.norm(dsc.cpu().numpy() - rsc) <= 1e-3 * np.linalg.norm(rsc)

@@ -271,3 +271,43 @@ def test_mip_is_the_maximum_then_one_lookup():
     rgba, _, _ = px1(v, cam1(eps=1e-3), tf, [1.0], mode=1)
     a32 = float(np.float32(0.05))
     assert abs(rgba[3] - a32) < 1e-9 and abs(rgba[0] - a32 * 7300 / 65535.0) < 1e-7
+
+
+def _identity_xf(C):
+    m = np.zeros((C, 3, 4), dtype=np.float32)
+    m[:, 0, 0] = m[:, 1, 1] = m[:, 2, 2] = 1.0
+    return m
+
+
+def test_channel_transform_identity_changes_nothing():
+    w = S.tiny()
+    vol = w.spec().volume()
+    v = dense(vol)
+    cam = dict(w.cameras[0])
+    cam["width"] = cam["height"] = 32
+    a = O.render(v, cam, w.tf(), [1, 1, 1], None, 0, 2)[1]
+    b = O.render(v, cam, w.tf(), [1, 1, 1], None, 0, 2, xf=_identity_xf(3))[1]
+    assert np.array_equal(a, b)
+
+
+def test_channel_translation_equals_shifted_data():
+    # Sec. "Correction of Chromatic Aberration": channel 1 sampled at p + (3, 0, 0) sees the same
+    # values as an unshifted render of data whose channel 1 is V'[x] = V[min(x + 3, X - 1)]
+    # at level 0 without pruning (zero margins keep the clamped edges equal).
+    w = S.tiny()
+    vol = w.spec().volume()
+    X = vol.shape[2]
+    vol[:, :, :8] = 0  # zero margins: clamp-to-edge then reads equal values on both sides
+    vol[:, :, X - 8:] = 0
+    shifted = vol.copy()
+    shifted[..., 1] = vol[:, :, np.minimum(np.arange(X) + 3, X - 1), 1]
+    cam = dict(w.cameras[0])
+    cam["width"] = cam["height"] = 40
+    cam["lod_error_px"] = 1e-3
+    xf = _identity_xf(3)
+    xf[1, 0, 3] = 3.0
+    a = O.render_image(dense(vol), cam, w.tf(), [1, 1, 1], xf=xf)[0]
+    b = O.render_image(dense(shifted), cam, w.tf(), [1, 1, 1])[0]
+    assert np.abs(a - b).max() < 1e-6
+    c = O.render_image(dense(vol), cam, w.tf(), [1, 1, 1])[0]
+    assert np.abs(a - c).max() > 1e-3  # the transform does something
