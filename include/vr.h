@@ -66,6 +66,12 @@ typedef struct {
     size_t pool_capacity_bytes; /* brick pool size; 0 = room for every brick of the full tree */
     int precision;              /* VR_FP32 or VR_FP16_INTERP: default precision of vr_render's DVR
                                    (FP16 sample interpolation and TF lookup, FP32 compositing) */
+    size_t cache_capacity_bytes; /* > 0: out-of-core rendering -- renders read bricks only from a
+                                    device render cache of this size, filled on request (Sec.
+                                    "GPU Data Structure", brick buffer + flag buffer); 0: renders
+                                    read the brick store directly */
+    int store_on_host;          /* 1: the brick store lives in mapped pinned host memory (the
+                                   construction kernels write it over the bus); 0: device memory */
 } vr_options;
 
 /* One view.  The camera looks from eye at target; up fixes the roll.  fov_y_deg is the vertical
@@ -179,6 +185,38 @@ vr_status vr_render_backward(vr_ctx* ctx, const vr_camera* cams, int n_cams, con
  * algorithmic bytes a frame must move.  The paper has no counterpart. */
 vr_status vr_render_footprint(vr_ctx* ctx, const vr_camera* cams, int n_cams, float* const* images,
                               uint32_t* const* voxel_marks, uint32_t* node_marks, void* cuda_stream);
+
+/* ---- out-of-core rendering (contexts created with cache_capacity_bytes > 0) ----
+ * vr_render then reads bricks only from the render cache.  A sample whose brick is missing
+ * requests it and uses the nearest resident brick of its parent or grandparent on the descent
+ * path, else the node's AVG, requesting those too (full-frame ray casting, Sec. "Full-Frame
+ * Ray-Casting").  Every sampled brick is flagged as used.  vr_cache_update then uploads requested
+ * bricks, coarser levels first: free slots first, then slots whose brick was not used in the last
+ * pass, then (full-frame) used bricks of finer levels than the request (Sec. "Brick Upload from
+ * RAM to GPU"); in refinement mode any slot may be replaced.  Inserting data drops the cached
+ * copies of every brick the insert changed (Sec. "Incremental Octree Updates on the GPU"). */
+typedef struct {
+    int64_t requested; /* distinct bricks requested by the passes since the last update */
+    int64_t uploaded, evicted, resident, capacity;
+} vr_cache_report;
+/* Uploads up to max_uploads requested bricks (synchronises the stream) and clears the flags. */
+vr_status vr_cache_update(vr_ctx* ctx, int max_uploads, int refinement, void* cuda_stream, vr_cache_report* out);
+/* Makes the bricks of the listed nodes resident (dense node numbering: levels 0..N in order,
+ * each level's node grid x fastest); nodes without a brick are skipped.  Synchronises. */
+vr_status vr_cache_load(vr_ctx* ctx, int64_t n, const int64_t* nodes, void* cuda_stream);
+/* Test hook: per node (dense numbering) residency and the used / requested flags of the passes
+ * since the last update (host arrays of vr_stats().nodes bytes).  Synchronises. */
+vr_status vr_cache_read(vr_ctx* ctx, uint8_t* resident, uint8_t* used, uint8_t* requested, void* cuda_stream);
+
+/* Refinement ray casting (Sec. "Refinement Ray-Casting") of one view into a device image: each
+ * pass resumes every unfinished ray from its saved sample and colour and runs it until it ends
+ * (pixel written) or reaches a brick that is not resident (request set, state saved).  The
+ * caller alternates vr_refine_pass and vr_cache_update(..., refinement = 1, ...) until *pending
+ * is 0; the image is then the full-quality render. */
+typedef struct vr_refine vr_refine;
+vr_status vr_refine_begin(vr_ctx* ctx, const vr_camera* cam, float* image, vr_refine** out);
+vr_status vr_refine_pass(vr_refine* r, void* cuda_stream, int64_t* pending, int64_t* samples);
+vr_status vr_refine_end(vr_refine* r);
 
 /* Test hook: level L of the volume as out[Z_L][Y_L][X_L][C] (host buffer), gathered from the
  * brick pool (never-touched bricks read as the background).  Synchronises the stream. */

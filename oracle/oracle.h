@@ -124,6 +124,17 @@ int or_render_grad_xf(or_volume* v, const or_camera* cam, const float* tf, const
                       int64_t n, const int32_t* px, const int32_t* py, const double* dl, double* dtf, double* dscale,
                       int threads);
 
+/* Full-frame rendering with a partial brick cache (Sec. "Full-Frame Ray-Casting"): resident[n]
+ * != 0 when node n's brick is in the render cache (dense numbering of or_node_index).  A sample
+ * whose node's brick is missing requests it and uses the nearest present brick of the parent or
+ * grandparent on its descent path, else the node's AVG; missing ancestors' bricks are requested
+ * too.  used/requested (per node, zeroed by the caller) receive the flags the render sets. */
+int or_render_cache(or_volume* v, const or_camera* cam, const float* tf, const float* scale, int mode, int64_t n,
+                    const int32_t* px, const int32_t* py, const uint8_t* resident, uint8_t* used, uint8_t* requested,
+                    or_pixel* out, int threads);
+int64_t or_node_count(const or_geom* g);
+int64_t or_node_index(const or_geom* g, int L, int64_t i, int64_t j, int64_t k);
+
 /* Gradient of sum_pixels sum_k dl[p][k] * I[p][k] with respect to tf and scale (FP64, natural
  * decisions).  dl: [n][4].  Outputs are overwritten. */
 int or_render_grad(or_volume* v, const or_camera* cam, const float* tf, const float* scale, int64_t n,

@@ -85,6 +85,15 @@ def lib():
         L.or_render_grad_xf.argtypes = [ctypes.c_void_p, ctypes.POINTER(Camera), ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+        L.or_render_cache.argtypes = [ctypes.c_void_p, ctypes.POINTER(Camera), ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_int]
+        L.or_node_count.restype = ctypes.c_int64
+        L.or_node_count.argtypes = [ctypes.POINTER(Geom)]
+        L.or_node_index.restype = ctypes.c_int64
+        L.or_node_index.argtypes = [ctypes.POINTER(Geom), ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
+                                    ctypes.c_int64]
         L.or_ray.argtypes = [ctypes.POINTER(Geom), ctypes.POINTER(Camera), ctypes.c_int, ctypes.c_int,
                              ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
                              ctypes.POINTER(ctypes.c_float)]
@@ -290,3 +299,44 @@ def tf_eval(tf_channel: np.ndarray, s: float, I: float) -> np.ndarray:
     out = (ctypes.c_double * 4)()
     lib().or_tf_eval(t.ctypes.data, float(s), float(I), out)
     return np.array(out[:])
+
+
+def node_count(vol_or_geom) -> int:
+    g = vol_or_geom.geom if isinstance(vol_or_geom, Volume) else vol_or_geom
+    return int(lib().or_node_count(ctypes.byref(g)))
+
+
+def node_index(vol_or_geom, L, i, j, k) -> int:
+    g = vol_or_geom.geom if isinstance(vol_or_geom, Volume) else vol_or_geom
+    return int(lib().or_node_index(ctypes.byref(g), L, i, j, k))
+
+
+def render_cache(vol: Volume, cam: dict, tf, scale, resident, pixels=None, mode=0, threads=0):
+    """Full-frame render with a partial brick cache.  resident: uint8 per node (node_index order).
+    Returns (n_cand, cand, samples, used, requested)."""
+    if pixels is None:
+        px, py = image_pixels(cam["width"], cam["height"])
+    else:
+        px = np.ascontiguousarray(pixels[0], dtype=np.int32)
+        py = np.ascontiguousarray(pixels[1], dtype=np.int32)
+    n = px.shape[0]
+    tf = np.ascontiguousarray(tf, dtype=np.float32)
+    sc = np.ascontiguousarray(scale, dtype=np.float32)
+    res = np.ascontiguousarray(resident, dtype=np.uint8)
+    nn = node_count(vol)
+    assert res.shape == (nn,)
+    used = np.zeros(nn, np.uint8)
+    req = np.zeros(nn, np.uint8)
+    out = (Pixel * max(n, 1))()
+    cs = camera_struct(cam)
+    rc = lib().or_render_cache(vol.handle, ctypes.byref(cs), tf.ctypes.data, sc.ctypes.data, mode, n,
+                               px.ctypes.data, py.ctypes.data, res.ctypes.data, used.ctypes.data, req.ctypes.data,
+                               ctypes.addressof(out), threads)
+    if rc != 0:
+        raise ValueError("oracle render_cache: invalid arguments")
+    arr = np.ctypeslib.as_array(ctypes.cast(out, ctypes.POINTER(ctypes.c_uint8)),
+                                shape=(max(n, 1) * ctypes.sizeof(Pixel),))
+    dt = np.dtype([("n_cand", np.int32), ("pad", np.int32), ("rgba", np.float64, (MAXCAND, 4)),
+                   ("samples", np.int64)])
+    rec = arr.view(dt)[:n]
+    return rec["n_cand"].copy(), rec["rgba"].copy(), rec["samples"].copy(), used, req

@@ -133,11 +133,12 @@ int or_lod_thresholds(const or_geom* g, const or_camera* cam, float* tl) {
  * the current node has no children.  Child boxes follow from halving the parent box;
  * the child index along an axis is floor(p / size) clamped to the parent's two
  * children and to the real node grid. */
-static int descend(or_volume* v, const float p[3], int Lstar, or_node* nd) {
+static int descend_path(or_volume* v, const float p[3], int Lstar, or_node* nd, int64_t path[OR_MAXL][3]) {
     const or_geom* g = or_volume_geom(v);
     int lev = g->N;
     int64_t idx[3] = {0, 0, 0};
     or_node_info(v, lev, 0, 0, 0, nd);
+    if (path) path[lev][0] = path[lev][1] = path[lev][2] = 0;
     while (lev > Lstar && nd->has_children) {
         --lev;
         float size = (float)((int64_t)g->M << lev);
@@ -150,8 +151,26 @@ static int descend(or_volume* v, const float p[3], int Lstar, or_node* nd) {
             idx[a] = q;
         }
         or_node_info(v, lev, idx[0], idx[1], idx[2], nd);
+        if (path)
+            for (int a = 0; a < 3; ++a) path[lev][a] = idx[a];
     }
     return lev;
+}
+
+static int descend(or_volume* v, const float p[3], int Lstar, or_node* nd) { return descend_path(v, p, Lstar, nd, NULL); }
+
+int64_t or_node_count(const or_geom* g) {
+    int64_t n = 0;
+    for (int L = 0; L <= g->N; ++L) n += g->nb[L][0] * g->nb[L][1] * g->nb[L][2];
+    return n;
+}
+
+/* Dense node numbering used for residency and flag arrays: levels 0..N in order, each level's
+ * node grid x fastest. */
+int64_t or_node_index(const or_geom* g, int L, int64_t i, int64_t j, int64_t k) {
+    int64_t off = 0;
+    for (int l = 0; l < L; ++l) off += g->nb[l][0] * g->nb[l][1] * g->nb[l][2];
+    return off + (k * g->nb[L][1] + j) * g->nb[L][0] + i;
 }
 
 /* Trilinear interpolation of level L at p (level-0 units; voxel i centred at (i+0.5) 2^L). */
@@ -228,8 +247,15 @@ static void channel_point(const float* m, const float p[3], float q[3]) {
     for (int i = 0; i < 3; ++i) q[i] = ((m[4 * i] * p[0] + m[4 * i + 1] * p[1]) + m[4 * i + 2] * p[2]) + m[4 * i + 3];
 }
 
+/* Brick cache state for out-of-core rendering (NULL res = every brick present). */
+typedef struct {
+    const uint8_t* res; /* per node: its brick is in the render cache */
+    uint8_t* used;      /* per node: its brick was sampled (output) */
+    uint8_t* req;       /* per node: its brick was requested (output) */
+} cache_io;
+
 static void march(or_volume* v, const or_camera* cam, const cam_derived* cd, const float* tf, const float* scale,
-                  const float* xf, int mode, int px, int py, or_pixel* out, recbuf* rec) {
+                  const float* xf, int mode, int px, int py, or_pixel* out, recbuf* rec, const cache_io* cio) {
     const or_geom* g = or_volume_geom(v);
     int C = g->C;
     memset(out, 0, sizeof(*out));
@@ -255,7 +281,38 @@ static void march(or_volume* v, const or_camera* cam, const cam_derived* cd, con
         for (int L = 1; L <= g->N; ++L)
             if (tk >= cd->tl[L]) Lstar = L;
         or_node nd;
-        int lev = descend(v, p, Lstar, &nd);
+        int64_t path[OR_MAXL][3];
+        int lev = descend_path(v, p, Lstar, &nd, path);
+        /* Full-frame ray casting with a partial brick cache (Sec. "Full-Frame Ray-Casting"): a
+         * missing brick is requested; the brick of the parent or grandparent on the descent path,
+         * if present, stands in (nearest first), else the node's AVG; those missing are requested
+         * as well. */
+        int samp_lev = nd.has_brick ? lev : -1;
+        if (cio && cio->res && nd.has_brick) {
+            const or_geom* gg = or_volume_geom(v);
+            int64_t nid = or_node_index(gg, lev, path[lev][0], path[lev][1], path[lev][2]);
+            if (cio->res[nid]) {
+                cio->used[nid] = 1;
+            } else {
+                cio->req[nid] = 1;
+                samp_lev = -1;
+                for (int up = 1; up <= 2 && lev + up <= gg->N; ++up) {
+                    int L2 = lev + up;
+                    or_node n2;
+                    or_node_info(v, L2, path[L2][0], path[L2][1], path[L2][2], &n2);
+                    if (!n2.has_brick) continue;
+                    int64_t nid2 = or_node_index(gg, L2, path[L2][0], path[L2][1], path[L2][2]);
+                    if (cio->res[nid2]) {
+                        if (samp_lev < 0) {
+                            samp_lev = L2;
+                            cio->used[nid2] = 1;
+                        }
+                    } else {
+                        cio->req[nid2] = 1;
+                    }
+                }
+            }
+        }
         or_node ndc[OR_MAXC];
         int levc[OR_MAXC];
         float pc[OR_MAXC][3];
@@ -270,7 +327,7 @@ static void march(or_volume* v, const or_camera* cam, const cam_derived* cd, con
             if (xf)
                 I = ndc[c].has_brick ? trilinear(v, levc[c], pc[c], c) : (double)ndc[c].avg[c];
             else
-                I = nd.has_brick ? trilinear(v, lev, p, c) : (double)nd.avg[c];
+                I = samp_lev >= 0 ? trilinear(v, samp_lev, p, c) : (double)nd.avg[c];
             if (mode == 1) {
                 if (I > mip[c]) mip[c] = I;
                 continue;
@@ -362,6 +419,7 @@ typedef struct {
     const float* tf;
     const float* scale;
     const float* xf; /* NULL or [C][3][4] per-channel transforms */
+    cache_io cio;
     int mode;
     const int32_t* px;
     const int32_t* py;
@@ -371,7 +429,7 @@ typedef struct {
 static void render_range(void* p, int64_t b, int64_t e) {
     render_job* j = (render_job*)p;
     for (int64_t i = b; i < e; ++i)
-        march(j->v, j->cam, &j->cd, j->tf, j->scale, j->xf, j->mode, j->px[i], j->py[i], &j->out[i], NULL);
+        march(j->v, j->cam, &j->cd, j->tf, j->scale, j->xf, j->mode, j->px[i], j->py[i], &j->out[i], NULL, &j->cio);
 }
 
 static int cam_valid(const or_camera* cam) {
@@ -391,6 +449,9 @@ int or_render_xf(or_volume* v, const or_camera* cam, const float* tf, const floa
     j.tf = tf;
     j.scale = scale;
     j.xf = xf;
+    j.cio.res = NULL;
+    j.cio.used = NULL;
+    j.cio.req = NULL;
     j.mode = mode;
     j.px = px;
     j.py = py;
@@ -402,6 +463,30 @@ int or_render_xf(or_volume* v, const or_camera* cam, const float* tf, const floa
 int or_render(or_volume* v, const or_camera* cam, const float* tf, const float* scale, int mode, int64_t n,
               const int32_t* px, const int32_t* py, or_pixel* out, int threads) {
     return or_render_xf(v, cam, tf, scale, NULL, mode, n, px, py, out, threads);
+}
+
+int or_render_cache(or_volume* v, const or_camera* cam, const float* tf, const float* scale, int mode, int64_t n,
+                    const int32_t* px, const int32_t* py, const uint8_t* resident, uint8_t* used, uint8_t* requested,
+                    or_pixel* out, int threads) {
+    if (!v || !cam_valid(cam) || !tf || !scale || !px || !py || !out || !resident || !used || !requested ||
+        (mode != 0 && mode != 1))
+        return -1;
+    render_job j;
+    j.v = v;
+    j.cam = cam;
+    cam_setup(or_volume_geom(v), cam, &j.cd);
+    j.tf = tf;
+    j.scale = scale;
+    j.xf = NULL;
+    j.cio.res = resident;
+    j.cio.used = used;
+    j.cio.req = requested;
+    j.mode = mode;
+    j.px = px;
+    j.py = py;
+    j.out = out;
+    or_parallel_for(n, 16, threads, render_range, &j);
+    return 0;
 }
 
 /* ---- adjoint ---- */
@@ -463,7 +548,8 @@ static void* grad_worker(void* p) {
         if (i >= j->n) break;
         rb.n = 0;
         or_pixel px;
-        march(j->rj.v, j->rj.cam, &j->rj.cd, j->rj.tf, j->rj.scale, j->rj.xf, 0, j->rj.px[i], j->rj.py[i], &px, &rb);
+        march(j->rj.v, j->rj.cam, &j->rj.cd, j->rj.tf, j->rj.scale, j->rj.xf, 0, j->rj.px[i], j->rj.py[i], &px, &rb,
+              NULL);
         ray_grad(g, j->rj.tf, &rb, j->dl + 4 * i, dtf, dsc);
     }
     free(rb.r);

@@ -7,6 +7,7 @@
 // rounding must not depend on FMA contraction (they decide sample levels).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -51,6 +52,20 @@ struct vr_ctx {
     float clip_default[VR_MAX_CLIP][4] = {};
     int tile_w = 8, tile_h = 4;
     int threads = 256, ctas_per_sm = 8; // render launch shape (autotuned per workload)
+    // out-of-core render cache (cache_cap slots; 0 = renders read the store directly)
+    long long cache_cap = 0;
+    uint16_t* cache = nullptr;
+    int* d_cslot = nullptr;
+    unsigned char* d_used = nullptr;
+    unsigned char* d_req = nullptr;
+    std::vector<int> h_cslot;        // node -> cache slot
+    std::vector<long long> h_owner;  // cache slot -> node
+    std::vector<unsigned char> h_used, h_req;
+    std::vector<signed char> node_level;
+    int2* d_glist = nullptr;
+    int2* h_glist = nullptr;
+    int glist_cap = 0;
+    bool store_host = false;
     int has_xf = 0;                     // per-channel sample transforms (identity when 0)
     float xf[VR_MAX_CHANNELS][12] = {};
     bool failed = false;
@@ -102,7 +117,17 @@ static void destroy_all(vr_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->dev);
     cudaDeviceSynchronize();
-    dfree(c, c->pool);
+    if (c->store_host) {
+        if (c->pool) cudaFreeHost(c->pool);
+    } else {
+        dfree(c, c->pool);
+    }
+    dfree(c, c->cache);
+    dfree(c, c->d_cslot);
+    dfree(c, c->d_used);
+    dfree(c, c->d_req);
+    dfree(c, c->d_glist);
+    if (c->h_glist) cudaFreeHost(c->h_glist);
     dfree(c, c->rn);
     dfree(c, c->ns);
     dfree(c, c->ps);
@@ -191,7 +216,48 @@ vr_status vr_create(const int64_t dims[3], int channels, int brick_size, const v
     }
     g.n_slots_cap = cap;
     c->h_slot.assign((size_t)nodes, -1);
-    c->pool = (uint16_t*)dalloc(c, (size_t)(cap * slot_bytes));
+    if (c->opt.store_on_host) {
+        c->store_host = true;
+        void* hp = nullptr;
+        if (cudaHostAlloc(&hp, (size_t)(cap * slot_bytes), cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+            cudaGetLastError();
+            hp = nullptr;
+        }
+        void* dp = nullptr;
+        if (hp && cudaHostGetDevicePointer(&dp, hp, 0) != cudaSuccess) {
+            cudaGetLastError();
+            dp = nullptr;
+        }
+        if (hp && dp != hp) { // unified addressing is expected on this platform
+            cudaFreeHost(hp);
+            hp = nullptr;
+        }
+        c->pool = (uint16_t*)hp;
+    } else {
+        c->pool = (uint16_t*)dalloc(c, (size_t)(cap * slot_bytes));
+    }
+    if (c->opt.cache_capacity_bytes > 0) {
+        c->cache_cap = std::min<long long>(full_slots, (long long)(c->opt.cache_capacity_bytes / slot_bytes));
+        if (c->cache_cap < 1) c->cache_cap = 1;
+        c->cache = (uint16_t*)dalloc(c, (size_t)(c->cache_cap * slot_bytes));
+        c->d_cslot = (int*)dalloc(c, sizeof(int) * (size_t)nodes);
+        c->d_used = (unsigned char*)dalloc(c, (size_t)nodes);
+        c->d_req = (unsigned char*)dalloc(c, (size_t)nodes);
+        if (!c->cache || !c->d_cslot || !c->d_used || !c->d_req) {
+            destroy_all(c);
+            return fail(nullptr, VR_ERR_OUT_OF_MEMORY, "render cache allocation failed");
+        }
+        cudaMemset(c->d_cslot, 0xff, sizeof(int) * (size_t)nodes);
+        cudaMemset(c->d_used, 0, (size_t)nodes);
+        cudaMemset(c->d_req, 0, (size_t)nodes);
+        c->h_cslot.assign((size_t)nodes, -1);
+        c->h_owner.assign((size_t)c->cache_cap, -1);
+        c->h_used.assign((size_t)nodes, 0);
+        c->h_req.assign((size_t)nodes, 0);
+        c->node_level.assign((size_t)nodes, 0);
+        for (int L = 0; L <= N; ++L)
+            for (long long n = g.noff[L]; n < g.noff[L + 1]; ++n) c->node_level[(size_t)n] = (signed char)L;
+    }
     c->rn = (RNode*)dalloc(c, sizeof(RNode) * (size_t)nodes);
     c->ns = (NStat*)dalloc(c, sizeof(NStat) * (size_t)nodes);
     c->ps = (PStat*)dalloc(c, sizeof(PStat) * (size_t)(cap * brick_size * channels));
@@ -310,6 +376,31 @@ vr_status vr_insert_block(vr_ctx* c, const int64_t origin[3], const int64_t exte
     const long long org[3] = {origin[0], origin[1], origin[2]}, ext[3] = {extent[0], extent[1], extent[2]};
     for (int L = 0; L <= g.N; ++L)
         CK(c, launch_level_update(g, L, lo[L], hi[L], src, org, ext, c->pool, c->rn, c->ns, c->ps, c->err, st));
+    if (c->cache_cap > 0) {
+        // cached copies of every brick this insert rewrote (interior or border) are stale now
+        bool dropped = false;
+        for (int L = 0; L <= g.N; ++L) {
+            long long b0[3], b1[3];
+            for (int a = 0; a < 3; ++a) {
+                b0[a] = std::max<long long>(0, (lo[L][a] + g.M - 1) / g.M - 1);
+                b1[a] = std::min<long long>(g.nb[L][a] - 1, (hi[L][a] + 1) / g.M);
+            }
+            for (long long k = b0[2]; k <= b1[2]; ++k)
+                for (long long j = b0[1]; j <= b1[1]; ++j)
+                    for (long long i = b0[0]; i <= b1[0]; ++i) {
+                        const size_t nid = (size_t)(g.noff[L] + (k * g.nb[L][1] + j) * g.nb[L][0] + i);
+                        const int cs = c->h_cslot[nid];
+                        if (cs >= 0) {
+                            c->h_owner[(size_t)cs] = -1;
+                            c->h_cslot[nid] = -1;
+                            dropped = true;
+                        }
+                    }
+        }
+        if (dropped)
+            CK(c, cudaMemcpyAsync(c->d_cslot, c->h_cslot.data(), sizeof(int) * c->h_cslot.size(), cudaMemcpyHostToDevice,
+                                  st));
+    }
     return VR_OK;
 }
 
@@ -466,6 +557,13 @@ static RenderArgs make_args(vr_ctx* c, int n, long long tiles) {
     a.err = c->err;
     a.has_xf = c->has_xf;
     std::memcpy(a.xf, c->xf, sizeof a.xf);
+    if (c->cache_cap > 0) {
+        a.cache.cslot = c->d_cslot;
+        a.cache.used = c->d_used;
+        a.cache.req = c->d_req;
+        a.cache.cache = c->cache;
+        a.cache.refine = 0;
+    }
     return a;
 }
 
@@ -536,6 +634,235 @@ vr_status vr_render_footprint(vr_ctx* c, const vr_camera* cams, int n, float* co
     for (int L = 0; L <= c->g.N; ++L) a.vmark[L] = voxel_marks[L];
     a.nmark = node_marks;
     CK(c, launch_render(a, 2, 0, grid_for(c, tiles, 256, 8), 256, st));
+    return VR_OK;
+}
+
+static vr_status cache_upload(vr_ctx* c, const std::vector<std::pair<long long, int>>& moves, cudaStream_t st) {
+    // moves: (node, cache slot); copies store slot -> cache slot for each, then publishes the table
+    const int n = (int)moves.size();
+    if (n > 0) {
+        if (n > c->glist_cap) {
+            CK(c, cudaStreamSynchronize(st));
+            dfree(c, c->d_glist);
+            if (c->h_glist) cudaFreeHost(c->h_glist);
+            c->h_glist = nullptr;
+            const int cap = std::max(n, 1024);
+            c->d_glist = (int2*)dalloc(c, sizeof(int2) * (size_t)cap);
+            if (!c->d_glist || cudaMallocHost(&c->h_glist, sizeof(int2) * (size_t)cap) != cudaSuccess) {
+                c->glist_cap = 0;
+                return fail(c, VR_ERR_OUT_OF_MEMORY, "cache upload list allocation failed");
+            }
+            c->glist_cap = cap;
+        }
+        CK(c, cudaStreamSynchronize(st));
+        for (int i = 0; i < n; ++i) c->h_glist[i] = make_int2(c->h_slot[(size_t)moves[i].first], moves[i].second);
+        CK(c, cudaMemcpyAsync(c->d_glist, c->h_glist, sizeof(int2) * (size_t)n, cudaMemcpyHostToDevice, st));
+        CK(c, launch_cache_gather(c->pool, c->cache, c->d_glist, n, c->g.slot_elems, st));
+    }
+    CK(c, cudaMemcpyAsync(c->d_cslot, c->h_cslot.data(), sizeof(int) * c->h_cslot.size(), cudaMemcpyHostToDevice, st));
+    CK(c, cudaStreamSynchronize(st));
+    return VR_OK;
+}
+
+vr_status vr_cache_update(vr_ctx* c, int max_uploads, int refinement, void* stream, vr_cache_report* out) {
+    vr_status s = check_ctx(c);
+    if (s != VR_OK) return s;
+    if (c->cache_cap <= 0) return fail(c, VR_ERR_INVALID_ARG, "context has no render cache");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t nn = c->h_cslot.size();
+    CK(c, cudaMemcpyAsync(c->h_used.data(), c->d_used, nn, cudaMemcpyDeviceToHost, st));
+    CK(c, cudaMemcpyAsync(c->h_req.data(), c->d_req, nn, cudaMemcpyDeviceToHost, st));
+    CK(c, cudaStreamSynchronize(st));
+    std::vector<long long> reqs;
+    for (size_t n = 0; n < nn; ++n)
+        if (c->h_req[n] && c->h_cslot[n] < 0 && c->h_slot[n] >= 0) reqs.push_back((long long)n);
+    // coarser levels first (they cover more of the volume), then node order
+    std::stable_sort(reqs.begin(), reqs.end(),
+                     [&](long long a, long long b) { return c->node_level[(size_t)a] > c->node_level[(size_t)b]; });
+    // victims in order of preference: free, unused in the last pass, then (by request) finer used
+    std::vector<int> free_slots, unused, used_by_level[MAXL];
+    for (long long sl = c->cache_cap - 1; sl >= 0; --sl) {
+        const long long owner = c->h_owner[(size_t)sl];
+        if (owner < 0)
+            free_slots.push_back((int)sl);
+        else if (refinement || !c->h_used[(size_t)owner])
+            unused.push_back((int)sl);
+        else
+            used_by_level[c->node_level[(size_t)owner]].push_back((int)sl);
+    }
+    std::vector<std::pair<long long, int>> moves;
+    long long evicted = 0;
+    for (long long node : reqs) {
+        if ((int)moves.size() >= max_uploads) break;
+        int slot = -1;
+        if (!free_slots.empty()) {
+            slot = free_slots.back();
+            free_slots.pop_back();
+        } else if (!unused.empty()) {
+            slot = unused.back();
+            unused.pop_back();
+        } else {
+            const int lr = c->node_level[(size_t)node];
+            for (int L = 0; L < lr && slot < 0; ++L)
+                if (!used_by_level[L].empty()) {
+                    slot = used_by_level[L].back();
+                    used_by_level[L].pop_back();
+                }
+        }
+        if (slot < 0) break;
+        const long long prev = c->h_owner[(size_t)slot];
+        if (prev >= 0) {
+            c->h_cslot[(size_t)prev] = -1;
+            ++evicted;
+        }
+        c->h_owner[(size_t)slot] = node;
+        c->h_cslot[(size_t)node] = slot;
+        moves.push_back({node, slot});
+    }
+    s = cache_upload(c, moves, st);
+    if (s != VR_OK) return s;
+    CK(c, cudaMemsetAsync(c->d_used, 0, nn, st));
+    CK(c, cudaMemsetAsync(c->d_req, 0, nn, st));
+    if (out) {
+        out->requested = (int64_t)reqs.size();
+        out->uploaded = (int64_t)moves.size();
+        out->evicted = evicted;
+        long long res = 0;
+        for (long long o : c->h_owner) res += o >= 0;
+        out->resident = res;
+        out->capacity = c->cache_cap;
+    }
+    return VR_OK;
+}
+
+vr_status vr_cache_load(vr_ctx* c, int64_t n, const int64_t* nodes, void* stream) {
+    vr_status s = check_ctx(c);
+    if (s != VR_OK) return s;
+    if (c->cache_cap <= 0) return fail(c, VR_ERR_INVALID_ARG, "context has no render cache");
+    if (n < 0 || (n > 0 && !nodes)) return fail(c, VR_ERR_INVALID_ARG, "bad node list");
+    const long long nn = (long long)c->h_cslot.size();
+    std::vector<unsigned char> keep((size_t)nn, 0);
+    for (int64_t i = 0; i < n; ++i) {
+        if (nodes[i] < 0 || nodes[i] >= nn) return fail(c, VR_ERR_INVALID_ARG, "node outside the tree");
+        keep[(size_t)nodes[i]] = 1;
+    }
+    std::vector<int> victims;
+    for (long long sl = c->cache_cap - 1; sl >= 0; --sl)
+        if (c->h_owner[(size_t)sl] < 0) victims.push_back((int)sl);
+    for (long long sl = c->cache_cap - 1; sl >= 0; --sl) {
+        const long long o = c->h_owner[(size_t)sl];
+        if (o >= 0 && !keep[(size_t)o]) victims.push_back((int)sl);
+    }
+    std::reverse(victims.begin(), victims.end()); // free slots are taken first (from the back)
+    std::vector<std::pair<long long, int>> moves;
+    for (int64_t i = 0; i < n; ++i) {
+        const long long node = nodes[i];
+        if (c->h_slot[(size_t)node] < 0 || c->h_cslot[(size_t)node] >= 0) continue;
+        if (victims.empty()) return fail(c, VR_ERR_OUT_OF_MEMORY, "render cache smaller than the node list");
+        const int slot = victims.back();
+        victims.pop_back();
+        const long long prev = c->h_owner[(size_t)slot];
+        if (prev >= 0) c->h_cslot[(size_t)prev] = -1;
+        c->h_owner[(size_t)slot] = node;
+        c->h_cslot[(size_t)node] = slot;
+        moves.push_back({node, slot});
+    }
+    return cache_upload(c, moves, (cudaStream_t)stream);
+}
+
+vr_status vr_cache_read(vr_ctx* c, uint8_t* resident, uint8_t* used, uint8_t* requested, void* stream) {
+    vr_status s = check_ctx(c);
+    if (s != VR_OK) return s;
+    if (c->cache_cap <= 0) return fail(c, VR_ERR_INVALID_ARG, "context has no render cache");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t nn = c->h_cslot.size();
+    if (used) CK(c, cudaMemcpyAsync(used, c->d_used, nn, cudaMemcpyDeviceToHost, st));
+    if (requested) CK(c, cudaMemcpyAsync(requested, c->d_req, nn, cudaMemcpyDeviceToHost, st));
+    CK(c, cudaStreamSynchronize(st));
+    if (resident)
+        for (size_t n = 0; n < nn; ++n) resident[n] = c->h_cslot[n] >= 0;
+    return VR_OK;
+}
+
+struct vr_refine {
+    vr_ctx* c = nullptr;
+    CamParam* d_cam = nullptr;
+    RefineState* state = nullptr;
+    unsigned int* pending = nullptr;
+    long long tiles = 0;
+};
+
+vr_status vr_refine_begin(vr_ctx* c, const vr_camera* cam, float* image, vr_refine** out) {
+    vr_status s = check_ctx(c);
+    if (s != VR_OK) return s;
+    if (!cam || !image || !out) return fail(c, VR_ERR_INVALID_ARG, "NULL argument");
+    if (c->cache_cap <= 0) return fail(c, VR_ERR_INVALID_ARG, "refinement needs a render cache");
+    if (!c->tf_set) return fail(c, VR_ERR_INVALID_ARG, "transfer functions not set");
+    CamParam cp;
+    std::memset(&cp, 0, sizeof cp);
+    if (!derive_camera(c, *cam, cp)) return fail(c, VR_ERR_INVALID_ARG, "invalid camera");
+    cp.img = image;
+    cp.tiles_x = (int)ceil_div(cp.W, c->tile_w);
+    cp.tile_begin = 0;
+    vr_refine* r = new vr_refine();
+    r->c = c;
+    r->tiles = (long long)cp.tiles_x * ceil_div(cp.H, c->tile_h);
+    r->d_cam = (CamParam*)dalloc(c, sizeof(CamParam));
+    r->state = (RefineState*)dalloc(c, sizeof(RefineState) * (size_t)cp.W * (size_t)cp.H);
+    r->pending = (unsigned int*)dalloc(c, sizeof(unsigned int) * 4);
+    if (!r->d_cam || !r->state || !r->pending) {
+        dfree(c, r->d_cam);
+        dfree(c, r->state);
+        dfree(c, r->pending);
+        delete r;
+        return fail(c, VR_ERR_OUT_OF_MEMORY, "refinement state allocation failed");
+    }
+    cudaError_t e = cudaMemcpy(r->d_cam, &cp, sizeof cp, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(r->state, 0, sizeof(RefineState) * (size_t)cp.W * (size_t)cp.H);
+    if (e != cudaSuccess) {
+        dfree(c, r->d_cam);
+        dfree(c, r->state);
+        dfree(c, r->pending);
+        delete r;
+        return cuda_fail(c, e, "refine_begin");
+    }
+    *out = r;
+    return VR_OK;
+}
+
+vr_status vr_refine_pass(vr_refine* r, void* stream, int64_t* pending, int64_t* samples) {
+    if (!r) return VR_ERR_INVALID_ARG;
+    vr_ctx* c = r->c;
+    vr_status s = check_ctx(c);
+    if (s != VR_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    RenderArgs a = make_args(c, 1, r->tiles);
+    a.cams = r->d_cam;
+    a.cache.refine = 1;
+    a.refine_state = r->state;
+    a.pending = r->pending;
+    CK(c, cudaMemsetAsync(r->pending, 0, sizeof(unsigned int), st));
+    CK(c, cudaMemsetAsync(c->counter, 0, sizeof(unsigned long long), st));
+    CK(c, cudaMemsetAsync(c->stats, 0, 2 * sizeof(unsigned long long), st));
+    CK(c, launch_render(a, 3, 0, grid_for(c, r->tiles, 256, 8), 256, st));
+    unsigned int hp = 0;
+    unsigned long long hs[2] = {0, 0};
+    CK(c, cudaMemcpyAsync(&hp, r->pending, sizeof hp, cudaMemcpyDeviceToHost, st));
+    CK(c, cudaMemcpyAsync(hs, c->stats, sizeof hs, cudaMemcpyDeviceToHost, st));
+    CK(c, cudaStreamSynchronize(st));
+    if (pending) *pending = hp;
+    if (samples) *samples = (int64_t)hs[0];
+    return VR_OK;
+}
+
+vr_status vr_refine_end(vr_refine* r) {
+    if (!r) return VR_ERR_INVALID_ARG;
+    cudaSetDevice(r->c->dev);
+    cudaDeviceSynchronize();
+    dfree(r->c, r->d_cam);
+    dfree(r->c, r->state);
+    dfree(r->c, r->pending);
+    delete r;
     return VR_OK;
 }
 

@@ -74,6 +74,22 @@ struct CamParam {
     long long tile_begin;
 };
 
+// Out-of-core render cache (Sec. "GPU Data Structure": brick buffer + flag buffer).
+struct CacheArgs {
+    int* cslot;             // per node: its brick's slot in the render cache, -1 = not resident
+    unsigned char* used;    // per node: brick sampled in this pass
+    unsigned char* req;     // per node: brick requested in this pass
+    const uint16_t* cache;  // render cache slots (same slot layout as the store)
+    int refine;             // refinement pass: suspend a ray at its first missing brick
+};
+
+struct RefineState { // one pixel of a refinement session
+    float C[3], A;
+    int k;      // next sample index
+    int status; // 0 = not started, 1 = suspended, 2 = done
+    int pad[2];
+};
+
 struct RenderArgs {
     Geo g;
     const uint16_t* pool;
@@ -86,6 +102,9 @@ struct RenderArgs {
     int tile_w, tile_h;
     unsigned int* counter;              // tile queue head (reset before each launch)
     unsigned long long* stats;          // [0] samples, [1] rays
+    CacheArgs cache;                    // cache.cslot == nullptr: the store is read directly
+    RefineState* refine_state;          // MODE 3: per pixel of the single camera
+    unsigned int* pending;              // MODE 3: rays still suspended after the pass
     int has_xf;                         // per-channel sample transforms active
     float xf[MAXC][12];                 // channel c samples at xf[c] (3x4, row-major) applied to p
     unsigned int* vmark[MAXL];          // footprint mode: one bit per level-L voxel
@@ -109,5 +128,7 @@ cudaError_t launch_read_voxels(const Geo& g, int L, const uint16_t* pool, const 
 cudaError_t launch_prepare_tf(int C, const float* tf, const float* scale, float4* tf2, float* scl, cudaStream_t st);
 cudaError_t launch_render(const RenderArgs& a, int mode, int fp16, int blocks, int threads, cudaStream_t st);
 cudaError_t launch_render_backward(const RenderArgs& a, int blocks, int threads, cudaStream_t st);
+cudaError_t launch_cache_gather(const uint16_t* store, uint16_t* cache, const int2* list, int n, long long slot_elems,
+                                cudaStream_t st);
 
 } // namespace vrk

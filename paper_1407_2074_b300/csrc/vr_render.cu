@@ -117,10 +117,16 @@ struct TFLookup {
 // Marches one ray; calls f.sample(I[C], ell) for every sample until it returns true.
 // H = false: I in raw uint16 units, FP32 interpolation.  H = true: the eight corners are cached as
 // normalised FP16 channel pairs (value / 65535), interpolated in half2; I is that FP16 result.
+// With a render cache (ca != nullptr) a node's brick is read from the cache when resident;
+// otherwise it is requested and, in a full-frame pass, the brick of the parent or grandparent on
+// the descent path stands in when resident (nearest first; missing ones are requested too), else
+// the node's AVG (Sec. "Full-Frame Ray-Casting").  In a refinement pass (ca->refine) the ray
+// stops at its first missing brick instead and march returns -(k + 1), k the sample to resume
+// from (Sec. "Refinement Ray-Casting").  k0 is the first sample index.
 template <int C, int VS, bool POW2, bool H, class F>
 __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restrict__ pool,
                                            const RNode* __restrict__ rn, const CamParam& cp, const float d[3], float t0,
-                                           float t1, F& f) {
+                                           float t1, F& f, const CacheArgs* ca = nullptr, int k0 = 0) {
     const float dt = cp.dt;
     const int N = g.N, M = g.M, S = g.S;
     int Lstar = 0;
@@ -142,8 +148,8 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
     float cv[8][C];
     constexpr int CP = (C + 1) / 2;
     __half2 hv[8][CP];
-    int k = 0;
-    float kf = 0.0f; // == (float)k, exact below 2^24
+    int k = k0;
+    float kf = (float)k0; // == (float)k, exact below 2^24
     for (;; ++k, kf += 1.0f) {
         const float tk = __fadd_rn(t0, __fmul_rn(kf, dt));
         if (!(tk < t1) || k >= MAX_SAMPLES) break;
@@ -214,6 +220,36 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
 #pragma unroll
             for (int c = 0; c < C; ++c) avg[c] = (float)nd.avg[c];
             cell = -1;
+            if (ca && brick) {
+                const long long nid = g.noff[lev] + ((long long)idx[2] * g.nb[lev][1] + idx[1]) * g.nb[lev][0] + idx[0];
+                const int cs = ca->cslot[nid];
+                if (cs >= 0) {
+                    ca->used[nid] = 1;
+                    sbase = ca->cache + (long long)cs * g.slot_elems;
+                } else {
+                    ca->req[nid] = 1;
+                    if (ca->refine) return -(long long)(k + 1);
+                    brick = false;
+                    sbase = nullptr;
+                    for (int up = 1; up <= 2 && lev + up <= N; ++up) {
+                        const int L2 = lev + up;
+                        const int i2[3] = {idx[0] >> up, idx[1] >> up, idx[2] >> up};
+                        const long long n2 = g.noff[L2] + ((long long)i2[2] * g.nb[L2][1] + i2[1]) * g.nb[L2][0] + i2[0];
+                        if (!(rn[n2].flags & F_BRICK)) continue;
+                        const int c2 = ca->cslot[n2];
+                        if (c2 < 0) {
+                            ca->req[n2] = 1;
+                        } else if (!brick) {
+                            brick = true;
+                            ca->used[n2] = 1;
+                            sbase = ca->cache + (long long)c2 * g.slot_elems;
+#pragma unroll
+                            for (int a = 0; a < 3; ++a) off[a] = (float)(i2[a] * M) - 0.5f;
+                            inv_vox = 1.0f / (float)(1 << L2);
+                        }
+                    }
+                }
+            }
         }
         float I[C];
         if (brick) {
@@ -719,7 +755,7 @@ __device__ __forceinline__ void load_tables(const RenderArgs& a, int C, float4* 
 #define VR_RENDER_MIN_CTAS 3 // resident 256-thread CTAs per SM the register budget is sized for
 #endif
 
-template <int C, int VS, int MODE, bool POW2, bool H, bool XF = false>
+template <int C, int VS, int MODE, bool POW2, bool H, bool XF = false, bool CACHE = false>
 __global__ void __launch_bounds__(256, VR_RENDER_MIN_CTAS) render_kernel(RenderArgs a) {
     extern __shared__ float4 s_tf[];
     __shared__ float s_scl[MAXC];
@@ -781,7 +817,7 @@ __global__ void __launch_bounds__(256, VR_RENDER_MIN_CTAS) render_kernel(RenderA
             if constexpr (XF)
                 n = march_xf<C, VS, POW2>(a.g, a.pool, a.rnodes, *cp, dd, r0, r1, a.xf, f);
             else
-                n = march<C, VS, POW2, H>(a.g, a.pool, a.rnodes, *cp, dd, r0, r1, f);
+                n = march<C, VS, POW2, H>(a.g, a.pool, a.rnodes, *cp, dd, r0, r1, f, CACHE ? &a.cache : nullptr);
             my_samples += (unsigned long long)n;
             if constexpr (MODE == 1) {
                 if (n > 0) {
@@ -961,17 +997,124 @@ __global__ void __launch_bounds__(128, 3) render_backward_kernel(RenderArgs a) {
         if (s_dtf[i] != 0.0f) atomicAdd(&a.dtf[i], s_dtf[i]);
 }
 
-template <int C, int VS, int MODE, bool POW2, bool H, bool XF = false>
+// One refinement pass over the pixels of a single camera: every unfinished ray resumes from its
+// saved sample index and compositing state, and either ends (pixel written) or stops again at its
+// next missing brick (state saved, counted in *pending).
+template <int C, int VS, bool POW2>
+__global__ void __launch_bounds__(256, VR_RENDER_MIN_CTAS) refine_kernel(RenderArgs a) {
+    extern __shared__ float4 s_tf[];
+    __shared__ float s_scl[MAXC];
+    load_tables(a, C, s_tf, s_scl);
+    const int lane = threadIdx.x & 31;
+    unsigned long long* counter = reinterpret_cast<unsigned long long*>(a.counter);
+    unsigned long long my_samples = 0;
+    unsigned int my_pending = 0;
+    const CamParam* cp = &a.cams[0];
+    for (;;) {
+        unsigned long long tile = 0;
+        if (lane == 0) tile = atomicAdd(counter, 1ull);
+        tile = __shfl_sync(0xffffffffu, tile, 0);
+        if ((long long)tile >= a.total_tiles) break;
+        const long long lt = (long long)tile;
+        const int px = (int)(lt % cp->tiles_x) * a.tile_w + lane % a.tile_w;
+        const int py = (int)(lt / cp->tiles_x) * a.tile_h + lane / a.tile_w;
+        if (px >= cp->W || py >= cp->H) continue;
+        const long long pix = (long long)py * cp->W + px;
+        RefineState st = a.refine_state[pix];
+        if (st.status == 2) continue;
+        float dd[3], r0, r1;
+        if (!ray_setup(*cp, a.g, px, py, dd, r0, r1)) {
+            reinterpret_cast<float4*>(cp->img)[pix] = make_float4(0.f, 0.f, 0.f, 0.f);
+            st.status = 2;
+            a.refine_state[pix] = st;
+            continue;
+        }
+        DVRComposite<C> f{{}, s_tf, s_scl, cp->ert};
+        const int k0 = st.status == 1 ? st.k : 0;
+        if (st.status == 1) {
+            f.Cr = st.C[0];
+            f.Cg = st.C[1];
+            f.Cb = st.C[2];
+            f.A = st.A;
+        }
+        const long long r = march<C, VS, POW2, false>(a.g, a.pool, a.rnodes, *cp, dd, r0, r1, f, &a.cache, k0);
+        if (r < 0) {
+            st.k = (int)(-r - 1);
+            st.C[0] = f.Cr;
+            st.C[1] = f.Cg;
+            st.C[2] = f.Cb;
+            st.A = f.A;
+            st.status = 1;
+            my_samples += (unsigned long long)(st.k - k0);
+            ++my_pending;
+        } else {
+            reinterpret_cast<float4*>(cp->img)[pix] = make_float4(f.Cr, f.Cg, f.Cb, f.A);
+            st.status = 2;
+            my_samples += (unsigned long long)(r - k0);
+        }
+        a.refine_state[pix] = st;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        my_samples += __shfl_xor_sync(0xffffffffu, my_samples, o);
+        my_pending += __shfl_xor_sync(0xffffffffu, my_pending, o);
+    }
+    if (lane == 0) {
+        if (a.stats) atomicAdd(&a.stats[0], my_samples);
+        if (my_pending) atomicAdd(a.pending, my_pending);
+    }
+}
+
+__global__ void cache_gather_kernel(const uint16_t* __restrict__ store, uint16_t* __restrict__ cache,
+                                    const int2* __restrict__ list, long long slot_elems) {
+    const int2 e = list[blockIdx.x]; // (store slot, cache slot)
+    const uint4* src = reinterpret_cast<const uint4*>(store + (long long)e.x * slot_elems);
+    uint4* dst = reinterpret_cast<uint4*>(cache + (long long)e.y * slot_elems);
+    const long long n16 = slot_elems * 2 / 16;
+    for (long long i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = src[i];
+}
+
+cudaError_t launch_cache_gather(const uint16_t* store, uint16_t* cache, const int2* list, int n, long long slot_elems,
+                                cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    cache_gather_kernel<<<n, 256, 0, st>>>(store, cache, list, slot_elems);
+    return cudaGetLastError();
+}
+
+template <int C, int VS, int MODE, bool POW2, bool H, bool XF = false, bool CACHE = false>
 static void launch_one(const RenderArgs& a, int blocks, int threads, cudaStream_t st) {
     const size_t smem = (size_t)C * 512 * sizeof(float4) + (H ? (size_t)C * 256 * sizeof(HalfEntry) : 0);
-    cudaFuncSetAttribute(render_kernel<C, VS, MODE, POW2, H, XF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(render_kernel<C, VS, MODE, POW2, H, XF, CACHE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
-    render_kernel<C, VS, MODE, POW2, H, XF><<<blocks, threads, smem, st>>>(a);
+    render_kernel<C, VS, MODE, POW2, H, XF, CACHE><<<blocks, threads, smem, st>>>(a);
 }
 
 template <int C, int VS>
 static cudaError_t launch_fwd_c(const RenderArgs& a, int mode, int fp16, int blocks, int threads, cudaStream_t st) {
     const bool p2 = a.g.pow2 != 0;
+    if (mode == 3) {
+        const size_t smem = (size_t)C * 512 * sizeof(float4);
+        if (p2) {
+            cudaFuncSetAttribute(refine_kernel<C, VS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            refine_kernel<C, VS, true><<<blocks, threads, smem, st>>>(a);
+        } else {
+            cudaFuncSetAttribute(refine_kernel<C, VS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            refine_kernel<C, VS, false><<<blocks, threads, smem, st>>>(a);
+        }
+        return cudaGetLastError();
+    }
+    if (a.cache.cslot && (mode == 0 || mode == 1 || mode == 2)) { // full-frame pass over the render cache
+        if (mode == 0) {
+            if (p2) launch_one<C, VS, 0, true, false, false, true>(a, blocks, threads, st);
+            else launch_one<C, VS, 0, false, false, false, true>(a, blocks, threads, st);
+        } else if (mode == 1) {
+            if (p2) launch_one<C, VS, 1, true, false, false, true>(a, blocks, threads, st);
+            else launch_one<C, VS, 1, false, false, false, true>(a, blocks, threads, st);
+        } else {
+            if (p2) launch_one<C, VS, 2, true, false, false, true>(a, blocks, threads, st);
+            else launch_one<C, VS, 2, false, false, false, true>(a, blocks, threads, st);
+        }
+        return cudaGetLastError();
+    }
     if (a.has_xf && (mode == 0 || mode == 1)) { // per-channel transforms: FP32 interpolation
         if (mode == 0) {
             if (p2) launch_one<C, VS, 0, true, false, true>(a, blocks, threads, st);

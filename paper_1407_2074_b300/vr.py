@@ -28,7 +28,13 @@ class VRError(RuntimeError):
 
 class Options(ctypes.Structure):
     _fields_ = [("background", ctypes.c_uint16), ("homog_threshold", ctypes.c_uint16),
-                ("pool_capacity_bytes", ctypes.c_size_t), ("precision", ctypes.c_int)]
+                ("pool_capacity_bytes", ctypes.c_size_t), ("precision", ctypes.c_int),
+                ("cache_capacity_bytes", ctypes.c_size_t), ("store_on_host", ctypes.c_int)]
+
+
+class CacheReport(ctypes.Structure):
+    _fields_ = [("requested", ctypes.c_int64), ("uploaded", ctypes.c_int64), ("evicted", ctypes.c_int64),
+                ("resident", ctypes.c_int64), ("capacity", ctypes.c_int64)]
 
 
 class Camera(ctypes.Structure):
@@ -74,6 +80,12 @@ def lib():
         L.vr_last_error.restype = ctypes.c_char_p
         L.vr_last_error.argtypes = [vp]
         L.vr_set_tile_shape.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+        L.vr_cache_update.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(CacheReport)]
+        L.vr_cache_load.argtypes = [vp, ctypes.c_int64, vp, vp]
+        L.vr_cache_read.argtypes = [vp, vp, vp, vp, vp]
+        L.vr_refine_begin.argtypes = [vp, ctypes.POINTER(Camera), vp, ctypes.POINTER(vp)]
+        L.vr_refine_pass.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+        L.vr_refine_end.argtypes = [vp]
         L.vr_set_launch_shape.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.vr_plan_create.argtypes = [vp, ctypes.POINTER(Camera), ctypes.c_int, ctypes.POINTER(vp), ctypes.c_int,
                                      ctypes.POINTER(vp)]
@@ -83,6 +95,8 @@ def lib():
         for f in ("vr_create", "vr_destroy", "vr_insert_block", "vr_insert_slice", "vr_set_transfer_functions",
                   "vr_set_clip_planes", "vr_set_channel_transforms", "vr_render", "vr_render_backward", "vr_read_level", "vr_read_voxels", "vr_read_node", "vr_render_footprint",
                   "vr_stats", "vr_set_tile_shape", "vr_set_launch_shape", "vr_plan_create", "vr_plan_launch",
+                  "vr_cache_update", "vr_cache_load", "vr_cache_read", "vr_refine_begin", "vr_refine_pass",
+                  "vr_refine_end",
                   "vr_plan_samples", "vr_plan_destroy"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
@@ -117,7 +131,7 @@ class Renderer:
     """One volume context (vr_ctx) on the current CUDA device."""
 
     def __init__(self, dims, channels, brick, background=0, tau=0, pool_capacity_bytes=0, precision="fp32",
-                 device=None):
+                 device=None, cache_capacity_bytes=0, store_on_host=False):
         import torch
 
         self._ctx = None
@@ -125,7 +139,8 @@ class Renderer:
             torch.cuda.set_device(torch.device(device))
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.dims, self.C, self.M = tuple(int(d) for d in dims), int(channels), int(brick)
-        opt = Options(background, tau, pool_capacity_bytes, VR_FP16_INTERP if precision == "fp16" else VR_FP32)
+        opt = Options(background, tau, pool_capacity_bytes, VR_FP16_INTERP if precision == "fp16" else VR_FP32,
+                      cache_capacity_bytes, 1 if store_on_host else 0)
         h = ctypes.c_void_p()
         rc = lib().vr_create((ctypes.c_int64 * 3)(*self.dims), self.C, self.M, ctypes.byref(opt), None,
                              ctypes.byref(h))
@@ -311,10 +326,67 @@ class Renderer:
                                        ctypes.c_void_p(_stream_ptr(stream))))
         return int(fl.value), list(avg[: self.C])
 
+    # ---- out-of-core rendering ----
+    def cache_update(self, max_uploads=1 << 30, refinement=False, stream=None) -> dict:
+        rep = CacheReport()
+        self._check(lib().vr_cache_update(self._ctx, int(min(max_uploads, 2 ** 31 - 1)), 1 if refinement else 0,
+                                          ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(rep)))
+        return {k: getattr(rep, k) for k, _ in CacheReport._fields_}
+
+    def cache_load(self, nodes, stream=None):
+        a = np.ascontiguousarray(np.asarray(nodes, dtype=np.int64).reshape(-1))
+        self._check(lib().vr_cache_load(self._ctx, a.shape[0], a.ctypes.data, ctypes.c_void_p(_stream_ptr(stream))))
+
+    def cache_read(self, stream=None):
+        n = self.stats().nodes
+        res, used, req = (np.zeros(n, np.uint8) for _ in range(3))
+        self._check(lib().vr_cache_read(self._ctx, res.ctypes.data, used.ctypes.data, req.ctypes.data,
+                                        ctypes.c_void_p(_stream_ptr(stream))))
+        return res, used, req
+
+    def refine(self, cam, image=None):
+        """Refinement session of one view; call .pass_() and cache_update(refinement=True) until done."""
+        return RefineSession(self, cam, image)
+
     def stats(self) -> Stats:
         s = Stats()
         self._check(lib().vr_stats(self._ctx, ctypes.byref(s)))
         return s
+
+
+class RefineSession:
+    """vr_refine: refinement ray casting of one view (resumable rays over passes)."""
+
+    def __init__(self, renderer, cam, image=None):
+        import torch
+
+        self.r = renderer
+        self.cam = cam
+        self.image = image if image is not None else torch.zeros((cam["height"], cam["width"], 4),
+                                                                 dtype=torch.float32, device=renderer.device)
+        cs = camera_struct(cam)
+        h = ctypes.c_void_p()
+        renderer._check(lib().vr_refine_begin(renderer.handle, ctypes.byref(cs), ctypes.c_void_p(self.image.data_ptr()),
+                                              ctypes.byref(h)))
+        self._p = h.value
+
+    def pass_(self, stream=None):
+        """One pass; returns (rays still pending, samples composited in the pass)."""
+        pend, samp = ctypes.c_int64(), ctypes.c_int64()
+        self.r._check(lib().vr_refine_pass(self._p, ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(pend),
+                                           ctypes.byref(samp)))
+        return pend.value, samp.value
+
+    def close(self):
+        if self._p:
+            lib().vr_refine_end(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class RenderPlan:

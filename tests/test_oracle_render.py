@@ -311,3 +311,39 @@ def test_channel_translation_equals_shifted_data():
     assert np.abs(a - b).max() < 1e-6
     c = O.render_image(dense(vol), cam, w.tf(), [1, 1, 1])[0]
     assert np.abs(a - c).max() > 1e-3  # the transform does something
+
+
+def test_full_frame_cache_semantics():
+    # Sec. "Full-Frame Ray-Casting".  (1) every brick present: the plain render, nothing requested;
+    # (2) only the root present: a level-0 sample falls back to its grandparent (the root, N = 2),
+    # i.e. the image of a camera whose level choice is the root everywhere; every missing brick on
+    # the paths is requested; (3) nothing present: a constant volume still renders its closed form
+    # through the AVG values.
+    w = S.tiny()
+    vol = w.spec().volume()
+    v = dense(vol)
+    cam = dict(w.cameras[0])
+    cam["width"] = cam["height"] = 32
+    cam["lod_error_px"] = 1e-3  # level 0 everywhere
+    tf, sc = w.tf(), [1.0, 1.0, 1.0]
+    nn = O.node_count(v)
+    root = O.node_index(v, v.N, 0, 0, 0)
+    allres = np.ones(nn, np.uint8)
+    nc, cand, _, used, req = O.render_cache(v, cam, tf, sc, allres)
+    ref = O.render(v, cam, tf, sc, None, 0)[1]
+    assert np.array_equal(cand, ref) and req.sum() == 0 and used.sum() > 0 and used[root] == 0
+    onlyroot = np.zeros(nn, np.uint8)
+    onlyroot[root] = 1
+    _, cand2, _, used2, req2 = O.render_cache(v, cam, tf, sc, onlyroot)
+    far = dict(cam)
+    far["lod_error_px"] = 1e6  # level N everywhere
+    ref2 = O.render(v, far, tf, sc, None, 0)[1]
+    assert np.abs(cand2[:, 0] - ref2[:, 0]).max() < 1e-12
+    assert used2[root] == 1 and used2.sum() == 1
+    lvl1 = [O.node_index(v, 1, i, j, k) for i in range(2) for j in range(2) for k in range(2)]
+    assert req2[lvl1].sum() > 0 and req2[:64].sum() > 0 and req2[root] == 0
+    const = dense(np.full((64, 64, 64, 1), 30000, dtype=np.uint16))
+    tf1 = const_tf(RGB, 1.0 - math.exp(-SIG))
+    c1 = cam1()
+    _, cc, _, _, rq = O.render_cache(const, c1, tf1, [1.0], np.zeros(O.node_count(const), np.uint8), ([0], [0]))
+    assert abs(cc[0, 0, 3] - (1.0 - math.exp(-SIG * 64.0))) < 1e-6 and rq.sum() > 0
