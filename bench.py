@@ -85,10 +85,9 @@ class ClockSampler:
 
 
 def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_1407_2074_b300 import dist as D
+
+    return D.env()
 
 
 def build_volume(w, r, torch):
@@ -374,7 +373,7 @@ def main():
         blocks.append((z0, b))
     torch.cuda.synchronize()
     nsteps = args.warmup + args.steps
-    frame_of = [(rank * nsteps + i) % 60 for i in range(nsteps)]
+    frame_of = vr.dist.frames_for_rank(rank, nsteps, 60)
     H, W = w.cameras[0]["height"], w.cameras[0]["width"]
     images = [torch.empty((H, W, 4), dtype=torch.float32, device="cuda") for _ in range(2)]
     # samples per frame (deterministic; measured once, untimed)
@@ -413,19 +412,11 @@ def main():
             ev[i][2].record()
         stop.record()
         torch.cuda.synchronize()
-    total_ms = start.elapsed_time(stop)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
     timed = range(args.warmup, nsteps)
     render_ms = float(np.mean([ev[i][1].elapsed_time(ev[i][2]) for i in timed]))
     insert_ms = float(np.mean([ev[i][0].elapsed_time(ev[i][1]) for i in timed]))
-    samples = float(sum(samples_of[frame_of[i]] for i in timed))
-    if dist:
-        t = torch.tensor([samples], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t)
-        samples = float(t.item())
+    total_ms, samples = vr.dist.aggregate(start.elapsed_time(stop),
+                                          float(sum(samples_of[frame_of[i]] for i in timed)), device="cuda")
     value = samples / (total_ms / 1000.0)
     ms_per_step = total_ms / args.steps
 
@@ -449,11 +440,7 @@ def main():
             out_host[i % 2].copy_(images[i % 2], non_blocking=True)
         e1.record()
         torch.cuda.synchronize()
-        e2e_ms = e0.elapsed_time(e1)
-        if dist:
-            t = torch.tensor([e2e_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
+        e2e_ms, _ = vr.dist.aggregate(e0.elapsed_time(e1), 0.0, device="cuda")
         e2e = {"value": samples / (e2e_ms / 1000.0), "unit": "samples/s",
                "h2d_bytes_per_step": int(SLICES_PER_STEP * X * Y * 3 * 2), "d2h_bytes_per_step": int(H * W * 16),
                "ms_per_step": e2e_ms / args.steps}

@@ -4,3 +4,4 @@ The compute path is libvr.so (hand-written sm_103a CUDA behind the C ABI in incl
 this package only marshals arguments to it.
 """
 from .vr import Renderer, RenderFn, render, VRError, LIB_PATH  # noqa: F401
+from . import dist  # noqa: F401
