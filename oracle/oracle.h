@@ -88,6 +88,13 @@ typedef void (*or_gen_fn)(void* user, int64_t x, int64_t y, int64_t z, uint16_t*
 or_volume* or_lazy_create(const int64_t dim[3], int C, int M, uint16_t bg, uint16_t tau, or_gen_fn gen, void* user,
                           int64_t z_lo, int64_t z_hi);
 
+/* ---- streamed volume: the state of a fully inserted volume whose level 0 is fed once, slab by
+ *      slab in z order (slab [nz][Y][X][C], z0 = the next slice), and read back through gen;
+ *      levels 1..N and node records are complete after or_stream_finish ---- */
+or_volume* or_stream_create(const int64_t dim[3], int C, int M, uint16_t bg, uint16_t tau, or_gen_fn gen, void* user);
+int or_stream_feed(or_volume* v, int64_t z0, int64_t nz, const uint16_t* slab, int threads);
+int or_stream_finish(or_volume* v, int threads);
+
 void or_volume_destroy(or_volume* v);
 const or_geom* or_volume_geom(const or_volume* v);
 uint16_t or_value(or_volume* v, int L, int64_t x, int64_t y, int64_t z, int c);

@@ -65,6 +65,11 @@ def lib():
         L.or_lazy_create.restype = ctypes.c_void_p
         L.or_lazy_create.argtypes = [i64p, ctypes.c_int, ctypes.c_int, ctypes.c_uint16, ctypes.c_uint16,
                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64]
+        L.or_stream_create.restype = ctypes.c_void_p
+        L.or_stream_create.argtypes = [i64p, ctypes.c_int, ctypes.c_int, ctypes.c_uint16, ctypes.c_uint16,
+                                       ctypes.c_void_p, ctypes.c_void_p]
+        L.or_stream_feed.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int]
+        L.or_stream_finish.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.or_volume_destroy.argtypes = [ctypes.c_void_p]
         L.or_volume_geom.restype = ctypes.POINTER(Geom)
         L.or_volume_geom.argtypes = [ctypes.c_void_p]
@@ -188,16 +193,51 @@ class DenseVolume(Volume):
         return arr.reshape(Z, Y, X, g.C).copy()
 
 
+class StreamVolume(Volume):
+    """A fully inserted volume whose level 0 is fed once, in z order, as slabs [nz][Y][X][C] and read
+    back through ``gen_fn`` (for volumes too large to hold level 0 in host memory); levels >= 1 and
+    the node records are complete after ``finish()``."""
+
+    def __init__(self, dims, channels, brick, gen_fn_addr: int, user: int, background=0, tau=0, owner=None):
+        """owner: the object that keeps ``user`` valid (e.g. the generator spec); held as long as this volume."""
+        h = lib().or_stream_create(_i64(dims), channels, brick, background, tau, ctypes.c_void_p(gen_fn_addr),
+                                   ctypes.c_void_p(user))
+        if not h:
+            raise ValueError("invalid volume geometry")
+        super().__init__(h, keep=(owner,))
+        self.C = channels
+        self.next_z = 0
+
+    def feed(self, z0, slab: np.ndarray, threads=0):
+        b = np.ascontiguousarray(slab)
+        if b.dtype == np.int16:
+            b = b.view(np.uint16)
+        if lib().or_stream_feed(self._h, z0, b.shape[0], b.ctypes.data, threads) != 0:
+            raise ValueError("slabs must arrive in z order and lie inside the volume")
+        self.next_z = z0 + b.shape[0]
+
+    def finish(self, threads=0):
+        if lib().or_stream_finish(self._h, threads) != 0:
+            raise ValueError("volume not completely fed")
+
+    def level(self, L) -> np.ndarray:
+        if L < 1:
+            raise ValueError("level 0 of a streamed volume is not stored")
+        return DenseVolume.level(self, L)
+
+
 class LazyVolume(Volume):
     """Level 0 from ``gen_fn(user, x, y, z, out[C])`` for z in [z_lo, z_hi), background elsewhere."""
 
-    def __init__(self, dims, channels, brick, gen_fn_addr: int, user: int, z_lo=0, z_hi=None, background=0, tau=0):
+    def __init__(self, dims, channels, brick, gen_fn_addr: int, user: int, z_lo=0, z_hi=None, background=0, tau=0,
+                 owner=None):
+        """owner: the object that keeps ``user`` valid (e.g. the generator spec); held as long as this volume."""
         z_hi = dims[2] if z_hi is None else z_hi
         h = lib().or_lazy_create(_i64(dims), channels, brick, background, tau, ctypes.c_void_p(gen_fn_addr),
                                  ctypes.c_void_p(user), z_lo, z_hi)
         if not h:
             raise ValueError("invalid volume geometry")
-        super().__init__(h)
+        super().__init__(h, keep=(owner,))
         self.C = channels
 
 

@@ -150,6 +150,12 @@ struct or_volume {
     int64_t z_lo, z_hi;
     memo_shard* vmemo[OR_MAXL];
     node_shard* nmemo;
+    /* streamed: level 0 fed once in z order and read back through gen; levels >= 1 in V[] */
+    int streamed;
+    int64_t next_z;     /* first level-0 slice not fed yet */
+    uint16_t* carry;    /* an even slice whose odd partner comes with the next feed */
+    int have_carry;
+    uint64_t* sum0;     /* [level-0 node][C] running sums */
 };
 
 const or_geom* or_volume_geom(const or_volume* v) { return &v->g; }
@@ -193,7 +199,7 @@ or_volume* or_dense_create(const int64_t dim[3], int C, int M, uint16_t bg, uint
 }
 
 int or_dense_insert(or_volume* v, const int64_t o[3], const int64_t e[3], const uint16_t* block) {
-    if (!v || v->lazy) return -1;
+    if (!v || v->lazy || v->streamed) return -1;
     const or_geom* g = &v->g;
     for (int a = 0; a < 3; ++a)
         if (o[a] < 0 || e[a] < 0 || o[a] + e[a] > g->dim[a]) return -1;
@@ -303,7 +309,7 @@ static void build_nodes_range(void* p, int64_t b, int64_t e) {
 }
 
 int or_dense_build(or_volume* v, int threads) {
-    if (!v || v->lazy) return -1;
+    if (!v || v->lazy || v->streamed) return -1;
     const or_geom* g = &v->g;
     for (int L = 1; L <= g->N; ++L) {
         lvl_arg a = {v, L};
@@ -319,7 +325,7 @@ int or_dense_build(or_volume* v, int threads) {
 
 const uint16_t* or_dense_level(or_volume* v, int L) {
     if (!v || v->lazy || L < 0 || L > v->g.N) return NULL;
-    return v->V[L];
+    return v->V[L]; /* NULL for level 0 of a streamed volume */
 }
 
 /* ---- lazy volume ---- */
@@ -428,6 +434,11 @@ static void lazy_voxel(or_volume* v, int L, int64_t x, int64_t y, int64_t z, uin
 
 uint16_t or_value(or_volume* v, int L, int64_t x, int64_t y, int64_t z, int c) {
     const or_geom* g = &v->g;
+    if (v->streamed && L == 0) {
+        uint16_t val[OR_MAXC] = {0};
+        v->gen(v->user, x, y, z, val);
+        return val[c];
+    }
     if (v->lazy) {
         uint16_t val[OR_MAXC];
         lazy_voxel(v, L, x, y, z, val);
@@ -473,6 +484,215 @@ static void lazy_node(or_volume* v, int L, int64_t i, int64_t j, int64_t k, or_n
     for (int c = 0; c < g->C; ++c) n->avg[c] = g->bg; /* read only when there is no brick */
 }
 
+/* ---- streamed volume ----
+ * The same state as a dense volume into which the whole level 0 was inserted, for volumes whose
+ * level 0 does not fit in host memory: level 0 is fed once, slab by slab in z order, and is not
+ * stored (or_value reads it back through the generator that produced it); level 1 is half-sampled
+ * from each pair of level-0 slices as the pair arrives; levels 2..N by build_level_rows.  Node
+ * records: level-0 brick min/max/sum accumulate while feeding; a level-L brick (L >= 1) is scanned
+ * in V[L]; the level-0 region of a node is the union of its children's level-0 regions, so its
+ * subtree min/max is the min/max over the children's. */
+or_volume* or_stream_create(const int64_t dim[3], int C, int M, uint16_t bg, uint16_t tau, or_gen_fn gen, void* user) {
+    or_volume* v = (or_volume*)calloc(1, sizeof(or_volume));
+    if (!v || !gen || or_geom_init(&v->g, dim, C, M, bg, tau) != 0) {
+        free(v);
+        return NULL;
+    }
+    const or_geom* g = &v->g;
+    v->streamed = 1;
+    v->gen = gen;
+    v->user = user;
+    for (int L = 0; L <= g->N; ++L) {
+        if (L >= 1) {
+            v->V[L] = (uint16_t*)malloc(sizeof(uint16_t) * (size_t)(g->ldim[L][0] * g->ldim[L][1] * g->ldim[L][2] * C));
+            if (!v->V[L]) {
+                or_volume_destroy(v);
+                return NULL;
+            }
+        }
+        v->nodes[L] = (or_node*)calloc((size_t)(g->nb[L][0] * g->nb[L][1] * g->nb[L][2]), sizeof(or_node));
+        if (!v->nodes[L]) {
+            or_volume_destroy(v);
+            return NULL;
+        }
+    }
+    const int64_t n0 = g->nb[0][0] * g->nb[0][1] * g->nb[0][2];
+    v->sum0 = (uint64_t*)calloc((size_t)(n0 * C), sizeof(uint64_t));
+    v->carry = (uint16_t*)malloc(sizeof(uint16_t) * (size_t)(dim[0] * dim[1] * C));
+    if (!v->sum0 || !v->carry) {
+        or_volume_destroy(v);
+        return NULL;
+    }
+    for (int64_t i = 0; i < n0; ++i)
+        for (int c = 0; c < C; ++c) {
+            v->nodes[0][i].bmin[c] = 0xffff;
+            v->nodes[0][i].bmax[c] = 0;
+        }
+    return v;
+}
+
+typedef struct {
+    or_volume* v;
+    const uint16_t* s0; /* level-0 slice z (and s1 = slice z + 1, or NULL) */
+    const uint16_t* s1;
+    int64_t z;
+} feed_arg;
+
+/* level-0 brick statistics of slice z, one task per row of bricks (disjoint node sets) */
+static void feed_stats_rows(void* p, int64_t b, int64_t e) {
+    feed_arg* a = (feed_arg*)p;
+    or_volume* v = a->v;
+    const or_geom* g = &v->g;
+    const int C = g->C, M = g->M;
+    const int64_t X = g->dim[0], Y = g->dim[1], k = a->z / M;
+    for (int64_t j = b; j < e; ++j) {
+        const int64_t y1 = (j + 1) * M < Y ? (j + 1) * M : Y;
+        for (int64_t y = j * M; y < y1; ++y)
+            for (int64_t x = 0; x < X; ++x) {
+                const int64_t nid = nidx(g, 0, x / M, j, k);
+                or_node* n = &v->nodes[0][nid];
+                const uint16_t* val = a->s0 + (y * X + x) * C;
+                for (int c = 0; c < C; ++c) {
+                    if (val[c] < n->bmin[c]) n->bmin[c] = val[c];
+                    if (val[c] > n->bmax[c]) n->bmax[c] = val[c];
+                    v->sum0[nid * C + c] += val[c];
+                }
+                n->count++;
+            }
+    }
+}
+
+/* level-1 slice z / 2 from level-0 slices z and z + 1 (s1 == NULL: z + 1 is outside the volume) */
+static void feed_level1_rows(void* p, int64_t b, int64_t e) {
+    feed_arg* a = (feed_arg*)p;
+    or_volume* v = a->v;
+    const or_geom* g = &v->g;
+    const int C = g->C;
+    const int64_t X = g->dim[0], Y = g->dim[1];
+    uint16_t* Q = v->V[1];
+    for (int64_t y = b; y < e; ++y)
+        for (int64_t x = 0; x < g->ldim[1][0]; ++x)
+            for (int c = 0; c < C; ++c) {
+                uint64_t S = 0, k = 0;
+                for (int dz = 0; dz < 2; ++dz) {
+                    const uint16_t* P = dz ? a->s1 : a->s0;
+                    if (!P) continue;
+                    for (int dy = 0; dy < 2; ++dy)
+                        for (int dx = 0; dx < 2; ++dx) {
+                            const int64_t cx = 2 * x + dx, cy = 2 * y + dy;
+                            if (cx < X && cy < Y) {
+                                S += P[(cy * X + cx) * C + c];
+                                ++k;
+                            }
+                        }
+                }
+                Q[vidx(g, 1, x, y, a->z / 2) * C + c] = rhu(S, k);
+            }
+}
+
+int or_stream_feed(or_volume* v, int64_t z0, int64_t nz, const uint16_t* slab, int threads) {
+    if (!v || !v->streamed || z0 != v->next_z || nz <= 0 || z0 + nz > v->g.dim[2] || !slab) return -1;
+    const or_geom* g = &v->g;
+    const int64_t X = g->dim[0], Y = g->dim[1], plane = X * Y * g->C, Z = g->dim[2];
+    for (int64_t z = z0; z < z0 + nz; ++z) {
+        const uint16_t* sz = slab + (z - z0) * plane;
+        feed_arg a = {v, sz, NULL, z};
+        or_parallel_for(g->nb[0][1], 1, threads, feed_stats_rows, &a);
+        if (g->N >= 1) {
+            if ((z & 1) == 0) {
+                if (z + 1 < z0 + nz) { /* partner in this slab */
+                    a.s1 = sz + plane;
+                    or_parallel_for(g->ldim[1][1], 8, threads, feed_level1_rows, &a);
+                } else if (z + 1 == Z) { /* last slice of an odd extent */
+                    or_parallel_for(g->ldim[1][1], 8, threads, feed_level1_rows, &a);
+                } else {
+                    memcpy(v->carry, sz, sizeof(uint16_t) * (size_t)plane);
+                    v->have_carry = 1;
+                }
+            } else if (z == z0 && v->have_carry) { /* odd partner of the carried slice */
+                feed_arg b = {v, v->carry, sz, z - 1};
+                or_parallel_for(g->ldim[1][1], 8, threads, feed_level1_rows, &b);
+                v->have_carry = 0;
+            }
+        }
+    }
+    v->next_z = z0 + nz;
+    return 0;
+}
+
+static void stream_nodes_range(void* p, int64_t b, int64_t e) {
+    lvl_arg* a = (lvl_arg*)p;
+    or_volume* v = a->v;
+    const or_geom* g = &v->g;
+    const int L = a->L, C = g->C, M = g->M;
+    for (int64_t r = b; r < e; ++r) {
+        const int64_t i = r % g->nb[L][0], j = (r / g->nb[L][0]) % g->nb[L][1], k = r / (g->nb[L][0] * g->nb[L][1]);
+        or_node* n = &v->nodes[L][r];
+        uint64_t sum[OR_MAXC] = {0};
+        if (L == 0) {
+            for (int c = 0; c < C; ++c) {
+                sum[c] = v->sum0[r * C + c];
+                n->smin[c] = n->bmin[c];
+                n->smax[c] = n->bmax[c];
+            }
+        } else {
+            n->count = 0;
+            for (int c = 0; c < C; ++c) {
+                n->bmin[c] = n->smin[c] = 0xffff;
+                n->bmax[c] = n->smax[c] = 0;
+            }
+            const int64_t lo[3] = {i * M, j * M, k * M};
+            int64_t hi[3];
+            for (int q = 0; q < 3; ++q) hi[q] = lo[q] + M < g->ldim[L][q] ? lo[q] + M : g->ldim[L][q];
+            for (int64_t z = lo[2]; z < hi[2]; ++z)
+                for (int64_t y = lo[1]; y < hi[1]; ++y)
+                    for (int64_t x = lo[0]; x < hi[0]; ++x) {
+                        const uint16_t* val = &v->V[L][vidx(g, L, x, y, z) * C];
+                        for (int c = 0; c < C; ++c) {
+                            sum[c] += val[c];
+                            if (val[c] < n->bmin[c]) n->bmin[c] = val[c];
+                            if (val[c] > n->bmax[c]) n->bmax[c] = val[c];
+                        }
+                        n->count++;
+                    }
+            for (int d = 0; d < 8; ++d) {
+                const int64_t ci = 2 * i + (d & 1), cj = 2 * j + ((d >> 1) & 1), ck = 2 * k + (d >> 2);
+                if (ci >= g->nb[L - 1][0] || cj >= g->nb[L - 1][1] || ck >= g->nb[L - 1][2]) continue;
+                const or_node* ch = &v->nodes[L - 1][nidx(g, L - 1, ci, cj, ck)];
+                for (int c = 0; c < C; ++c) {
+                    if (ch->smin[c] < n->smin[c]) n->smin[c] = ch->smin[c];
+                    if (ch->smax[c] > n->smax[c]) n->smax[c] = ch->smax[c];
+                }
+            }
+        }
+        n->touched = 1; /* the whole volume was fed */
+        n->brick_homog = 1;
+        n->subtree_homog = 1;
+        for (int c = 0; c < C; ++c) {
+            if (!((int)n->bmax[c] - (int)n->bmin[c] < (int)g->tau)) n->brick_homog = 0;
+            if (!((int)n->smax[c] - (int)n->smin[c] < (int)g->tau)) n->subtree_homog = 0;
+            n->avg[c] = rhu(sum[c], (uint64_t)n->count);
+        }
+        n->has_children = (L > 0) && !n->subtree_homog;
+        n->has_brick = !n->brick_homog;
+    }
+}
+
+int or_stream_finish(or_volume* v, int threads) {
+    if (!v || !v->streamed || v->next_z != v->g.dim[2] || v->built) return -1;
+    const or_geom* g = &v->g;
+    for (int L = 2; L <= g->N; ++L) {
+        lvl_arg a = {v, L};
+        or_parallel_for(g->ldim[L][1] * g->ldim[L][2], 4, threads, build_level_rows, &a);
+    }
+    for (int L = 0; L <= g->N; ++L) { /* children before parents */
+        lvl_arg a = {v, L};
+        or_parallel_for(g->nb[L][0] * g->nb[L][1] * g->nb[L][2], 1, threads, stream_nodes_range, &a);
+    }
+    v->built = 1;
+    return 0;
+}
+
 int or_node_info(or_volume* v, int L, int64_t i, int64_t j, int64_t k, or_node* out) {
     const or_geom* g = &v->g;
     if (L < 0 || L > g->N || i < 0 || j < 0 || k < 0 || i >= g->nb[L][0] || j >= g->nb[L][1] || k >= g->nb[L][2])
@@ -509,5 +729,7 @@ void or_volume_destroy(or_volume* v) {
         free(v->nmemo);
     }
     free(v->ins);
+    free(v->carry);
+    free(v->sum0);
     free(v);
 }

@@ -196,7 +196,7 @@ def _full_size_render(w, frames, tau, n_px, seed):
     del buf
     tf, sc = w.tf(), [1.0, 1.0, 1.0]
     imgs = _render(r, w.cameras, tf, sc)
-    lazy = O.LazyVolume(w.dims, 3, w.brick, spec.voxel_fn, spec.handle, 0, Z, tau=0)
+    lazy = O.LazyVolume(w.dims, 3, w.brick, spec.voxel_fn, spec.handle, 0, Z, tau=0, owner=spec)
     rng = np.random.default_rng(seed)
     for cam, img in zip(w.cameras, imgs):
         hit = np.argwhere(img[..., 3] > 0.05)
@@ -214,6 +214,79 @@ def test_streamed_full_size_sampled_pixels():
 def test_large_full_size_sampled_pixels():
     """The 24 GiB 2048x2048x1024 volume at 1920x1080 (orbit frame 0), sampled pixels."""
     _full_size_render(S.large(tau=0), None, 0, 24, 2)
+
+
+def _stream_oracle(w, tau, slab=16):
+    """The oracle state of the whole workload volume, fed in z order from the synthetic generator
+    (its device form, checked against the host form on one slab here and in the generator tests)."""
+    import torch
+
+    spec = w.spec()
+    X, Y, Z = w.dims
+    st = O.StreamVolume(w.dims, 3, w.brick, spec.voxel_fn, spec.handle, tau=tau, owner=spec)
+    buf = torch.empty((slab, Y, X, 3), dtype=torch.int16, device="cuda")
+    host = torch.empty((slab, Y, X, 3), dtype=torch.int16, pin_memory=True)
+    s = torch.cuda.current_stream().cuda_stream
+    for z0 in range(0, Z, slab):
+        z1 = min(Z, z0 + slab)
+        spec.generate_device(buf.data_ptr(), z0, z1, s)
+        host[: z1 - z0].copy_(buf[: z1 - z0])
+        torch.cuda.synchronize()
+        if z0 == slab * (Z // (2 * slab)):
+            assert np.array_equal(host[: z1 - z0].numpy().view(np.uint16), spec.slices(z0, z1))
+        st.feed(z0, host[: z1 - z0].numpy())
+    st.finish()
+    return st
+
+
+@pytest.mark.parametrize("name", ["streamed", "large"])
+def test_full_size_tau_3277_frames_fp32_and_fp16(name):
+    """The benchmarked configuration: full-size volume with tau = 3277 (homogeneous subtrees pruned,
+    closed-form runs), 1920x1080 orbit frames 0, 15, 30, 45, the default launch shape; sampled
+    pixels of the FP32 render within the parity tolerance of the oracle, FP16 interpolation within
+    its own bound."""
+    import torch
+    import paper_1407_2074_b300 as vr
+    from paper_1407_2074_b300 import vr as V
+
+    frames = (0, 15, 30, 45)
+    if name == "streamed":
+        w = S.streamed(tau=3277)
+        w.cameras = [S.streamed(tau=3277, frame=f).cameras[0] for f in frames]
+    else:
+        w = S.large(tau=3277, frames=frames)
+    spec = w.spec()
+    X, Y, Z = w.dims
+    r = vr.Renderer(w.dims, 3, w.brick, tau=w.tau)
+    buf = torch.empty((8, Y, X, 3), dtype=torch.int16, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    for z0 in range(0, Z, 8):
+        spec.generate_device(buf.data_ptr(), z0, min(Z, z0 + 8), s)
+        r.insert_block((0, 0, z0), buf[: min(Z, z0 + 8) - z0])
+    del buf
+    tf, sc = w.tf(), [1.0, 1.0, 1.0]
+    r.set_transfer_functions(torch.from_numpy(tf).cuda(), torch.ones(3, device="cuda"))
+    H, W = w.cameras[0]["height"], w.cameras[0]["width"]
+    img32 = torch.empty((H, W, 4), device="cuda")
+    img16 = torch.empty((H, W, 4), device="cuda")
+    st = _stream_oracle(w, 3277)
+    rng = np.random.default_rng(7)
+    for f, cam in zip(frames, w.cameras):
+        r.render([cam], [img32])
+        r.render([cam], [img16], mode=V.VR_MODE_DVR | V.VR_RENDER_FP16)
+        torch.cuda.synchronize()
+        a32, a16 = img32.cpu().numpy(), img16.cpu().numpy()
+        hit = np.argwhere(a32[..., 3] > 0.05)
+        pick = np.concatenate([hit[rng.choice(len(hit), size=min(40, len(hit)), replace=False)],
+                               np.stack([rng.integers(0, H, 8), rng.integers(0, W, 8)], 1)])
+        px, py = pick[:, 1].astype(np.int32), pick[:, 0].astype(np.int32)
+        nc, cand, _ = O.render(st, cam, tf, sc, (px, py))
+        e32 = admissible_error(a32[py, px], nc, cand)
+        e16 = admissible_error(a16[py, px], nc, cand)
+        print(f"{name} frame {f}: FP32 max {e32.max():.2e}; FP16 max {e16.max():.2e} mean {e16.mean():.2e}")
+        assert e32.max() <= RGBA_TOL, (f, e32.max())
+        assert e16.max() <= 2e-2, (f, e16.max())
+    r.close()
 
 
 def test_homogeneous_runs_with_early_termination():

@@ -179,7 +179,7 @@ def test_lazy_volume_matches_dense_volume():
         dense = O.DenseVolume(dims, 3, 8, 100, tau)
         dense.insert((0, 0, 10), vol[10:30])
         dense.build(threads=2)
-        lazy = O.LazyVolume(dims, 3, 8, spec.voxel_fn, spec.handle, 10, 30, background=100, tau=tau)
+        lazy = O.LazyVolume(dims, 3, 8, spec.voxel_fn, spec.handle, 10, 30, background=100, tau=tau, owner=spec)
         rng = np.random.default_rng(tau)
         for L in range(dense.N + 1):
             X, Y, Z = dense.level_dims(L)
@@ -196,3 +196,49 @@ def test_lazy_volume_matches_dense_volume():
                         assert (a.touched, a.has_children, a.has_brick) == (b.touched, b.has_children, b.has_brick)
                         if not a.has_brick:
                             assert list(a.avg[:3]) == list(b.avg[:3])
+
+
+@pytest.mark.parametrize("dims,C,M,tau,cuts", [((48, 40, 37), 3, 8, 400, (5, 6, 1, 7, 18)),
+                                               ((33, 21, 19), 1, 4, 0, (2, 2, 2, 2, 2, 2, 2, 2, 3)),
+                                               ((40, 24, 30), 2, 6, 900, (30,)),
+                                               ((64, 64, 64), 3, 16, 3277, (8,) * 8)])
+def test_streamed_volume_matches_dense_volume(dims, C, M, tau, cuts):
+    """The streamed construction (level 0 fed once in z order, levels >= 1 and node records from
+    one pass) is the dense oracle's state: every level >= 1 and every node record are equal, level
+    0 reads back the generator, and a render gives the same numbers."""
+    spec = S.VolumeSpec(S.KIND_SPIM, dims, C, 30, seed=5)
+    vol = spec.volume()
+    dense = O.DenseVolume(dims, C, M, 0, tau)
+    dense.insert((0, 0, 0), vol)
+    dense.build(threads=2)
+    st = O.StreamVolume(dims, C, M, spec.voxel_fn, spec.handle, tau=tau, owner=spec)
+    z = 0
+    for n in cuts:  # uneven slabs, odd and even starts
+        st.feed(z, vol[z:z + n], threads=2)
+        z += n
+    assert z == dims[2]
+    with pytest.raises(ValueError):
+        st.feed(0, vol[:1])  # out of order
+    st.finish(threads=2)
+    for L in range(1, dense.N + 1):
+        assert np.array_equal(st.level(L), dense.level(L)), L
+    g = dense.geom
+    fields = ("touched", "has_children", "has_brick", "brick_homog", "subtree_homog", "count")
+    for L in range(dense.N + 1):
+        for k in range(g.nb[L][2]):
+            for j in range(g.nb[L][1]):
+                for i in range(g.nb[L][0]):
+                    a, b = dense.node(L, i, j, k), st.node(L, i, j, k)
+                    assert all(getattr(a, f) == getattr(b, f) for f in fields), (L, i, j, k)
+                    for arr in ("avg", "bmin", "bmax", "smin", "smax"):
+                        assert list(getattr(a, arr)[:C]) == list(getattr(b, arr)[:C]), (L, i, j, k, arr)
+    rng = np.random.default_rng(1)
+    for _ in range(40):
+        x, y, zz = (int(rng.integers(d)) for d in dims)
+        assert [st.value(0, x, y, zz, c) for c in range(C)] == list(vol[zz, y, x])
+    if C == 3:
+        cam = S.orbit_camera(dims, 2.0 * max(dims), 30.0, 20.0, 24, 20, lod_error_px=0.7)
+        tf = S.make_tf([11, 12, 13])
+        nc_a, ca, sa = O.render(dense, cam, tf, [1.0, 1.0, 1.0])
+        nc_b, cb, sb = O.render(st, cam, tf, [1.0, 1.0, 1.0])
+        assert np.array_equal(nc_a, nc_b) and np.array_equal(ca, cb) and np.array_equal(sa, sb)
