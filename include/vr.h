@@ -47,6 +47,7 @@ enum { VR_MODE_DVR = 0, VR_MODE_MIP = 1 };
 /* OR-ed into vr_render's mode: this call interpolates samples and reads the transfer functions in
  * FP16 (normalised intensities), compositing in FP32 -- as if the context had VR_FP16_INTERP. */
 #define VR_RENDER_FP16 0x10
+enum { VR_HOST_BLOCK = 0, VR_DEVICE_BLOCK = 1, VR_HOST_ASYNC = 2 }; /* vr_insert_block on_device */
 #define VR_MAX_CHANNELS 4
 #define VR_MAX_LEVELS 16
 #define VR_MAX_CLIP 3
@@ -118,9 +119,15 @@ vr_status vr_destroy(vr_ctx* ctx);
  * channels interleaved per voxel as in Sec. "Handling Multi-Channel Data").  Already inserted
  * values are overwritten (Sec. "Incremental Construction", step 1); every level on the
  * insertion path is updated by 2x2x2 round-half-up half-sampling (step 2) and the homogeneity
- * flags and AVG values of the touched nodes are refreshed (step 3).  on_device != 0: block is a
- * device pointer; otherwise a host pointer copied by the library (pinned memory makes the copy
- * asynchronous; pageable memory is copied before the call returns).  Stream-ordered.
+ * flags and AVG values of the touched nodes are refreshed (step 3).
+ * on_device: 1 (VR_DEVICE_BLOCK) block is a device pointer; 0 (VR_HOST_BLOCK) a host pointer
+ * copied by the library on cuda_stream (pinned memory makes the copy asynchronous; pageable
+ * memory is copied before the call returns); 2 (VR_HOST_ASYNC) a host pointer whose copy runs on
+ * the library's own upload stream without waiting for earlier work on cuda_stream, so that it
+ * overlaps the rendering already queued there (the paper builds the octree beside the renderer,
+ * Sec. "Incremental Construction"): the block must hold its values at the call and stay unchanged
+ * until cuda_stream has passed this insert; two staging buffers alternate, so at most two such
+ * uploads are in flight.  The updates themselves are ordered on cuda_stream in every mode.
  * Errors: VR_ERR_INVALID_ARG (block outside the volume, NULL block), VR_ERR_OUT_OF_MEMORY (the
  * brick pool is exhausted; nothing is modified), VR_ERR_STATE, VR_ERR_CUDA. */
 vr_status vr_insert_block(vr_ctx* ctx, const int64_t origin[3], const int64_t extent[3], const uint16_t* block,

@@ -40,6 +40,14 @@ struct vr_ctx {
     long long slots_used = 0;
     uint16_t* stage = nullptr;
     size_t stage_bytes = 0;
+    // overlapped host uploads (VR_HOST_ASYNC): two staging buffers filled on the library's own
+    // upload stream; stage_free[b] is recorded on the caller's stream once level 0 has read buffer b
+    cudaStream_t up_stream = nullptr;
+    uint16_t* up_stage[2] = {nullptr, nullptr};
+    size_t up_bytes[2] = {0, 0};
+    cudaEvent_t stage_free[2] = {nullptr, nullptr};
+    cudaEvent_t up_done[2] = {nullptr, nullptr};
+    int up_next = 0;
     SlotInit* d_list = nullptr;
     SlotInit* h_list = nullptr;
     int list_cap = 0;
@@ -137,6 +145,13 @@ static void destroy_all(vr_ctx* c) {
     dfree(c, c->counter);
     dfree(c, c->stats);
     dfree(c, c->stage);
+    if (c->up_stream) cudaStreamSynchronize(c->up_stream);
+    for (int b = 0; b < 2; ++b) {
+        dfree(c, c->up_stage[b]);
+        if (c->stage_free[b]) cudaEventDestroy(c->stage_free[b]);
+        if (c->up_done[b]) cudaEventDestroy(c->up_done[b]);
+    }
+    if (c->up_stream) cudaStreamDestroy(c->up_stream);
     dfree(c, c->d_list);
     dfree(c, c->d_cams);
     if (c->h_list) cudaFreeHost(c->h_list);
@@ -271,7 +286,12 @@ vr_status vr_create(const int64_t dims[3], int channels, int brick_size, const v
         return fail(nullptr, VR_ERR_OUT_OF_MEMORY, "device allocation failed");
     }
     if (cudaEventCreateWithFlags(&c->list_ev, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->cams_ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&c->cams_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->stage_free[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->stage_free[1], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->up_done[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->up_done[1], cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->up_stream, cudaStreamNonBlocking) != cudaSuccess) {
         destroy_all(c);
         return fail(nullptr, VR_ERR_CUDA, "event creation failed");
     }
@@ -308,6 +328,8 @@ vr_status vr_insert_block(vr_ctx* c, const int64_t origin[3], const int64_t exte
     vr_status s = check_ctx(c);
     if (s != VR_OK) return s;
     if (!origin || !extent || !block) return fail(c, VR_ERR_INVALID_ARG, "NULL argument");
+    if (on_device != VR_HOST_BLOCK && on_device != VR_DEVICE_BLOCK && on_device != VR_HOST_ASYNC)
+        return fail(c, VR_ERR_INVALID_ARG, "on_device must be VR_HOST_BLOCK, VR_DEVICE_BLOCK or VR_HOST_ASYNC");
     const Geo& g = c->g;
     for (int a = 0; a < 3; ++a)
         if (origin[a] < 0 || extent[a] <= 0 || origin[a] + extent[a] > g.ldim[0][a])
@@ -331,7 +353,26 @@ vr_status vr_insert_block(vr_ctx* c, const int64_t origin[3], const int64_t exte
     // stage host data
     const uint16_t* src = block;
     const size_t bytes = (size_t)extent[0] * extent[1] * extent[2] * g.C * sizeof(uint16_t);
-    if (!on_device) {
+    int up = -1; // staging buffer of an overlapped upload
+    if (on_device == VR_HOST_ASYNC) {
+        // the copy waits only until level 0 of the insert before last has read this buffer, not
+        // for earlier work on the caller's stream; the caller's stream waits for the copy
+        up = c->up_next;
+        c->up_next ^= 1;
+        if (bytes > c->up_bytes[up]) {
+            CK(c, cudaEventSynchronize(c->stage_free[up]));
+            CK(c, cudaStreamSynchronize(c->up_stream));
+            dfree(c, c->up_stage[up]);
+            c->up_stage[up] = (uint16_t*)dalloc(c, bytes);
+            c->up_bytes[up] = c->up_stage[up] ? bytes : 0;
+            if (!c->up_stage[up]) return fail(c, VR_ERR_OUT_OF_MEMORY, "staging allocation failed");
+        }
+        CK(c, cudaStreamWaitEvent(c->up_stream, c->stage_free[up], 0));
+        CK(c, cudaMemcpyAsync(c->up_stage[up], block, bytes, cudaMemcpyHostToDevice, c->up_stream));
+        CK(c, cudaEventRecord(c->up_done[up], c->up_stream));
+        CK(c, cudaStreamWaitEvent(st, c->up_done[up], 0));
+        src = c->up_stage[up];
+    } else if (!on_device) {
         if (bytes > c->stage_bytes) {
             CK(c, cudaStreamSynchronize(st));
             dfree(c, c->stage);
@@ -374,8 +415,10 @@ vr_status vr_insert_block(vr_ctx* c, const int64_t origin[3], const int64_t exte
         CK(c, launch_slot_init(g, c->pool, c->rn, c->ps, c->d_list, n, st));
     }
     const long long org[3] = {origin[0], origin[1], origin[2]}, ext[3] = {extent[0], extent[1], extent[2]};
-    for (int L = 0; L <= g.N; ++L)
+    for (int L = 0; L <= g.N; ++L) {
         CK(c, launch_level_update(g, L, lo[L], hi[L], src, org, ext, c->pool, c->rn, c->ns, c->ps, c->err, st));
+        if (L == 0 && up >= 0) CK(c, cudaEventRecord(c->stage_free[up], st));
+    }
     if (c->cache_cap > 0) {
         // cached copies of every brick this insert rewrote (interior or border) are stale now
         bool dropped = false;

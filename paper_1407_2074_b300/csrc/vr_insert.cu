@@ -31,6 +31,10 @@ __device__ __forceinline__ uint16_t rhu(unsigned long long S, unsigned long long
     return (uint16_t)((2ull * S + k) / (2ull * k));
 }
 
+// rhu for k = 2^sh children (always the case: k is a product of factors 1 or 2 per axis):
+// floor((2S + k) / (2k)) = (S + k/2) >> sh.  S <= 8 * 65535 keeps everything in 32 bits.
+__device__ __forceinline__ uint32_t rhu_pow2(uint32_t S, uint32_t sh) { return (S + ((1u << sh) >> 1)) >> sh; }
+
 __global__ void init_nodes_kernel(Geo g, RNode* rn, NStat* ns) {
     long long n = g.noff[g.N + 1];
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -158,7 +162,52 @@ __device__ __forceinline__ void block_reduce_stats(uint32_t (&mn)[C], uint32_t (
     __syncthreads();
 }
 
+constexpr int MAX_S = 130; // slot edge for the largest brick (M = 128)
+
+// One position of level L > 0: round-half-up mean of its in-volume children (2x2x2, one child slot).
 template <int C, int VS>
+__device__ __forceinline__ void half_sample(const LevelArgs& a, int L, int x, int y, int z, int msh, uint16_t (&v)[VS]) {
+    const Geo& g = a.g;
+    const int M = g.M, S = g.S;
+    const int cx = 2 * x, cy = 2 * y, cz = 2 * z;
+    const bool hx = cx + 1 < (int)g.ldim[L - 1][0], hy = cy + 1 < (int)g.ldim[L - 1][1],
+               hz = cz + 1 < (int)g.ldim[L - 1][2];
+    const int cbx = msh >= 0 ? cx >> msh : cx / M, cby = msh >= 0 ? cy >> msh : cy / M,
+              cbz = msh >= 0 ? cz >> msh : cz / M;
+    const long long cnid = g.noff[L - 1] + ((long long)cbz * g.nb[L - 1][1] + cby) * g.nb[L - 1][0] + cbx;
+    const int cs = a.rn[cnid].slot;
+    const uint32_t ksh = (uint32_t)hx + (uint32_t)hy + (uint32_t)hz; // k = 2^ksh children
+    if (cs < 0 || cs >= g.n_slots_cap) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) v[c] = g.bg;
+        if (cs >= g.n_slots_cap) atomicOr(a.err, ERR_SLOT_RANGE);
+        return;
+    }
+    const uint16_t* cp = a.pool + (long long)cs * g.slot_elems +
+                         (((cz - cbz * M + 1) * S + (cy - cby * M + 1)) * S + (cx - cbx * M + 1)) * VS;
+    uint32_t sum[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) sum[c] = 0;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const int dx = e & 1, dy = (e >> 1) & 1, dz = e >> 2;
+        if ((dx && !hx) || (dy && !hy) || (dz && !hz)) continue;
+        const uint16_t* q = cp + ((dz * S + dy) * S + dx) * VS;
+        if (VS == 4) {
+            const uint2 w = *reinterpret_cast<const uint2*>(q); // one 8-byte voxel
+            const uint32_t ws[2] = {w.x, w.y};
+#pragma unroll
+            for (int c = 0; c < C; ++c) sum[c] += (c & 1) ? (ws[c >> 1] >> 16) : (ws[c >> 1] & 0xffffu);
+        } else {
+#pragma unroll
+            for (int c = 0; c < C; ++c) sum[c] += q[c];
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c) v[c] = (uint16_t)rhu_pow2(sum[c], ksh);
+}
+
+template <int C, int VS, bool LEVEL0>
 __global__ void __launch_bounds__(256) level_update_kernel(LevelArgs a) {
     const Geo& g = a.g;
     const int L = a.L, M = g.M, S = g.S;
@@ -198,96 +247,109 @@ __global__ void __launch_bounds__(256) level_update_kernel(LevelArgs a) {
         nin[d] = (int)(r < M ? r : M);
     }
     // When the change covers every interior in-volume position of a plane (always for whole
-    // slices) the plane statistics are gathered while writing; otherwise re-read afterwards.
+    // slices) the plane statistics are gathered while writing: per thread, per warp (reduce
+    // instructions), then one shared atomic per warp and plane; otherwise re-read afterwards.
     const bool full_xy = l0[0] <= 1 && l1[0] >= nin[0] && l0[1] <= 1 && l1[1] >= nin[1];
+    const bool gather = interior && full_xy; // uniform in the CTA
+    __shared__ uint32_t s_pmn[MAX_S][C], s_pmx[MAX_S][C], s_psm[MAX_S][C];
+    if (gather) {
+        for (int i = threadIdx.x; i < S * C; i += blockDim.x) {
+            s_pmn[i / C][i % C] = 0xffffu;
+            s_pmx[i / C][i % C] = 0u;
+            s_psm[i / C][i % C] = 0u;
+        }
+        __syncthreads();
+    }
     const int bx0 = (int)(b[0] * M) - 1, by0 = (int)(b[1] * M) - 1, bz0 = (int)(b[2] * M) - 1;
     const int X = (int)g.ldim[L][0], Y = (int)g.ldim[L][1], Z = (int)g.ldim[L][2];
     const int msh = a.mshift; // log2(M) when M is a power of two, else -1
+    // t / nx as a multiply-high: exact because t * nx < S^3 < 2^32
+    const uint32_t mnx = nx > 1 ? (uint32_t)((0x100000000ull + (unsigned)nx - 1) / (unsigned)nx) : 0u;
+    // U positions per thread per round: their loads are issued before any of their stores
+    constexpr int U = LEVEL0 ? 4 : 2;
+    const uint16_t* __restrict__ blk = a.block;
     for (int lz = l0[2]; lz <= l1[2]; ++lz) {
         const int z = clampi(bz0 + lz, 0, Z - 1);
-        const bool stats_here = interior && full_xy && lz >= 1 && lz <= nin[2]; // uniform in the CTA
-        uint32_t mn[C], mx[C];
-        unsigned long long sm[C];
+        const bool stats_here = gather && lz >= 1 && lz <= nin[2]; // uniform in the CTA
+        uint32_t mn[C], mx[C], sm32[C]; // a thread's share of one plane stays below 2^32
 #pragma unroll
         for (int c = 0; c < C; ++c) {
             mn[c] = 0xffffu;
             mx[c] = 0;
-            sm[c] = 0;
+            sm32[c] = 0;
         }
-        for (int t = threadIdx.x; t < np; t += blockDim.x) {
-            const int ty = t / nx;
-            const int lx = l0[0] + (t - ty * nx), ly = l0[1] + ty;
-            const int x = clampi(bx0 + lx, 0, X - 1), y = clampi(by0 + ly, 0, Y - 1);
-            uint16_t v[VS];
+        const uint16_t* src_plane = LEVEL0 ? blk + (long long)(z - a.org[2]) * a.ext[1] * a.ext[0] * C : nullptr;
+        for (int t0 = threadIdx.x; t0 < np; t0 += U * blockDim.x) {
+            uint16_t v[U][VS];
+            int lxs[U], lys[U];
+            bool ok[U];
 #pragma unroll
-            for (int c = 0; c < VS; ++c) v[c] = 0;
-            if (L == 0) {
-                const uint16_t* src =
-                    a.block + ((((long long)(z - a.org[2]) * a.ext[1]) + (y - a.org[1])) * a.ext[0] + (x - a.org[0])) * C;
+            for (int u = 0; u < U; ++u) {
+                const int t = t0 + u * (int)blockDim.x;
+                ok[u] = t < np;
 #pragma unroll
-                for (int c = 0; c < C; ++c) v[c] = src[c];
-            } else {
-                const int cx = 2 * x, cy = 2 * y, cz = 2 * z;
-                const bool hx = cx + 1 < (int)g.ldim[L - 1][0], hy = cy + 1 < (int)g.ldim[L - 1][1],
-                           hz = cz + 1 < (int)g.ldim[L - 1][2];
-                const int cbx = msh >= 0 ? cx >> msh : cx / M, cby = msh >= 0 ? cy >> msh : cy / M,
-                          cbz = msh >= 0 ? cz >> msh : cz / M;
-                const long long cnid = g.noff[L - 1] + ((long long)cbz * g.nb[L - 1][1] + cby) * g.nb[L - 1][0] + cbx;
-                const int cs = a.rn[cnid].slot;
-                const unsigned k = (1u + hx) * (1u + hy) * (1u + hz);
-                if (cs < 0 || cs >= g.n_slots_cap) {
+                for (int c = 0; c < VS; ++c) v[u][c] = 0;
+                const int ty = nx > 1 ? (int)__umulhi((uint32_t)t, mnx) : t;
+                lxs[u] = l0[0] + (t - ty * nx);
+                lys[u] = l0[1] + ty;
+                if (!ok[u]) continue;
+                const int x = clampi(bx0 + lxs[u], 0, X - 1), y = clampi(by0 + lys[u], 0, Y - 1);
+                if (LEVEL0) {
+                    const uint16_t* src = src_plane + ((long long)(y - a.org[1]) * a.ext[0] + (x - a.org[0])) * C;
 #pragma unroll
-                    for (int c = 0; c < C; ++c) v[c] = g.bg;
-                    if (cs >= g.n_slots_cap) atomicOr(a.err, ERR_SLOT_RANGE);
+                    for (int c = 0; c < C; ++c) v[u][c] = src[c];
                 } else {
-                    const uint16_t* cp = a.pool + (long long)cs * g.slot_elems +
-                                         (((cz - cbz * M + 1) * S + (cy - cby * M + 1)) * S + (cx - cbx * M + 1)) * VS;
-                    uint32_t sum[C];
-#pragma unroll
-                    for (int c = 0; c < C; ++c) sum[c] = 0;
-                    for (int dz = 0; dz <= (int)hz; ++dz)
-                        for (int dy = 0; dy <= (int)hy; ++dy)
-                            for (int dx = 0; dx <= (int)hx; ++dx) {
-                                const uint16_t* q = cp + ((dz * S + dy) * S + dx) * VS;
-#pragma unroll
-                                for (int c = 0; c < C; ++c) sum[c] += q[c];
-                            }
-#pragma unroll
-                    for (int c = 0; c < C; ++c) v[c] = rhu(sum[c], k);
+                    half_sample<C, VS>(a, L, x, y, z, msh, v[u]);
                 }
             }
-            uint16_t* d = dst + ((lz * S + ly) * S + lx) * VS;
-            if (VS == 4) {
-                uint2 w;
-                w.x = (uint32_t)v[0] | ((uint32_t)v[VS > 1 ? 1 : 0] << 16);
-                w.y = (uint32_t)v[VS > 2 ? 2 : 0] | ((uint32_t)v[VS > 3 ? 3 : 0] << 16);
-                *reinterpret_cast<uint2*>(d) = w;
-            } else if (VS == 2) {
-                *reinterpret_cast<uint32_t*>(d) = (uint32_t)v[0] | ((uint32_t)v[VS > 1 ? 1 : 0] << 16);
-            } else {
-                d[0] = v[0];
-            }
-            if (stats_here && lx >= 1 && lx <= nin[0] && ly >= 1 && ly <= nin[1]) {
 #pragma unroll
-                for (int c = 0; c < C; ++c) {
-                    mn[c] = min(mn[c], (uint32_t)v[c]);
-                    mx[c] = max(mx[c], (uint32_t)v[c]);
-                    sm[c] += v[c];
+            for (int u = 0; u < U; ++u) {
+                if (!ok[u]) continue;
+                uint16_t* d = dst + ((lz * S + lys[u]) * S + lxs[u]) * VS;
+                if (VS == 4) {
+                    uint2 w;
+                    w.x = (uint32_t)v[u][0] | ((uint32_t)v[u][VS > 1 ? 1 : 0] << 16);
+                    w.y = (uint32_t)v[u][VS > 2 ? 2 : 0] | ((uint32_t)v[u][VS > 3 ? 3 : 0] << 16);
+                    *reinterpret_cast<uint2*>(d) = w;
+                } else if (VS == 2) {
+                    *reinterpret_cast<uint32_t*>(d) = (uint32_t)v[u][0] | ((uint32_t)v[u][VS > 1 ? 1 : 0] << 16);
+                } else {
+                    d[0] = v[u][0];
+                }
+                if (stats_here && lxs[u] >= 1 && lxs[u] <= nin[0] && lys[u] >= 1 && lys[u] <= nin[1]) {
+#pragma unroll
+                    for (int c = 0; c < C; ++c) {
+                        mn[c] = min(mn[c], (uint32_t)v[u][c]);
+                        mx[c] = max(mx[c], (uint32_t)v[u][c]);
+                        sm32[c] += v[u][c];
+                    }
                 }
             }
         }
         if (stats_here) {
-            block_reduce_stats<C>(mn, mx, sm);
-            if (threadIdx.x == 0) {
 #pragma unroll
-                for (int c = 0; c < C; ++c) {
-                    PStat p;
-                    p.mn = (uint16_t)mn[c];
-                    p.mx = (uint16_t)mx[c];
-                    p.sum = (uint32_t)sm[c];
-                    a.ps[((long long)slot * M + (lz - 1)) * C + c] = p;
+            for (int c = 0; c < C; ++c) {
+                const uint32_t wmn = __reduce_min_sync(0xffffffffu, mn[c]);
+                const uint32_t wmx = __reduce_max_sync(0xffffffffu, mx[c]);
+                const uint32_t wsm = __reduce_add_sync(0xffffffffu, sm32[c]);
+                if ((threadIdx.x & 31) == 0) {
+                    atomicMin(&s_pmn[lz][c], wmn);
+                    atomicMax(&s_pmx[lz][c], wmx);
+                    atomicAdd(&s_psm[lz][c], wsm);
                 }
             }
+        }
+    }
+    if (gather) {
+        __syncthreads();
+        const int pz0 = l0[2] > 1 ? l0[2] : 1, pz1 = l1[2] < nin[2] ? l1[2] : nin[2];
+        for (int i = threadIdx.x; i < (pz1 - pz0 + 1) * C; i += blockDim.x) {
+            const int lz = pz0 + i / C, c = i % C;
+            PStat p;
+            p.mn = (uint16_t)s_pmn[lz][c];
+            p.mx = (uint16_t)s_pmx[lz][c];
+            p.sum = s_psm[lz][c];
+            a.ps[((long long)slot * M + (lz - 1)) * C + c] = p;
         }
     }
     if (!interior) return; // only border copies changed: the node's own statistics did not
@@ -405,6 +467,14 @@ __global__ void __launch_bounds__(256) level_update_kernel(LevelArgs a) {
     a.rn[nid] = r;
 }
 
+template <int C, int VS>
+static void launch_level(const LevelArgs& a, bool level0, long long nblocks, cudaStream_t st) {
+    if (level0)
+        level_update_kernel<C, VS, true><<<(unsigned)nblocks, 256, 0, st>>>(a);
+    else
+        level_update_kernel<C, VS, false><<<(unsigned)nblocks, 256, 0, st>>>(a);
+}
+
 cudaError_t launch_level_update(const Geo& g, int L, const long long lo[3], const long long hi[3],
                                 const uint16_t* block, const long long org[3], const long long ext[3], uint16_t* pool,
                                 RNode* rn, NStat* ns, PStat* ps, int* err, cudaStream_t st) {
@@ -439,10 +509,10 @@ cudaError_t launch_level_update(const Geo& g, int L, const long long lo[3], cons
     if (nblocks <= 0) return cudaSuccess;
     if (nblocks > 0x7fffffffLL) return cudaErrorInvalidValue;
     switch (g.C) {
-        case 1: level_update_kernel<1, 1><<<(unsigned)nblocks, 256, 0, st>>>(a); break;
-        case 2: level_update_kernel<2, 2><<<(unsigned)nblocks, 256, 0, st>>>(a); break;
-        case 3: level_update_kernel<3, 4><<<(unsigned)nblocks, 256, 0, st>>>(a); break;
-        default: level_update_kernel<4, 4><<<(unsigned)nblocks, 256, 0, st>>>(a); break;
+        case 1: launch_level<1, 1>(a, L == 0, nblocks, st); break;
+        case 2: launch_level<2, 2>(a, L == 0, nblocks, st); break;
+        case 3: launch_level<3, 4>(a, L == 0, nblocks, st); break;
+        default: launch_level<4, 4>(a, L == 0, nblocks, st); break;
     }
     return cudaGetLastError();
 }

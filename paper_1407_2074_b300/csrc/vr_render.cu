@@ -92,6 +92,11 @@ __device__ __forceinline__ void opacity(float al, float ell, float& a, float& om
     }
 }
 
+// A uint16 voxel value h as the float 2^23 + h (exponent bits or'ed in, no conversion).  Sums and
+// differences of such values are exact, so only the constant term of a cell removes the offset.
+constexpr float VBIAS = 8388608.0f;
+__device__ __forceinline__ float biased(uint32_t h) { return __uint_as_float(0x4B000000u | h); }
+
 constexpr float ALPHA_MAX = 1.0f - 1e-6f;
 constexpr int MAX_SAMPLES = 1 << 24; // (float)k stays exact; bounds every ray
 
@@ -257,7 +262,7 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
             int i0[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                const float u = __fsub_rn(__fmul_rn(p[a], inv_vox), off[a]);
+                const float u = fmaf(p[a], inv_vox, -off[a]); // == (p * 2^-L) - off: the product is exact
                 const float fl = floorf(u);
                 int ii = (int)fl;
                 fr[a] = __fsub_rn(u, fl);
@@ -271,23 +276,26 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     const uint16_t* v = cp0 + ((long long)(((q >> 2) & 1) * S + ((q >> 1) & 1)) * S + (q & 1)) * VS;
+                    // corner values as 2^23 + value (see biased())
                     if (VS == 4) {
                         const uint2 w = __ldg(reinterpret_cast<const uint2*>(v));
                         const uint32_t ws[2] = {w.x, w.y};
 #pragma unroll
-                        for (int c = 0; c < C; ++c) cv[q][c] = (float)((ws[c >> 1] >> (16 * (c & 1))) & 0xffffu);
+                        for (int c = 0; c < C; ++c)
+                            cv[q][c] = biased((c & 1) ? (ws[c >> 1] >> 16) : (ws[c >> 1] & 0xffffu));
                     } else if (VS == 2) {
                         const uint32_t w = __ldg(reinterpret_cast<const unsigned int*>(v));
 #pragma unroll
-                        for (int c = 0; c < C; ++c) cv[q][c] = (float)((w >> (16 * c)) & 0xffffu);
+                        for (int c = 0; c < C; ++c) cv[q][c] = biased(c ? (w >> 16) : (w & 0xffffu));
                     } else {
-                        cv[q][0] = (float)__ldg(reinterpret_cast<const unsigned short*>(v));
+                        cv[q][0] = biased(__ldg(reinterpret_cast<const unsigned short*>(v)));
                     }
                     if (H) {
                         constexpr float inv = 1.0f / 65535.0f;
 #pragma unroll
                         for (int j = 0; j < CP; ++j)
-                            hv[q][j] = __floats2half2_rn(cv[q][2 * j] * inv, (2 * j + 1 < C) ? cv[q][2 * j + 1] * inv : 0.0f);
+                            hv[q][j] = __floats2half2_rn((cv[q][2 * j] - VBIAS) * inv,
+                                                         (2 * j + 1 < C) ? (cv[q][2 * j + 1] - VBIAS) * inv : 0.0f);
                     }
                 }
                 if (!H) {
@@ -298,6 +306,7 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
                     for (int c = 0; c < C; ++c) {
                         const float v0 = cv[0][c], v1 = cv[1][c], v2 = cv[2][c], v3 = cv[3][c];
                         const float v4 = cv[4][c], v5 = cv[5][c], v6 = cv[6][c], v7 = cv[7][c];
+                        cv[0][c] = v0 - VBIAS;
                         cv[1][c] = v1 - v0;
                         cv[2][c] = v2 - v0;
                         cv[4][c] = v4 - v0;
@@ -512,7 +521,7 @@ __device__ __forceinline__ long long march_xf(const Geo& g, const uint16_t* __re
                 int i0[3];
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    const float u = __fsub_rn(__fmul_rn(q[a], inv_vox[c]), off[c][a]);
+                    const float u = fmaf(q[a], inv_vox[c], -off[c][a]); // exact product, one rounding
                     const float fl = floorf(u);
                     const int ii = (int)fl;
                     fr[a] = __fsub_rn(u, fl);
@@ -524,8 +533,8 @@ __device__ __forceinline__ long long march_xf(const Geo& g, const uint16_t* __re
                     float v[8];
 #pragma unroll
                     for (int e = 0; e < 8; ++e)
-                        v[e] = (float)__ldg(sbase[c] + coff + ((((e >> 2) & 1) * S + ((e >> 1) & 1)) * S + (e & 1)) * VS + c);
-                    cv[c][0] = v[0];
+                        v[e] = biased(__ldg(sbase[c] + coff + ((((e >> 2) & 1) * S + ((e >> 1) & 1)) * S + (e & 1)) * VS + c));
+                    cv[c][0] = v[0] - VBIAS;
                     cv[c][1] = v[1] - v[0];
                     cv[c][2] = v[2] - v[0];
                     cv[c][4] = v[4] - v[0];

@@ -17,6 +17,7 @@ VR_OK, VR_ERR_INVALID_ARG, VR_ERR_OUT_OF_MEMORY, VR_ERR_CUDA, VR_ERR_STATE, VR_E
 VR_FP32, VR_FP16_INTERP = 0, 1
 VR_MODE_DVR, VR_MODE_MIP = 0, 1
 VR_RENDER_FP16 = 0x10
+VR_HOST_BLOCK, VR_DEVICE_BLOCK, VR_HOST_ASYNC = 0, 1, 2  # vr_insert_block on_device
 F_CHILDREN, F_BRICK, F_TOUCHED = 1, 2, 4
 
 
@@ -170,8 +171,11 @@ class Renderer:
         return self._ctx
 
     # ---- construction ----
-    def insert_block(self, origin, block, stream=None):
-        """block: [ez][ey][ex][C] uint16, a CUDA tensor (device) or a numpy array / CPU tensor (host)."""
+    def insert_block(self, origin, block, stream=None, overlap=False):
+        """block: [ez][ey][ex][C] uint16, a CUDA tensor (device) or a numpy array / CPU tensor (host).
+        overlap=True (host blocks): the upload runs on the library's upload stream beside the work
+        already queued on `stream` (VR_HOST_ASYNC); keep the block unchanged until `stream` has
+        passed this insert."""
         import torch
 
         ext = None
@@ -186,7 +190,7 @@ class Renderer:
                 b = b.view(np.uint16)  # same bytes; keeps pinned host memory pinned
             b = np.ascontiguousarray(b, dtype=np.uint16)
             ext = (b.shape[2], b.shape[1], b.shape[0])
-            ptr, on_dev, keep = b.ctypes.data, 0, b
+            ptr, on_dev, keep = b.ctypes.data, (VR_HOST_ASYNC if overlap else 0), b
         self._check(lib().vr_insert_block(self._ctx, (ctypes.c_int64 * 3)(*origin), (ctypes.c_int64 * 3)(*ext),
                                           ctypes.c_void_p(ptr), on_dev, ctypes.c_void_p(_stream_ptr(stream))))
         return keep

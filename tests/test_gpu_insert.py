@@ -84,6 +84,38 @@ def test_random_order_blocks_and_overwrites(C, M, dims):
     _compare_state(r, oracle_dense(vol, M, bg=123, tau=600))
 
 
+def test_overlapped_host_uploads_interleaved_with_renders():
+    """VR_HOST_ASYNC: pinned host blocks of changing sizes uploaded on the library's upload
+    stream while renders are queued between the inserts; the state equals the oracle's."""
+    import ctypes
+
+    import torch
+    from paper_1407_2074_b300 import vr as V
+
+    w = S.tiny()
+    vol = w.spec().volume()
+    r = _renderer(w.dims, 3, 16, tau=2000)
+    r.set_transfer_functions(torch.from_numpy(w.tf()).cuda(), torch.ones(3, device="cuda"))
+    cam = dict(w.cameras[0])
+    img = torch.empty((cam["height"], cam["width"], 4), device="cuda")
+    keep = []
+    z = 0
+    for n in (1, 4, 2, 8, 3, 16, 5, 25):  # staging buffers grow and alternate
+        h = torch.empty((n, 64, 64, 3), dtype=torch.int16, pin_memory=True)
+        h.numpy()[:] = vol[z:z + n].view(np.int16)
+        keep.append((h, r.insert_block((0, 0, z), h.numpy(), overlap=True)))
+        r.render([cam], [img])
+        z += n
+    assert z == 64
+    torch.cuda.synchronize()
+    _compare_state(r, oracle_dense(vol, 16, tau=2000))
+    blk = np.zeros((1, 2, 2, 3), np.uint16)
+    st = r._ctx
+    with pytest.raises(V.VRError):
+        r._check(V.lib().vr_insert_block(st, (ctypes.c_int64 * 3)(0, 0, 0), (ctypes.c_int64 * 3)(2, 2, 1),
+                                         ctypes.c_void_p(blk.ctypes.data), 3, None))
+
+
 def test_pool_exhaustion_status():
     from paper_1407_2074_b300 import vr as V
 
@@ -127,7 +159,7 @@ def test_streamed_full_size_sampled_bricks():
         spec.generate_device(buf.data_ptr(), z0, z0 + 8, st)
         r.insert_block((0, 0, z0), buf)
     torch.cuda.synchronize()
-    lazy = O.LazyVolume(w.dims, 3, 32, spec.voxel_fn, spec.handle, 0, Z, tau=0)
+    lazy = O.LazyVolume(w.dims, 3, 32, spec.voxel_fn, spec.handle, 0, Z, tau=0, owner=spec)
     rng = np.random.default_rng(11)
     for L in range(lazy.N + 1):
         dims_L = lazy.level_dims(L)
