@@ -11,7 +11,7 @@
 //              node without children; the node is cached until the sample leaves its box or L*
 //              rises above its level;
 //   intensity  AVG of a brick-less node, else trilinear inside the node's slot (the border
-//              voxels make the eight corners one slot); the eight corners are cached per cell;
+//              voxels make the eight corners one slot), corners re-read at every sample;
 //   TF         x = sat(I s / 65535), entry i = min(floor(255 x), 254), linear (smem table);
 //   composite  a = 1 - (1 - alpha)^l, C += (1 - A) a rgb, A += (1 - A) a per channel in order;
 //   ERT        stop once A >= ert after a sample.
@@ -148,8 +148,9 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
     float avg[C];
     float off[3] = {0, 0, 0};
     float inv_vox = 1.0f;
-    // cell cache (offset of the cached cell's first corner inside the slot, -1 = none)
-    int cell = -1;
+    // the eight corners of the sample's cell, re-read at every sample (L1 hits).  A per-lane cell
+    // cache made the reload a branch that some lane of the warp takes at almost every sample
+    // (lanes enter new cells at different samples), which cost more than the loads it saved.
     float cv[8][C];
     constexpr int CP = (C + 1) / 2;
     __half2 hv[8][CP];
@@ -224,7 +225,6 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
             sbase = brick ? pool + (long long)nd.slot * g.slot_elems : nullptr;
 #pragma unroll
             for (int c = 0; c < C; ++c) avg[c] = (float)nd.avg[c];
-            cell = -1;
             if (ca && brick) {
                 const long long nid = g.noff[lev] + ((long long)idx[2] * g.nb[lev][1] + idx[1]) * g.nb[lev][0] + idx[0];
                 const int cs = ca->cslot[nid];
@@ -269,8 +269,7 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
                 i0[a] = ii < 0 ? 0 : (ii > M ? M : ii);
             }
             const int coff = ((i0[2] * S + i0[1]) * S + i0[0]) * VS;
-            if (coff != cell) {
-                cell = coff;
+            {
                 const uint16_t* cp0 = sbase + coff;
                 f.on_cell(g, nlev, cidx, i0);
 #pragma unroll
