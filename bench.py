@@ -325,11 +325,24 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--fp16", type=int, default=1, help="also time the FP16-interpolation render")
     ap.add_argument("--suite", type=int, default=1, help="also run the batched and differentiable legs")
+    ap.add_argument("--leg", choices=["batched", "adjoint", "out_of_core"],
+                    help="run only this secondary leg and print its JSON (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.leg:
+        import torch
+        import __graft_entry__
+
+        __graft_entry__.build_all(import_package=True)
+        import paper_1407_2074_b300 as vr
+        from synth import synth as S
+
+        fn = {"batched": batched_leg, "adjoint": adjoint_leg, "out_of_core": table1_leg}[args.leg]
+        print(json.dumps({args.leg: fn(torch, vr, S)}), flush=True)
         return
 
     import torch

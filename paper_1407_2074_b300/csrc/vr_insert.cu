@@ -207,8 +207,8 @@ __device__ __forceinline__ void half_sample(const LevelArgs& a, int L, int x, in
     for (int c = 0; c < C; ++c) v[c] = (uint16_t)rhu_pow2(sum[c], ksh);
 }
 
-template <int C, int VS, bool LEVEL0>
-__global__ void __launch_bounds__(256) level_update_kernel(LevelArgs a) {
+template <int C, int VS, bool LEVEL0, bool WIDE = false>
+__global__ void __launch_bounds__(WIDE ? 1024 : 256) level_update_kernel(LevelArgs a) {
     const Geo& g = a.g;
     const int L = a.L, M = g.M, S = g.S;
     long long bb = blockIdx.x;
@@ -469,10 +469,16 @@ __global__ void __launch_bounds__(256) level_update_kernel(LevelArgs a) {
 
 template <int C, int VS>
 static void launch_level(const LevelArgs& a, bool level0, long long nblocks, cudaStream_t st) {
-    if (level0)
+    if (level0) {
         level_update_kernel<C, VS, true><<<(unsigned)nblocks, 256, 0, st>>>(a);
-    else
-        level_update_kernel<C, VS, false><<<(unsigned)nblocks, 256, 0, st>>>(a);
+    } else {
+        // the upper levels have a few slots only: wider CTAs shorten each slot's chain of
+        // dependent loads (child slot, then children) instead of leaving SMs idle
+        if (nblocks < 2 * 148)
+            level_update_kernel<C, VS, false, true><<<(unsigned)nblocks, 1024, 0, st>>>(a);
+        else
+            level_update_kernel<C, VS, false><<<(unsigned)nblocks, 256, 0, st>>>(a);
+    }
 }
 
 cudaError_t launch_level_update(const Geo& g, int L, const long long lo[3], const long long hi[3],
