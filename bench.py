@@ -508,11 +508,24 @@ def main():
             "traffic": None, "kernel": "render_kernel<3,4,DVR>", "algorithmic_bytes_per_launch": U,
             "peak_kind": peak_kind, "algorithmic_bytes_frames": len(fp),
             "distinct_voxels_per_level_first_frame": vox, "distinct_nodes_first_frame": nodes}
-    tr = os.path.join(ROOT, "profiles", f"render_{args.workload}_traffic.json")
+    # DRAM traffic and executed instructions of the same kernel from one ncu capture (one pass per
+    # launch, orbit frames 0-5), valid while the render sources are unchanged
+    issue = None
+    tr = os.path.join(ROOT, "profiles", f"render_{args.workload}_counters.json")
     if os.path.exists(tr):
         d = json.load(open(tr))
         if d.get("source_hash") == source_hash():
             roof["traffic"] = d.get("traffic_bytes_per_launch")
+            fr = d.get("frames", [])
+            if fr and all(f in samples_of for f in fr):
+                # instructions per composited sample on the captured frames, at the live sample rate
+                ips = sum(d["thread_instructions_per_frame"]) / sum(samples_of[f] for f in fr)
+                mhz = clk.summary().get("sm_mhz") or 2032.0
+                ipeak = 148 * 4 * 32 * mhz * 1e6 / 1e12
+                ach = ips * (samples / args.steps / ws) / (render_ms / 1e3) / 1e12
+                issue = {"bound": "issue", "achieved": ach, "peak": ipeak, "unit": "T thread-instructions/s",
+                         "frac": ach / ipeak, "thread_instructions_per_sample": ips,
+                         "peak_from": "148 SMs x 4 schedulers x 32 lanes x median SM clock"}
 
     batched = adjoint = table1 = None
     if args.suite and rank == 0:
@@ -542,7 +555,7 @@ def main():
                                     "achieved": ins_bytes / (insert_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                                     "frac": ins_bytes / (insert_ms / 1e3) / 1e9 / peak},
                 "samples_per_frame": samples / args.steps / ws, "build_s_full_volume": build_s,
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp16": fp16,
+                "roofline": roof, "issue_roofline": issue, "cpu_baseline": cpu, "e2e": e2e, "fp16": fp16,
                 "batched": batched, "adjoint": adjoint, "out_of_core": table1,
                 "gpu_launches": launches_per_step * args.steps, "clocks": clk.summary()}
         print(json.dumps(line), flush=True)

@@ -739,6 +739,16 @@ struct MIPMax : NoHooks {
     }
 };
 
+// Pixel of a lane in tile lt of its camera: tiles in raster order, tile_w x tile_h lanes (both
+// powers of two, tile_w * tile_h = 32); 32-bit index arithmetic (a camera has < 2^31 tiles).
+__device__ __forceinline__ void tile_pixel(long long lt, int tiles_x, int tile_w, int tile_h, int lane, int& px, int& py) {
+    const unsigned t = (unsigned)lt, tx = (unsigned)tiles_x;
+    const unsigned row = t / tx;
+    const int sh = __ffs(tile_w) - 1;
+    px = (int)(t - row * tx) * tile_w + (lane & (tile_w - 1));
+    py = (int)row * tile_h + (lane >> sh);
+}
+
 __device__ __forceinline__ int find_camera(const CamParam* __restrict__ cams, int n, long long tile) {
     int lo = 0, hi = n - 1;
     while (lo < hi) {
@@ -800,8 +810,8 @@ __global__ void __launch_bounds__(256, VR_RENDER_MIN_CTAS) render_kernel(RenderA
         const int ci = find_camera(a.cams, a.n_cams, (long long)tile);
         const CamParam* cp = &a.cams[ci];
         const long long lt = (long long)tile - cp->tile_begin;
-        const int px = (int)(lt % cp->tiles_x) * a.tile_w + lane % a.tile_w;
-        const int py = (int)(lt / cp->tiles_x) * a.tile_h + lane / a.tile_w;
+        int px, py;
+        tile_pixel(lt, cp->tiles_x, a.tile_w, a.tile_h, lane, px, py);
         if (px >= cp->W || py >= cp->H) continue;
         float dd[3], r0, r1;
         float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -958,8 +968,8 @@ __global__ void __launch_bounds__(128, 3) render_backward_kernel(RenderArgs a) {
         const int ci = find_camera(a.cams, a.n_cams, tile);
         const CamParam& cp = a.cams[ci];
         const long long lt = (long long)tile - cp.tile_begin;
-        const int px = (int)(lt % cp.tiles_x) * a.tile_w + lane % a.tile_w;
-        const int py = (int)(lt / cp.tiles_x) * a.tile_h + lane / a.tile_w;
+        int px, py;
+        tile_pixel(lt, cp.tiles_x, a.tile_w, a.tile_h, lane, px, py);
         if (px >= cp.W || py >= cp.H) continue;
         float d[3], t0, t1;
         if (!ray_setup(cp, a.g, px, py, d, t0, t1)) continue;
@@ -1024,8 +1034,8 @@ __global__ void __launch_bounds__(256, VR_RENDER_MIN_CTAS) refine_kernel(RenderA
         tile = __shfl_sync(0xffffffffu, tile, 0);
         if ((long long)tile >= a.total_tiles) break;
         const long long lt = (long long)tile;
-        const int px = (int)(lt % cp->tiles_x) * a.tile_w + lane % a.tile_w;
-        const int py = (int)(lt / cp->tiles_x) * a.tile_h + lane / a.tile_w;
+        int px, py;
+        tile_pixel(lt, cp->tiles_x, a.tile_w, a.tile_h, lane, px, py);
         if (px >= cp->W || py >= cp->H) continue;
         const long long pix = (long long)py * cp->W + px;
         RefineState st = a.refine_state[pix];
