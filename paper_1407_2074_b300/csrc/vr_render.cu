@@ -148,12 +148,58 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
     float avg[C];
     float off[3] = {0, 0, 0};
     float inv_vox = 1.0f;
-    // the eight corners of the sample's cell, re-read at every sample (L1 hits).  A per-lane cell
-    // cache made the reload a branch that some lane of the warp takes at almost every sample
-    // (lanes enter new cells at different samples), which cost more than the loads it saved.
-    float cv[8][C];
     constexpr int CP = (C + 1) / 2;
     __half2 hv[8][CP];
+    // FP32 trilinear at position pp inside the cached node's brick.  The eight corners of the cell
+    // are re-read at every sample (L1 hits): a per-lane cell cache made the reload a branch that
+    // some lane of the warp takes at almost every sample (lanes enter new cells at different
+    // samples), which cost more than the loads it saved.  Corners are 2^23 + value (biased()), so
+    // the polynomial coefficients are exact differences and only the constant term drops 2^23:
+    //   I = k0 + kx fx + ky fy + kz fz + kxy fx fy + kxz fx fz + kyz fy fz + kxyz fx fy fz
+    auto trilinear = [&](const float (&pp)[3], float (&out)[C]) {
+        float fr[3];
+        int i0[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float u = fmaf(pp[a], inv_vox, -off[a]);
+            const float fl = floorf(u);
+            int ii = (int)fl;
+            fr[a] = __fsub_rn(u, fl);
+            i0[a] = ii < 0 ? 0 : (ii > M ? M : ii);
+        }
+        const uint16_t* cp0 = sbase + ((i0[2] * S + i0[1]) * S + i0[0]) * VS;
+        f.on_cell(g, nlev, cidx, i0);
+        float w[8][C];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const uint16_t* v = cp0 + ((long long)(((q >> 2) & 1) * S + ((q >> 1) & 1)) * S + (q & 1)) * VS;
+            if (VS == 4) {
+                const uint2 x = __ldg(reinterpret_cast<const uint2*>(v));
+                const uint32_t ws[2] = {x.x, x.y};
+#pragma unroll
+                for (int c = 0; c < C; ++c) w[q][c] = biased((c & 1) ? (ws[c >> 1] >> 16) : (ws[c >> 1] & 0xffffu));
+            } else if (VS == 2) {
+                const uint32_t x = __ldg(reinterpret_cast<const unsigned int*>(v));
+#pragma unroll
+                for (int c = 0; c < C; ++c) w[q][c] = biased(c ? (x >> 16) : (x & 0xffffu));
+            } else {
+                w[q][0] = biased(__ldg(reinterpret_cast<const unsigned short*>(v)));
+            }
+        }
+        const float fxy = fr[0] * fr[1], fxz = fr[0] * fr[2], fyz = fr[1] * fr[2], fxyz = fxy * fr[2];
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const float v0 = w[0][c], v1 = w[1][c], v2 = w[2][c], v3 = w[3][c];
+            const float v4 = w[4][c], v5 = w[5][c], v6 = w[6][c], v7 = w[7][c];
+            float v = fmaf(fr[0], v1 - v0, v0 - VBIAS);
+            v = fmaf(fr[1], v2 - v0, v);
+            v = fmaf(fr[2], v4 - v0, v);
+            v = fmaf(fxy, (v3 - v2) - (v1 - v0), v);
+            v = fmaf(fxz, (v5 - v4) - (v1 - v0), v);
+            v = fmaf(fyz, (v6 - v4) - (v2 - v0), v);
+            out[c] = fmaf(fxyz, ((v7 - v6) - (v5 - v4)) - ((v3 - v2) - (v1 - v0)), v);
+        }
+    };
     int k = k0;
     float kf = (float)k0; // == (float)k, exact below 2^24
     for (;; ++k, kf += 1.0f) {
@@ -256,8 +302,53 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
                 }
             }
         }
+        if constexpr (F::kPairs && !H) {
+            // two consecutive samples in the same brick node (same level, full segments): both
+            // intensities, TF lookups and opacities are computed before the two are composited in
+            // order, so the gathers and lookups of the second overlap those of the first
+            if (brick && ell == dt && k + 1 < MAX_SAMPLES) {
+                const float kf2 = kf + 1.0f;
+                const float tk2 = __fadd_rn(t0, __fmul_rn(kf2, dt));
+                if (tk2 < t1 && __fsub_rn(t1, tk2) >= dt && tk2 < tnext && tk2 < tl_limit) {
+                    float p2[3];
+                    bool in = true;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) p2[a] = __fadd_rn(cp.eye[a], __fmul_rn(tk2, d[a]));
+                    if (POW2) {
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) in = in && ((p2[a] < bnd[a]) != neg[a]);
+                    } else {
+                        const float size = (float)(M << nlev);
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            int q = (int)floorf(__fdiv_rn(p2[a], size));
+                            const int qm = (int)g.nb[nlev][a] - 1;
+                            q = q < 0 ? 0 : (q > qm ? qm : q);
+                            in = in && (q == cidx[a]);
+                        }
+                    }
+                    if (in) {
+                        float I1[C], I2[C];
+                        trilinear(p, I1);
+                        trilinear(p2, I2);
+                        const int st = f.sample2(I1, I2, dt);
+                        ++k;
+                        if (st == 1) break;
+                        kf = kf2;
+                        if (st == 2) {
+                            ++k;
+                            break;
+                        }
+                        continue;
+                    }
+                }
+            }
+        }
         float I[C];
-        if (brick) {
+        if (brick && !H) {
+            trilinear(p, I);
+        } else if (brick) {
+            // FP16: corners cached as normalised half pairs, interpolated in half2
             float fr[3];
             int i0[3];
 #pragma unroll
@@ -268,80 +359,41 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
                 fr[a] = __fsub_rn(u, fl);
                 i0[a] = ii < 0 ? 0 : (ii > M ? M : ii);
             }
-            const int coff = ((i0[2] * S + i0[1]) * S + i0[0]) * VS;
-            {
-                const uint16_t* cp0 = sbase + coff;
-                f.on_cell(g, nlev, cidx, i0);
+            const uint16_t* cp0 = sbase + ((i0[2] * S + i0[1]) * S + i0[0]) * VS;
+            f.on_cell(g, nlev, cidx, i0);
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const uint16_t* v = cp0 + ((long long)(((q >> 2) & 1) * S + ((q >> 1) & 1)) * S + (q & 1)) * VS;
-                    // corner values as 2^23 + value (see biased())
-                    if (VS == 4) {
-                        const uint2 w = __ldg(reinterpret_cast<const uint2*>(v));
-                        const uint32_t ws[2] = {w.x, w.y};
+            for (int q = 0; q < 8; ++q) {
+                const uint16_t* v = cp0 + ((long long)(((q >> 2) & 1) * S + ((q >> 1) & 1)) * S + (q & 1)) * VS;
+                float cv[C];
+                if (VS == 4) {
+                    const uint2 w = __ldg(reinterpret_cast<const uint2*>(v));
+                    const uint32_t ws[2] = {w.x, w.y};
 #pragma unroll
-                        for (int c = 0; c < C; ++c)
-                            cv[q][c] = biased((c & 1) ? (ws[c >> 1] >> 16) : (ws[c >> 1] & 0xffffu));
-                    } else if (VS == 2) {
-                        const uint32_t w = __ldg(reinterpret_cast<const unsigned int*>(v));
+                    for (int c = 0; c < C; ++c) cv[c] = (float)((c & 1) ? (ws[c >> 1] >> 16) : (ws[c >> 1] & 0xffffu));
+                } else if (VS == 2) {
+                    const uint32_t w = __ldg(reinterpret_cast<const unsigned int*>(v));
 #pragma unroll
-                        for (int c = 0; c < C; ++c) cv[q][c] = biased(c ? (w >> 16) : (w & 0xffffu));
-                    } else {
-                        cv[q][0] = biased(__ldg(reinterpret_cast<const unsigned short*>(v)));
-                    }
-                    if (H) {
-                        constexpr float inv = 1.0f / 65535.0f;
-#pragma unroll
-                        for (int j = 0; j < CP; ++j)
-                            hv[q][j] = __floats2half2_rn((cv[q][2 * j] - VBIAS) * inv,
-                                                         (2 * j + 1 < C) ? (cv[q][2 * j + 1] - VBIAS) * inv : 0.0f);
-                    }
+                    for (int c = 0; c < C; ++c) cv[c] = (float)(c ? (w >> 16) : (w & 0xffffu));
+                } else {
+                    cv[0] = (float)__ldg(reinterpret_cast<const unsigned short*>(v));
                 }
-                if (!H) {
-                    // trilinear as a polynomial in (fx, fy, fz); integer corners make every
-                    // coefficient exact: I = k0 + kx fx + ky fy + kz fz + kxy fx fy + kxz fx fz
-                    //                        + kyz fy fz + kxyz fx fy fz
+                constexpr float inv = 1.0f / 65535.0f;
 #pragma unroll
-                    for (int c = 0; c < C; ++c) {
-                        const float v0 = cv[0][c], v1 = cv[1][c], v2 = cv[2][c], v3 = cv[3][c];
-                        const float v4 = cv[4][c], v5 = cv[5][c], v6 = cv[6][c], v7 = cv[7][c];
-                        cv[0][c] = v0 - VBIAS;
-                        cv[1][c] = v1 - v0;
-                        cv[2][c] = v2 - v0;
-                        cv[4][c] = v4 - v0;
-                        cv[3][c] = (v3 - v2) - (v1 - v0);
-                        cv[5][c] = (v5 - v4) - (v1 - v0);
-                        cv[6][c] = (v6 - v4) - (v2 - v0);
-                        cv[7][c] = ((v7 - v6) - (v5 - v4)) - ((v3 - v2) - (v1 - v0));
-                    }
-                }
+                for (int j = 0; j < CP; ++j)
+                    hv[q][j] = __floats2half2_rn(cv[2 * j] * inv, (2 * j + 1 < C) ? cv[2 * j + 1] * inv : 0.0f);
             }
-            if (H) {
-                const __half2 fx = __float2half2_rn(fr[0]), fy = __float2half2_rn(fr[1]), fz = __float2half2_rn(fr[2]);
+            const __half2 fx = __float2half2_rn(fr[0]), fy = __float2half2_rn(fr[1]), fz = __float2half2_rn(fr[2]);
 #pragma unroll
-                for (int j = 0; j < CP; ++j) {
-                    const __half2 c00 = __hfma2(fx, __hsub2(hv[1][j], hv[0][j]), hv[0][j]);
-                    const __half2 c10 = __hfma2(fx, __hsub2(hv[3][j], hv[2][j]), hv[2][j]);
-                    const __half2 c01 = __hfma2(fx, __hsub2(hv[5][j], hv[4][j]), hv[4][j]);
-                    const __half2 c11 = __hfma2(fx, __hsub2(hv[7][j], hv[6][j]), hv[6][j]);
-                    const __half2 c0 = __hfma2(fy, __hsub2(c10, c00), c00);
-                    const __half2 c1 = __hfma2(fy, __hsub2(c11, c01), c01);
-                    const float2 r = __half22float2(__hfma2(fz, __hsub2(c1, c0), c0));
-                    I[2 * j] = r.x;
-                    if (2 * j + 1 < C) I[2 * j + 1] = r.y;
-                }
-            } else {
-                const float fxy = fr[0] * fr[1], fxz = fr[0] * fr[2], fyz = fr[1] * fr[2], fxyz = fxy * fr[2];
-#pragma unroll
-                for (int c = 0; c < C; ++c) {
-                    float v = fmaf(fr[0], cv[1][c], cv[0][c]);
-                    v = fmaf(fr[1], cv[2][c], v);
-                    v = fmaf(fr[2], cv[4][c], v);
-                    v = fmaf(fxy, cv[3][c], v);
-                    v = fmaf(fxz, cv[5][c], v);
-                    v = fmaf(fyz, cv[6][c], v);
-                    I[c] = fmaf(fxyz, cv[7][c], v);
-                }
+            for (int j = 0; j < CP; ++j) {
+                const __half2 c00 = __hfma2(fx, __hsub2(hv[1][j], hv[0][j]), hv[0][j]);
+                const __half2 c10 = __hfma2(fx, __hsub2(hv[3][j], hv[2][j]), hv[2][j]);
+                const __half2 c01 = __hfma2(fx, __hsub2(hv[5][j], hv[4][j]), hv[4][j]);
+                const __half2 c11 = __hfma2(fx, __hsub2(hv[7][j], hv[6][j]), hv[6][j]);
+                const __half2 c0 = __hfma2(fy, __hsub2(c10, c00), c00);
+                const __half2 c1 = __hfma2(fy, __hsub2(c11, c01), c01);
+                const float2 r = __half22float2(__hfma2(fz, __hsub2(c1, c0), c0));
+                I[2 * j] = r.x;
+                if (2 * j + 1 < C) I[2 * j + 1] = r.y;
             }
         } else {
 #pragma unroll
@@ -563,6 +615,7 @@ __device__ __forceinline__ long long march_xf(const Geo& g, const uint16_t* __re
 
 struct NoHooks {
     static constexpr bool kRuns = false; // composites runs of equal samples in closed form
+    static constexpr bool kPairs = false; // has sample2 (two samples shaded together)
     __device__ __forceinline__ void on_node(long long) {}
     __device__ __forceinline__ void on_cell(const Geo&, int, const int*, const int*) {}
 };
@@ -616,6 +669,39 @@ struct DVRComposite : NoHooks {
             lnq += ell * log1pf(-al);
         }
         return composite_run(lnq, K, n, ert, A, Cr, Cg, Cb, stop);
+    }
+    // Two full-segment samples: shading of both first, then compositing in order.  Returns 1 when
+    // the first sample terminates the ray (the second is dropped), 2 when the second does, else 0.
+    static constexpr bool kPairs = RUNS;
+    __device__ __forceinline__ int sample2(const float (&I1)[C], const float (&I2)[C], float ell) {
+        float r[2][C], gg[2][C], b[2][C], a[2][C], om[2][C];
+#pragma unroll
+        for (int s2 = 0; s2 < 2; ++s2)
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                TFLookup<C> t;
+                t.eval(s_tf, s_scl, c, s2 ? I2[c] : I1[c]);
+                const float al = fminf(fmaxf(t.al, 0.0f), ALPHA_MAX);
+                opacity(al, ell, a[s2][c], om[s2][c]);
+                r[s2][c] = t.r;
+                gg[s2][c] = t.g;
+                b[s2][c] = t.b;
+            }
+        float T = 1.0f - A;
+#pragma unroll
+        for (int s2 = 0; s2 < 2; ++s2) {
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const float w = T * a[s2][c];
+                Cr = fmaf(w, r[s2][c], Cr);
+                Cg = fmaf(w, gg[s2][c], Cg);
+                Cb = fmaf(w, b[s2][c], Cb);
+                T *= om[s2][c];
+            }
+            A = 1.0f - T;
+            if (A >= ert) return s2 + 1;
+        }
+        return 0;
     }
     __device__ __forceinline__ bool sample(const float (&I)[C], float ell) {
         float T = 1.0f - A; // transmittance: w = T a, T <- T (1 - a)
