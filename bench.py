@@ -221,6 +221,49 @@ def batched_leg(torch, vr, S, reps=20):
     return out
 
 
+def streamed_leg(torch, vr, S):
+    """The streaming use of the method: a 1024x1024x512x3 SPIM-like volume arrives 8 slices at a
+    time and a 1920x1080 frame (oblique clip plane, orbit 5.625 deg per frame) is rendered after
+    every block, 64 blocks from an empty tree to the full volume; tau = 3277 and tau = 0.
+    Inputs are device-resident; CUDA events around each insert and render."""
+    out = {}
+    for tau in (3277, 0):
+        w = S.streamed(tau=tau)
+        spec = w.spec()
+        X, Y, Z = w.dims
+        vol = torch.empty((Z, Y, X, 3), dtype=torch.int16, device="cuda")
+        st = torch.cuda.current_stream().cuda_stream
+        spec.generate_device(vol.data_ptr(), 0, Z, st)
+        r = vr.Renderer(w.dims, 3, w.brick, tau=tau)
+        r.set_transfer_functions(torch.from_numpy(w.tf()).cuda(), torch.ones(3, device="cuda"))
+        img = torch.empty((1080, 1920, 4), device="cuda")
+        n = Z // SLICES_PER_STEP
+        cams = [S.streamed(tau=tau, frame=f).cameras[0] for f in range(n)]
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(n)]
+        samples = 0
+        torch.cuda.synchronize()
+        for i in range(n):
+            ev[i][0].record()
+            r.insert_block((0, 0, i * SLICES_PER_STEP), vol[i * SLICES_PER_STEP:(i + 1) * SLICES_PER_STEP])
+            ev[i][1].record()
+            r.render([cams[i]], [img])
+            ev[i][2].record()
+            samples += r.stats().last_render_samples  # synchronises; the events time the GPU work only
+        torch.cuda.synchronize()
+        ins = [ev[i][0].elapsed_time(ev[i][1]) for i in range(n)]
+        ren = [ev[i][1].elapsed_time(ev[i][2]) for i in range(n)]
+        out[f"tau{tau}"] = {"blocks": n, "insert_ms_per_8_slices": float(np.mean(ins)),
+                            "render_ms_per_frame": float(np.mean(ren)),
+                            "ms_per_step": float(np.mean(ins) + np.mean(ren)),
+                            "samples_per_s": samples / (sum(ren) / 1e3),
+                            "last_frame_render_ms": ren[-1], "pool_gb": r.stats().pool_bytes / 1e9}
+        r.close()
+        del vol
+        torch.cuda.empty_cache()
+    out["workload"] = w.name + ": 8 slices inserted, then one 1920x1080 frame, 64 times"
+    return out
+
+
 def adjoint_leg(torch, vr, S, steps=200):
     """512^3 x 3 SPIM-like volume, 512x512 view: fit TF tables [3,256,4] + scales [3] to a target
     rendered with other tables (seeds 201-203) and scales (0.8, 1, 1.25); mean-L2 loss, Adam lr 1e-2,
@@ -352,7 +395,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--fp16", type=int, default=1, help="also time the FP16-interpolation render")
     ap.add_argument("--suite", type=int, default=1, help="also run the batched and differentiable legs")
-    ap.add_argument("--leg", choices=["batched", "adjoint", "out_of_core"],
+    ap.add_argument("--leg", choices=["batched", "adjoint", "out_of_core", "streamed"],
                     help="run only this secondary leg and print its JSON (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -368,7 +411,8 @@ def main():
         import paper_1407_2074_b300 as vr
         from synth import synth as S
 
-        fn = {"batched": batched_leg, "adjoint": adjoint_leg, "out_of_core": table1_leg}[args.leg]
+        fn = {"batched": batched_leg, "adjoint": adjoint_leg, "out_of_core": table1_leg,
+              "streamed": streamed_leg}[args.leg]
         print(json.dumps({args.leg: fn(torch, vr, S)}), flush=True)
         return
 
@@ -554,7 +598,7 @@ def main():
                          "frac": ach / ipeak, "thread_instructions_per_sample": ips,
                          "peak_from": "148 SMs x 4 schedulers x 32 lanes x median SM clock"}
 
-    batched = adjoint = table1 = None
+    batched = adjoint = table1 = streamed = None
     if args.suite and rank == 0:
         del blocks
         r.close()
@@ -562,6 +606,7 @@ def main():
         batched = batched_leg(torch, vr, S)
         adjoint = adjoint_leg(torch, vr, S)
         table1 = table1_leg(torch, vr, S)
+        streamed = streamed_leg(torch, vr, S)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -586,7 +631,7 @@ def main():
                                     "frac": ins_bytes / (insert_ms / 1e3) / 1e9 / peak},
                 "samples_per_frame": samples / args.steps / ws, "build_s_full_volume": build_s,
                 "roofline": roof, "issue_roofline": issue, "cpu_baseline": cpu, "e2e": e2e, "fp16": fp16,
-                "batched": batched, "adjoint": adjoint, "out_of_core": table1,
+                "batched": batched, "adjoint": adjoint, "out_of_core": table1, "streamed": streamed,
                 "gpu_launches": launches_per_step * args.steps, "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     if dist:
