@@ -149,7 +149,6 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
     float off[3] = {0, 0, 0};
     float inv_vox = 1.0f;
     constexpr int CP = (C + 1) / 2;
-    __half2 hv[8][CP];
     // FP32 trilinear at position pp inside the cached node's brick.  The eight corners of the cell
     // are re-read at every sample (L1 hits): a per-lane cell cache made the reload a branch that
     // some lane of the warp takes at almost every sample (lanes enter new cells at different
@@ -198,6 +197,56 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
             v = fmaf(fxz, (v5 - v4) - (v1 - v0), v);
             v = fmaf(fyz, (v6 - v4) - (v2 - v0), v);
             out[c] = fmaf(fxyz, ((v7 - v6) - (v5 - v4)) - ((v3 - v2) - (v1 - v0)), v);
+        }
+    };
+    // FP16 trilinear: corners as normalised half pairs, interpolated in half2
+    auto trilinear_h = [&](const float (&pp)[3], float (&out)[C]) {
+        float fr[3];
+        int i0[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float u = fmaf(pp[a], inv_vox, -off[a]); // == (p * 2^-L) - off: the product is exact
+            const float fl = floorf(u);
+            int ii = (int)fl;
+            fr[a] = __fsub_rn(u, fl);
+            i0[a] = ii < 0 ? 0 : (ii > M ? M : ii);
+        }
+        const uint16_t* cp0 = sbase + ((i0[2] * S + i0[1]) * S + i0[0]) * VS;
+        f.on_cell(g, nlev, cidx, i0);
+        __half2 hv[8][CP];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const uint16_t* v = cp0 + ((long long)(((q >> 2) & 1) * S + ((q >> 1) & 1)) * S + (q & 1)) * VS;
+            float cv[C];
+            if (VS == 4) {
+                const uint2 w = __ldg(reinterpret_cast<const uint2*>(v));
+                const uint32_t ws[2] = {w.x, w.y};
+#pragma unroll
+                for (int c = 0; c < C; ++c) cv[c] = (float)((c & 1) ? (ws[c >> 1] >> 16) : (ws[c >> 1] & 0xffffu));
+            } else if (VS == 2) {
+                const uint32_t w = __ldg(reinterpret_cast<const unsigned int*>(v));
+#pragma unroll
+                for (int c = 0; c < C; ++c) cv[c] = (float)(c ? (w >> 16) : (w & 0xffffu));
+            } else {
+                cv[0] = (float)__ldg(reinterpret_cast<const unsigned short*>(v));
+            }
+            constexpr float inv = 1.0f / 65535.0f;
+#pragma unroll
+            for (int j = 0; j < CP; ++j)
+                hv[q][j] = __floats2half2_rn(cv[2 * j] * inv, (2 * j + 1 < C) ? cv[2 * j + 1] * inv : 0.0f);
+        }
+        const __half2 fx = __float2half2_rn(fr[0]), fy = __float2half2_rn(fr[1]), fz = __float2half2_rn(fr[2]);
+#pragma unroll
+        for (int j = 0; j < CP; ++j) {
+            const __half2 c00 = __hfma2(fx, __hsub2(hv[1][j], hv[0][j]), hv[0][j]);
+            const __half2 c10 = __hfma2(fx, __hsub2(hv[3][j], hv[2][j]), hv[2][j]);
+            const __half2 c01 = __hfma2(fx, __hsub2(hv[5][j], hv[4][j]), hv[4][j]);
+            const __half2 c11 = __hfma2(fx, __hsub2(hv[7][j], hv[6][j]), hv[6][j]);
+            const __half2 c0 = __hfma2(fy, __hsub2(c10, c00), c00);
+            const __half2 c1 = __hfma2(fy, __hsub2(c11, c01), c01);
+            const float2 r = __half22float2(__hfma2(fz, __hsub2(c1, c0), c0));
+            out[2 * j] = r.x;
+            if (2 * j + 1 < C) out[2 * j + 1] = r.y;
         }
     };
     int k = k0;
@@ -302,7 +351,7 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
                 }
             }
         }
-        if constexpr (F::kPairs && !H) {
+        if constexpr (F::kPairs) {
             // two consecutive samples in the same brick node (same level, full segments): both
             // intensities, TF lookups and opacities are computed before the two are composited in
             // order, so the gathers and lookups of the second overlap those of the first
@@ -329,8 +378,13 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
                     }
                     if (in) {
                         float I1[C], I2[C];
-                        trilinear(p, I1);
-                        trilinear(p2, I2);
+                        if constexpr (H) {
+                            trilinear_h(p, I1);
+                            trilinear_h(p2, I2);
+                        } else {
+                            trilinear(p, I1);
+                            trilinear(p2, I2);
+                        }
                         const int st = f.sample2(I1, I2, dt);
                         ++k;
                         if (st == 1) break;
@@ -348,53 +402,7 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
         if (brick && !H) {
             trilinear(p, I);
         } else if (brick) {
-            // FP16: corners cached as normalised half pairs, interpolated in half2
-            float fr[3];
-            int i0[3];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const float u = fmaf(p[a], inv_vox, -off[a]); // == (p * 2^-L) - off: the product is exact
-                const float fl = floorf(u);
-                int ii = (int)fl;
-                fr[a] = __fsub_rn(u, fl);
-                i0[a] = ii < 0 ? 0 : (ii > M ? M : ii);
-            }
-            const uint16_t* cp0 = sbase + ((i0[2] * S + i0[1]) * S + i0[0]) * VS;
-            f.on_cell(g, nlev, cidx, i0);
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const uint16_t* v = cp0 + ((long long)(((q >> 2) & 1) * S + ((q >> 1) & 1)) * S + (q & 1)) * VS;
-                float cv[C];
-                if (VS == 4) {
-                    const uint2 w = __ldg(reinterpret_cast<const uint2*>(v));
-                    const uint32_t ws[2] = {w.x, w.y};
-#pragma unroll
-                    for (int c = 0; c < C; ++c) cv[c] = (float)((c & 1) ? (ws[c >> 1] >> 16) : (ws[c >> 1] & 0xffffu));
-                } else if (VS == 2) {
-                    const uint32_t w = __ldg(reinterpret_cast<const unsigned int*>(v));
-#pragma unroll
-                    for (int c = 0; c < C; ++c) cv[c] = (float)(c ? (w >> 16) : (w & 0xffffu));
-                } else {
-                    cv[0] = (float)__ldg(reinterpret_cast<const unsigned short*>(v));
-                }
-                constexpr float inv = 1.0f / 65535.0f;
-#pragma unroll
-                for (int j = 0; j < CP; ++j)
-                    hv[q][j] = __floats2half2_rn(cv[2 * j] * inv, (2 * j + 1 < C) ? cv[2 * j + 1] * inv : 0.0f);
-            }
-            const __half2 fx = __float2half2_rn(fr[0]), fy = __float2half2_rn(fr[1]), fz = __float2half2_rn(fr[2]);
-#pragma unroll
-            for (int j = 0; j < CP; ++j) {
-                const __half2 c00 = __hfma2(fx, __hsub2(hv[1][j], hv[0][j]), hv[0][j]);
-                const __half2 c10 = __hfma2(fx, __hsub2(hv[3][j], hv[2][j]), hv[2][j]);
-                const __half2 c01 = __hfma2(fx, __hsub2(hv[5][j], hv[4][j]), hv[4][j]);
-                const __half2 c11 = __hfma2(fx, __hsub2(hv[7][j], hv[6][j]), hv[6][j]);
-                const __half2 c0 = __hfma2(fy, __hsub2(c10, c00), c00);
-                const __half2 c1 = __hfma2(fy, __hsub2(c11, c01), c01);
-                const float2 r = __half22float2(__hfma2(fz, __hsub2(c1, c0), c0));
-                I[2 * j] = r.x;
-                if (2 * j + 1 < C) I[2 * j + 1] = r.y;
-            }
+            trilinear_h(p, I);
         } else {
 #pragma unroll
             for (int c = 0; c < C; ++c) I[c] = H ? __half2float(__float2half_rn(avg[c] * (1.0f / 65535.0f))) : avg[c];
@@ -763,6 +771,33 @@ struct DVRCompositeH : NoHooks {
             lnq += ell * log1pf(-al);
         }
         return composite_run(lnq, K, n, ert, A, Cr, Cg, Cb, stop);
+    }
+    static constexpr bool kPairs = true;
+    __device__ __forceinline__ int sample2(const float (&I1)[C], const float (&I2)[C], float ell) {
+        float2 rg[2][C], ba[2][C];
+        float a[2][C];
+#pragma unroll
+        for (int s2 = 0; s2 < 2; ++s2)
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                lookup(c, s2 ? I2[c] : I1[c], rg[s2][c], ba[s2][c]);
+                const float al = fminf(fmaxf(ba[s2][c].y, 0.0f), ALPHA_MAX);
+                float oma;
+                opacity(al, ell, a[s2][c], oma);
+            }
+#pragma unroll
+        for (int s2 = 0; s2 < 2; ++s2) {
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const float wgt = (1.0f - A) * a[s2][c];
+                Cr = fmaf(wgt, rg[s2][c].x, Cr);
+                Cg = fmaf(wgt, rg[s2][c].y, Cg);
+                Cb = fmaf(wgt, ba[s2][c].x, Cb);
+                A += wgt;
+            }
+            if (A >= ert) return s2 + 1;
+        }
+        return 0;
     }
     __device__ __forceinline__ bool sample(const float (&I)[C], float ell) {
 #pragma unroll
