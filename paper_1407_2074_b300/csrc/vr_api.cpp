@@ -655,7 +655,7 @@ vr_status vr_render_backward(vr_ctx* c, const vr_camera* cams, int n, const floa
     a.stats = nullptr;
     a.dtf = dtf;
     a.dscale = dscale;
-    CK(c, launch_render_backward(a, grid_for(c, tiles, 128, 3), 128, st));
+    CK(c, launch_render_backward(a, grid_for(c, tiles, 128, 5), 128, st));
     return VR_OK;
 }
 
