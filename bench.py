@@ -227,6 +227,16 @@ def streamed_leg(torch, vr, S):
     every block, 64 blocks from an empty tree to the full volume; tau = 3277 and tau = 0.
     Inputs are device-resident; CUDA events around each insert and render."""
     out = {}
+    # untimed warm-up of the kernels this leg launches (module load, first-launch costs)
+    wt = S.streamed(tau=3277, dims=(256, 256, 16), nuclei=50)
+    rt = vr.Renderer(wt.dims, 3, wt.brick, tau=wt.tau)
+    rt.set_transfer_functions(torch.from_numpy(wt.tf()).cuda(), torch.ones(3, device="cuda"))
+    tb = torch.empty((8, 256, 256, 3), dtype=torch.int16, device="cuda")
+    wt.spec().generate_device(tb.data_ptr(), 0, 8, torch.cuda.current_stream().cuda_stream)
+    rt.insert_block((0, 0, 0), tb)
+    rt.render([wt.cameras[0]])
+    torch.cuda.synchronize()
+    rt.close()
     for tau in (3277, 0):
         w = S.streamed(tau=tau)
         spec = w.spec()
