@@ -351,58 +351,56 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
                 }
             }
         }
-        if constexpr (F::kPairs) {
-            // two consecutive samples in the same brick node (same level, full segments): both
-            // intensities, TF lookups and opacities are computed before the two are composited in
-            // order, so the gathers and lookups of the second overlap those of the first
-            if (brick && ell == dt && k + 1 < MAX_SAMPLES) {
-                const float kf2 = kf + 1.0f;
-                const float tk2 = __fadd_rn(t0, __fmul_rn(kf2, dt));
-                if (tk2 < t1 && __fsub_rn(t1, tk2) >= dt && tk2 < tnext && tk2 < tl_limit) {
-                    float p2[3];
-                    bool in = true;
+        float I[C];
+        if (brick) {
+            if constexpr (H)
+                trilinear_h(p, I);
+            else
+                trilinear(p, I);
+            if constexpr (F::kPairs) {
+                // the next sample too when it lies in the same brick node at the same level with a
+                // full segment: both are shaded before the two are composited in order, so the
+                // gathers and lookups of the second overlap those of the first
+                if (ell == dt && k + 1 < MAX_SAMPLES) {
+                    const float kf2 = kf + 1.0f;
+                    const float tk2 = __fadd_rn(t0, __fmul_rn(kf2, dt));
+                    if (tk2 < t1 && __fsub_rn(t1, tk2) >= dt && tk2 < tnext && tk2 < tl_limit) {
+                        float p2[3];
+                        bool in = true;
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) p2[a] = __fadd_rn(cp.eye[a], __fmul_rn(tk2, d[a]));
-                    if (POW2) {
+                        for (int a = 0; a < 3; ++a) p2[a] = __fadd_rn(cp.eye[a], __fmul_rn(tk2, d[a]));
+                        if (POW2) {
 #pragma unroll
-                        for (int a = 0; a < 3; ++a) in = in && ((p2[a] < bnd[a]) != neg[a]);
-                    } else {
-                        const float size = (float)(M << nlev);
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            int q = (int)floorf(__fdiv_rn(p2[a], size));
-                            const int qm = (int)g.nb[nlev][a] - 1;
-                            q = q < 0 ? 0 : (q > qm ? qm : q);
-                            in = in && (q == cidx[a]);
-                        }
-                    }
-                    if (in) {
-                        float I1[C], I2[C];
-                        if constexpr (H) {
-                            trilinear_h(p, I1);
-                            trilinear_h(p2, I2);
+                            for (int a = 0; a < 3; ++a) in = in && ((p2[a] < bnd[a]) != neg[a]);
                         } else {
-                            trilinear(p, I1);
-                            trilinear(p2, I2);
+                            const float size = (float)(M << nlev);
+#pragma unroll
+                            for (int a = 0; a < 3; ++a) {
+                                int q = (int)floorf(__fdiv_rn(p2[a], size));
+                                const int qm = (int)g.nb[nlev][a] - 1;
+                                q = q < 0 ? 0 : (q > qm ? qm : q);
+                                in = in && (q == cidx[a]);
+                            }
                         }
-                        const int st = f.sample2(I1, I2, dt);
-                        ++k;
-                        if (st == 1) break;
-                        kf = kf2;
-                        if (st == 2) {
+                        if (in) {
+                            float I2[C];
+                            if constexpr (H)
+                                trilinear_h(p2, I2);
+                            else
+                                trilinear(p2, I2);
+                            const int st = f.sample2(I, I2, dt);
                             ++k;
-                            break;
+                            if (st == 1) break;
+                            kf = kf2;
+                            if (st == 2) {
+                                ++k;
+                                break;
+                            }
+                            continue;
                         }
-                        continue;
                     }
                 }
             }
-        }
-        float I[C];
-        if (brick && !H) {
-            trilinear(p, I);
-        } else if (brick) {
-            trilinear_h(p, I);
         } else {
 #pragma unroll
             for (int c = 0; c < C; ++c) I[c] = H ? __half2float(__float2half_rn(avg[c] * (1.0f / 65535.0f))) : avg[c];
