@@ -574,6 +574,37 @@ def main():
         fp16 = {"ms_per_frame": ms16, "samples_per_s": samples / args.steps / (ms16 / 1000.0),
                 "max_abs_diff_vs_fp32": float(d.max().item()), "mean_abs_diff_vs_fp32": float(d.mean().item())}
 
+    # the next rows on the same frames: MIP (one TF lookup per channel after the per-channel
+    # maxima) and per-channel affine sample transforms (chromatic-aberration correction)
+    variants = None
+    if args.fp16:
+        vimg = [torch.empty((H, W, 4), dtype=torch.float32, device="cuda") for _ in range(2)]
+
+        def time_frames(mode):
+            r.render([w.cameras[frame_of[0]]], [vimg[0]], mode=mode)
+            torch.cuda.synchronize()
+            v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            v0.record()
+            for i in range(args.warmup, nsteps):
+                r.render([w.cameras[frame_of[i]]], [vimg[i % 2]], mode=mode)
+            v1.record()
+            torch.cuda.synchronize()
+            return v0.elapsed_time(v1) / args.steps
+
+        mip_ms = time_frames(vr.vr.VR_MODE_MIP)
+        c0 = np.array(w.dims, np.float64) / 2.0
+        xf = np.zeros((3, 3, 4), np.float32)
+        for c, (sc_, sh) in enumerate(((1.0, (0.0, 0.0, 0.0)), (1.001, (0.6, -0.3, 1.2)),
+                                       (0.999, (-0.8, 0.5, -1.5)))):
+            xf[c, :, :3] = np.eye(3) * sc_
+            xf[c, :, 3] = c0 - sc_ * c0 + np.array(sh)
+        r.set_channel_transforms(xf)
+        xf_ms = time_frames(vr.vr.VR_MODE_DVR)
+        r.set_channel_transforms(None)
+        variants = {"mip_ms_per_frame": mip_ms, "channel_transforms_ms_per_frame": xf_ms,
+                    "channel_transforms": "channel 0 identity; channels 1, 2 scaled by 1.001 / 0.999 about the "
+                                          "volume centre and shifted by (0.6, -0.3, 1.2) / (-0.8, 0.5, -1.5) voxels"}
+
     # algorithmic footprint of the render, averaged over the timed frames: distinct voxels x C x 2 B
     # + node entries x 16 B + transfer-function tables + image
     fp = {}
@@ -641,6 +672,7 @@ def main():
                                     "frac": ins_bytes / (insert_ms / 1e3) / 1e9 / peak},
                 "samples_per_frame": samples / args.steps / ws, "build_s_full_volume": build_s,
                 "roofline": roof, "issue_roofline": issue, "cpu_baseline": cpu, "e2e": e2e, "fp16": fp16,
+                "next_rows": variants,
                 "batched": batched, "adjoint": adjoint, "out_of_core": table1, "streamed": streamed,
                 "gpu_launches": launches_per_step * args.steps, "clocks": clk.summary()}
         print(json.dumps(line), flush=True)

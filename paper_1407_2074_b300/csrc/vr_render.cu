@@ -856,6 +856,12 @@ struct MIPMax : NoHooks {
         for (int c = 0; c < C; ++c) mx[c] = fmaxf(mx[c], I[c]);
         return false;
     }
+    static constexpr bool kPairs = true;
+    __device__ __forceinline__ int sample2(const float (&I1)[C], const float (&I2)[C], float) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) mx[c] = fmaxf(mx[c], fmaxf(I1[c], I2[c]));
+        return 0;
+    }
 };
 
 // Pixel of a lane in tile lt of its camera: tiles in raster order, tile_w x tile_h lanes (both

@@ -85,6 +85,31 @@ def test_tiny_mip(tiny):
     _check_full(img, ov, w.cameras[0], tf, sc, mode=1)
 
 
+@pytest.mark.parametrize("tau,eps", [(0, 0.6), (3277, 1.5)])
+def test_mip_streamed_matches_oracle(tau, eps):
+    """MIP (samples of a brick node taken in pairs) on a SPIM-like volume rendered while it
+    streams in and again when complete: the image and the sample count equal the oracle's
+    sample-by-sample maximum."""
+    import torch
+
+    dims = (160, 128, 96)
+    spec = S.VolumeSpec(S.KIND_SPIM, dims, 3, 150, seed=21)
+    vol = spec.volume()
+    r = _build(vol, 16, tau=tau, z_hi=48)
+    cam = S.orbit_camera(dims, 1.7 * 160, 25.0, 15.0, 200, 150, lod_error_px=eps)
+    tf, sc = S.make_tf([11, 12, 13]), [1.0, 1.0, 1.0]
+    _render(r, [cam], tf, sc, mode=1)  # render, then stream the rest of the volume in
+    dev = torch.from_numpy(vol.view(np.int16)).cuda()
+    for z in range(48, 96):
+        r.insert_slice(z, dev[z])
+    ov = oracle_dense(vol, 16, tau=tau)
+    img = _render(r, [cam], tf, sc, mode=1)[0]
+    nc, cand, samples = O.render(ov, cam, tf, sc, None, 1)
+    err = admissible_error(img.reshape(-1, 4), nc, cand)
+    assert err.max() <= RGBA_TOL
+    assert r.stats().last_render_samples == int(samples.sum())
+
+
 def test_context_clip_planes_apply_to_cameras_without_their_own(tiny):
     w, vol, ov = tiny
     r = _build(vol, 16)
