@@ -476,7 +476,7 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
 // March with a per-channel affine sample transform (Sec. "Correction of Chromatic Aberration"):
 // channel c samples at q_c = X_c p, X_c a 3x4 matrix applied in single precision in a fixed order
 // (((m0 p0 + m1 p1) + m2 p2) + m3).  Each channel descends from its own point and keeps its own
-// node and cell cache; the node test checks both faces because rounded transformed positions
+// node cache; the node test checks both faces because rounded transformed positions
 // need not be monotone.  Samples are composited one by one (no closed-form runs).
 template <int C, int VS, bool POW2, class F>
 __device__ __forceinline__ long long march_xf(const Geo& g, const uint16_t* __restrict__ pool,
@@ -486,7 +486,7 @@ __device__ __forceinline__ long long march_xf(const Geo& g, const uint16_t* __re
     const int N = g.N, M = g.M, S = g.S;
     int Lstar = 0;
     float tnext = (N >= 1) ? cp.tl[1] : CUDART_INF_F;
-    int nlev[C], cell[C];
+    int nlev[C];
     float tl_limit[C], lo[C][3], hi[C][3], off[C][3], inv_vox[C], avg[C], cv[C][8];
     const uint16_t* sbase[C];
     bool brick[C];
@@ -494,7 +494,6 @@ __device__ __forceinline__ long long march_xf(const Geo& g, const uint16_t* __re
 #pragma unroll
     for (int c = 0; c < C; ++c) {
         nlev[c] = -1;
-        cell[c] = -1;
         tl_limit[c] = 0.0f;
         brick[c] = false;
         sbase[c] = nullptr;
@@ -571,7 +570,6 @@ __device__ __forceinline__ long long march_xf(const Geo& g, const uint16_t* __re
                 brick[c] = (nd.flags & F_BRICK) && nd.slot >= 0 && nd.slot < g.n_slots_cap;
                 sbase[c] = brick[c] ? pool + (long long)nd.slot * g.slot_elems : nullptr;
                 avg[c] = (float)nd.avg[c];
-                cell[c] = -1;
             }
             if (brick[c]) {
                 float fr[3];
@@ -585,8 +583,8 @@ __device__ __forceinline__ long long march_xf(const Geo& g, const uint16_t* __re
                     i0[a] = ii < 0 ? 0 : (ii > M ? M : ii);
                 }
                 const int coff = ((i0[2] * S + i0[1]) * S + i0[0]) * VS;
-                if (coff != cell[c]) {
-                    cell[c] = coff;
+                {
+                    // corners re-read at every sample (no divergent per-lane cell cache)
                     float v[8];
 #pragma unroll
                     for (int e = 0; e < 8; ++e)
