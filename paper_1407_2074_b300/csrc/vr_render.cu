@@ -649,7 +649,7 @@ __device__ __forceinline__ long long composite_run(float lnq, const float K[3], 
     return j;
 }
 
-template <int C, bool RUNS = true>
+template <int C, bool RUNS = true, bool PAIRS = RUNS>
 struct DVRComposite : NoHooks {
     static constexpr bool kRuns = RUNS;
     const float4* s_tf;
@@ -676,7 +676,7 @@ struct DVRComposite : NoHooks {
     }
     // Two full-segment samples: shading of both first, then compositing in order.  Returns 1 when
     // the first sample terminates the ray (the second is dropped), 2 when the second does, else 0.
-    static constexpr bool kPairs = RUNS;
+    static constexpr bool kPairs = PAIRS;
     __device__ __forceinline__ int sample2(const float (&I1)[C], const float (&I2)[C], float ell) {
         float r[2][C], gg[2][C], b[2][C], a[2][C], om[2][C];
 #pragma unroll
@@ -993,13 +993,18 @@ __global__ void __launch_bounds__(256, VR_RENDER_MIN_CTAS) render_kernel(RenderA
 }
 
 // Reverse-mode sweep in forward order.  With the final (C_f, A_f) of the ray known, the adjoint
-// of the opacity after channel-step j is
-//   gA_j+ = [ -gC.(C_f - C_j+) + gA_f (1 - A_f) ] / (1 - A_j+),
-// and for the update C += (1-A) a rgb, A += (1-A) a:
-//   dL/da_j   = (1 - A_j-) gC.rgb_j + [ -gC.(C_f - C_j+) + gA_f (1 - A_f) ] / (1 - a_j),
-//   dL/drgb_j = gC (1 - A_j-) a_j,     da/dalpha = l (1 - a) / (1 - alpha).
+// of channel-step j of the update C += T a rgb, T <- T (1 - a) (T = 1 - A) is
+//   dL/da_j   = T_j gC.rgb_j + [ -gC.(C_f - C_j+) + gA_f (1 - A_f) ] / (1 - a_j),
+//   dL/drgb_j = gC T_j a_j,     da/dalpha = l (1 - a) / (1 - alpha).
+// The sweep repeats the forward arithmetic of DVRComposite (transmittance form, closed-form runs
+// through brick-less nodes, no pairs) so that it stops at the same sample.  A run of n equal
+// samples contributes the sums over its samples in closed form: sample s, channel c has
+// T_{s,c} = T_0 q^s P_c (P_c = prod_{c' < c} (1 - a_c'), q = P_C) and
+// C_(s,c)+ = C_0 + T_0 K (1 - q^s) / (1 - q) + T_0 q^s R_c (R_c = sum_{c' <= c} P_c' a_c' rgb_c',
+// K = R_{C-1}), so every term is a geometric series in q.
 template <int C>
 struct DVRAdjoint : NoHooks {
+    static constexpr bool kRuns = true;
     const float4* s_tf;
     const float* s_scl;
     float* s_dtf; // [C][256][4]
@@ -1036,7 +1041,26 @@ struct DVRAdjoint : NoHooks {
 #pragma unroll
         for (int c = 0; c < C; ++c) flush(c);
     }
+    // table gradient gq (rgba) of channel c at lookup t, and the scale gradient
+    __device__ __forceinline__ void accumulate(int c, const TFLookup<C>& t, const float (&gq)[4], float I) {
+        const float4 D = s_tf[(C + c) * 256 + t.i];
+        const float glam = gq[0] * D.x + gq[1] * D.y + gq[2] * D.z + gq[3] * D.w;
+        if (t.i != pk[c]) {
+            flush(c);
+            pk[c] = t.i;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            pS[c][q] += gq[q];
+            pL[c][q] = fmaf(t.lam, gq[q], pL[c][q]);
+        }
+        if (t.xr > 0.0f && t.xr < 1.0f) dsc[c] += glam * 255.0f * I * (1.0f / 65535.0f);
+    }
+    __device__ __forceinline__ float suffix_term() const {
+        return -(gC[0] * (Cf[0] - Cp[0]) + gC[1] * (Cf[1] - Cp[1]) + gC[2] * (Cf[2] - Cp[2])) + gAf * (1.0f - Af);
+    }
     __device__ __forceinline__ bool sample(const float (&I)[C], float ell) {
+        float T = 1.0f - A;
 #pragma unroll
         for (int c = 0; c < C; ++c) {
             TFLookup<C> t;
@@ -1045,30 +1069,56 @@ struct DVRAdjoint : NoHooks {
             const float al = fminf(fmaxf(t.al, 0.0f), ALPHA_MAX);
             float a, oma;
             opacity(al, ell, a, oma);
-            const float T = 1.0f - A;
             const float w = T * a;
             Cp[0] = fmaf(w, t.r, Cp[0]);
             Cp[1] = fmaf(w, t.g, Cp[1]);
             Cp[2] = fmaf(w, t.b, Cp[2]);
-            A += w;
-            const float suffix = -(gC[0] * (Cf[0] - Cp[0]) + gC[1] * (Cf[1] - Cp[1]) + gC[2] * (Cf[2] - Cp[2])) +
-                                 gAf * (1.0f - Af);
-            const float ga = T * (gC[0] * t.r + gC[1] * t.g + gC[2] * t.b) + suffix / oma;
+            const float ga = T * (gC[0] * t.r + gC[1] * t.g + gC[2] * t.b) + suffix_term() / oma;
             const float gq[4] = {gC[0] * w, gC[1] * w, gC[2] * w, clamped ? 0.0f : ga * ell * oma / (1.0f - al)};
-            const float4 D = s_tf[(C + c) * 256 + t.i];
-            const float glam = gq[0] * D.x + gq[1] * D.y + gq[2] * D.z + gq[3] * D.w;
-            if (t.i != pk[c]) {
-                flush(c);
-                pk[c] = t.i;
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                pS[c][q] += gq[q];
-                pL[c][q] = fmaf(t.lam, gq[q], pL[c][q]);
-            }
-            if (t.xr > 0.0f && t.xr < 1.0f) dsc[c] += glam * 255.0f * I[c] * (1.0f / 65535.0f);
+            accumulate(c, t, gq, I[c]);
+            T *= oma;
         }
+        A = 1.0f - T;
         return A >= ert;
+    }
+    __device__ __forceinline__ long long run(const float (&I)[C], long long n, float ell, bool& stop) {
+        TFLookup<C> t[C];
+        float a[C], oma[C], al[C], P[C], R[C][3];
+        float lnq = 0.0f, qpre = 1.0f, K[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            t[c].eval(s_tf, s_scl, c, I[c]);
+            al[c] = fminf(fmaxf(t[c].al, 0.0f), ALPHA_MAX);
+            opacity(al[c], ell, a[c], oma[c]);
+            P[c] = qpre;
+            const float w = qpre * a[c];
+            K[0] = fmaf(w, t[c].r, K[0]);
+            K[1] = fmaf(w, t[c].g, K[1]);
+            K[2] = fmaf(w, t[c].b, K[2]);
+            R[c][0] = K[0];
+            R[c][1] = K[1];
+            R[c][2] = K[2];
+            qpre *= oma[c];
+            lnq += ell * log1pf(-al[c]);
+        }
+        const float T0 = 1.0f - A;
+        const float alpha0 = suffix_term(); // before the run: C_0 = Cp
+        const long long j = composite_run(lnq, K, n, ert, A, Cp[0], Cp[1], Cp[2], stop);
+        const float nj = (float)j;
+        const float Sg = (lnq < 0.0f) ? expm1f(nj * lnq) / expm1f(lnq) : nj; // sum_{s<j} q^s
+        const float beta = (lnq < 0.0f) ? T0 * (gC[0] * K[0] + gC[1] * K[1] + gC[2] * K[2]) / -expm1f(lnq) : 0.0f;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const float gamma = T0 * (gC[0] * R[c][0] + gC[1] * R[c][1] + gC[2] * R[c][2]);
+            const float ga = T0 * P[c] * (gC[0] * t[c].r + gC[1] * t[c].g + gC[2] * t[c].b) * Sg +
+                             (alpha0 * nj + beta * (nj - Sg) + gamma * Sg) / oma[c];
+            const float wsum = T0 * P[c] * a[c] * Sg;
+            const bool clamped = !(t[c].al >= 0.0f && t[c].al <= ALPHA_MAX);
+            const float gq[4] = {gC[0] * wsum, gC[1] * wsum, gC[2] * wsum,
+                                 clamped ? 0.0f : ga * ell * oma[c] / (1.0f - al[c])};
+            accumulate(c, t[c], gq, I[c]);
+        }
+        return j;
     }
 };
 
@@ -1099,7 +1149,7 @@ __global__ void __launch_bounds__(128, 5) render_backward_kernel(RenderArgs a) {
         if (!ray_setup(cp, a.g, px, py, d, t0, t1)) continue;
         const float4 gl = reinterpret_cast<const float4*>(cp.dimg)[(long long)py * cp.W + px];
         if (gl.x == 0.0f && gl.y == 0.0f && gl.z == 0.0f && gl.w == 0.0f) continue;
-        DVRComposite<C, false> fw{{}, s_tf, s_scl, cp.ert}; // sample by sample, like the adjoint sweep
+        DVRComposite<C, true, false> fw{{}, s_tf, s_scl, cp.ert}; // the sweep's arithmetic: runs, no pairs
         if constexpr (XF)
             march_xf<C, VS, POW2>(a.g, a.pool, a.rnodes, cp, d, t0, t1, a.xf, fw);
         else

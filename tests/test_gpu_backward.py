@@ -70,6 +70,44 @@ def test_backward_with_early_termination_normwise():
     assert np.linalg.norm(dsc.cpu().numpy() - rsc) <= 1e-3 * np.linalg.norm(rsc)
 
 
+@pytest.mark.parametrize("ert", [2.0, 0.99])
+def test_backward_through_homogeneous_runs(ert):
+    """A SPIM-like volume with tau = 3277: the background outside the tissue is brick-less, and
+    the sweep takes its runs of equal samples in closed form; the gradient still equals the
+    oracle's sample-by-sample FP64 one."""
+    import torch
+    import paper_1407_2074_b300 as vr
+
+    dims = (96, 80, 64)
+    spec = S.VolumeSpec(S.KIND_SPIM, dims, 3, 60, seed=17)
+    vol = spec.volume()
+    r = vr.Renderer(dims, 3, 16, tau=3277)
+    r.insert_block((0, 0, 0), torch.from_numpy(vol.view(np.int16)).cuda())
+    ov = oracle_dense(vol, 16, tau=3277)
+    g = ov.geom
+    brickless = sum(not ov.node(L, i, j, k).has_brick for L in range(g.N + 1) for k in range(g.nb[L][2])
+                    for j in range(g.nb[L][1]) for i in range(g.nb[L][0]) if ov.node(L, i, j, k).touched)
+    assert brickless > 10
+    cam = S.orbit_camera(dims, 2.0 * 96, 30.0, 20.0, 40, 36, lod_error_px=0.7)
+    cam["ert_alpha"] = ert
+    tf = S.make_tf([11, 12, 13])
+    tf[..., 3] = np.minimum(1.0, tf[..., 3] * (8.0 if ert < 1.0 else 2.0))
+    sc = np.array([1.0, 0.9, 1.2], np.float32)
+    dl = np.random.default_rng(3).normal(size=(cam["height"], cam["width"], 4)).astype(np.float32)
+    r.set_transfer_functions(torch.from_numpy(tf), torch.from_numpy(sc))
+    dtf, dsc = r.render_backward([cam], [torch.from_numpy(dl).cuda()])
+    torch.cuda.synchronize()
+    px, py = O.image_pixels(cam["width"], cam["height"])
+    rtf, rsc = O.render_grad(ov, cam, tf, sc, (px, py), dl.reshape(-1, 4).astype(np.float64))
+    if ert > 1.0:
+        _grad_close(dtf.cpu().numpy(), rtf)
+        _grad_close(dsc.cpu().numpy(), rsc)
+    else:
+        g = dtf.cpu().numpy()
+        assert np.linalg.norm(g - rtf) <= 1e-3 * np.linalg.norm(rtf)
+        assert np.linalg.norm(dsc.cpu().numpy() - rsc) <= 1e-3 * np.linalg.norm(rsc)
+
+
 def test_autograd_function_and_finite_differences():
     import torch
     import paper_1407_2074_b300 as vr
