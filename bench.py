@@ -471,10 +471,12 @@ def main():
     H, W = w.cameras[0]["height"], w.cameras[0]["width"]
     images = [torch.empty((H, W, 4), dtype=torch.float32, device="cuda") for _ in range(2)]
     # samples per frame (deterministic; measured once, untimed)
-    samples_of = {}
+    samples_of, rays_of = {}, {}
     for f in sorted(set(frame_of)):
         r.render([w.cameras[f]], [images[0]])
-        samples_of[f] = r.stats().last_render_samples
+        st_ = r.stats()
+        samples_of[f] = st_.last_render_samples
+        rays_of[f] = st_.last_render_rays
     # per-kernel launch count per step: level updates (N + 1) + the render kernel
     launches_per_step = r.levels + 1
 
@@ -511,6 +513,8 @@ def main():
         torch.cuda.synchronize()
     timed = range(args.warmup, nsteps)
     render_ms = float(np.mean([ev[i][1].elapsed_time(ev[i][2]) for i in timed]))
+    render_ms_median = float(np.median([ev[i][1].elapsed_time(ev[i][2]) for i in timed]))
+    rays_per_frame = float(np.mean([rays_of[frame_of[i]] for i in timed]))
     insert_ms = float(np.mean([ev[i][0].elapsed_time(ev[i][1]) for i in timed]))
     total_ms, samples = vr.dist.aggregate(start.elapsed_time(stop),
                                           float(sum(samples_of[frame_of[i]] for i in timed)), device="cuda")
@@ -628,6 +632,7 @@ def main():
         d = json.load(open(tr))
         if d.get("source_hash") == source_hash():
             roof["traffic"] = d.get("traffic_bytes_per_launch")
+            roof["l2_traffic"] = d.get("l2_bytes_per_launch")  # lts__t_bytes.sum of the same launches
             fr = d.get("frames", [])
             if fr and all(f in samples_of for f in fr):
                 # instructions per composited sample on the captured frames, at the live sample rate
@@ -666,7 +671,11 @@ def main():
                            "dims": list(w.dims), "channels": 3, "brick": w.brick, "tau": w.tau, "step_voxels": 0.5,
                            "lod_error_px": 1.0, "ert_alpha": 0.99, "l2": "inputs larger than L2 (brick pool "
                            f"{pool_gb:.1f} GB)", "parallelism": f"replicas x{ws}"},
-                "ms_per_frame": render_ms, "insert_ms_per_8_slices": insert_ms,
+                "ms_per_frame": render_ms, "ms_per_frame_median": render_ms_median,
+                "pixel_rays_per_s": H * W / (render_ms / 1e3),
+                "volume_rays_per_s": rays_per_frame / (render_ms / 1e3),
+                "logical_gather_bytes_per_s": 48.0 * samples / args.steps / ws / (render_ms / 1e3),
+                "insert_ms_per_8_slices": insert_ms,
                 "insert_roofline": {"bound": "hbm", "algorithmic_bytes": ins_bytes,
                                     "achieved": ins_bytes / (insert_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                                     "frac": ins_bytes / (insert_ms / 1e3) / 1e9 / peak},
