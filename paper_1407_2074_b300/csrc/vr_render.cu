@@ -281,11 +281,30 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
             }
         }
         if (!valid) {
-            // getNodeAtPosition: descend from the root towards L*
+            // getNodeAtPosition: descend from the root towards L*.  With power-of-two node sizes
+            // the descent restarts at the lowest ancestor of the cached node whose box holds p
+            // (at level L* or above): every ancestor has children, and from there the descent
+            // visits exactly the nodes the root descent would.
             int lev = N;
             int idx[3] = {0, 0, 0};
-            RNode nd = rn[g.noff[N]];
-            f.on_node(g.noff[N]);
+            if (POW2 && nlev >= 0) {
+                for (int A = nlev + 1 > Lstar ? nlev + 1 : Lstar; A < N; ++A) {
+                    const int sh = A - nlev;
+                    const float inv = 1.0f / (float)(M << A);
+                    bool in = true;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) in = in && ((int)floorf(__fmul_rn(p[a], inv)) == (cidx[a] >> sh));
+                    if (in) {
+                        lev = A;
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) idx[a] = cidx[a] >> sh;
+                        break;
+                    }
+                }
+            }
+            const long long nid0 = g.noff[lev] + ((long long)idx[2] * g.nb[lev][1] + idx[1]) * g.nb[lev][0] + idx[0];
+            RNode nd = rn[nid0];
+            f.on_node(nid0);
             while (lev > Lstar && (nd.flags & F_CHILDREN)) {
                 --lev;
                 const float size = (float)(M << lev);
