@@ -97,6 +97,9 @@ __device__ __forceinline__ void opacity(float al, float ell, float& a, float& om
 constexpr float VBIAS = 8388608.0f;
 __device__ __forceinline__ float biased(uint32_t h) { return __uint_as_float(0x4B000000u | h); }
 
+// 2^-e as a float, exactly (0 <= e < 126): the reciprocal of a power-of-two size without a division
+__device__ __forceinline__ float pow2_neg(int e) { return __int_as_float((127 - e) << 23); }
+
 constexpr float ALPHA_MAX = 1.0f - 1e-6f;
 constexpr int MAX_SAMPLES = 1 << 24; // (float)k stays exact; bounds every ray
 
@@ -134,6 +137,7 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
                                            float t1, F& f, const CacheArgs* ca = nullptr, int k0 = 0) {
     const float dt = cp.dt;
     const int N = g.N, M = g.M, S = g.S;
+    const int mlog = __ffs(M) - 1; // log2(M) when POW2
     int Lstar = 0;
     float tnext = cp.tl[1 <= N ? 1 : N + 1];
     if (N < 1) tnext = CUDART_INF_F;
@@ -290,7 +294,7 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
             if (POW2 && nlev >= 0) {
                 for (int A = nlev + 1 > Lstar ? nlev + 1 : Lstar; A < N; ++A) {
                     const int sh = A - nlev;
-                    const float inv = 1.0f / (float)(M << A);
+                    const float inv = pow2_neg(mlog + A);
                     bool in = true;
 #pragma unroll
                     for (int a = 0; a < 3; ++a) in = in && ((int)floorf(__fmul_rn(p[a], inv)) == (cidx[a] >> sh));
@@ -308,7 +312,7 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
             while (lev > Lstar && (nd.flags & F_CHILDREN)) {
                 --lev;
                 const float size = (float)(M << lev);
-                const float inv = 1.0f / size;
+                const float inv = POW2 ? pow2_neg(mlog + lev) : 0.0f;
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
                     const float qf = POW2 ? floorf(__fmul_rn(p[a], inv)) : floorf(__fdiv_rn(p[a], size));
@@ -334,7 +338,7 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
                     bnd[a] = (idx[a] == 0) ? -CUDART_INF_F : (float)idx[a] * size;
                 off[a] = (float)(idx[a] * M) - 0.5f;
             }
-            inv_vox = 1.0f / (float)(1 << lev);
+            inv_vox = pow2_neg(lev);
             brick = (nd.flags & F_BRICK) && nd.slot >= 0 && nd.slot < g.n_slots_cap;
             sbase = brick ? pool + (long long)nd.slot * g.slot_elems : nullptr;
 #pragma unroll
@@ -364,7 +368,7 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
                             sbase = ca->cache + (long long)c2 * g.slot_elems;
 #pragma unroll
                             for (int a = 0; a < 3; ++a) off[a] = (float)(i2[a] * M) - 0.5f;
-                            inv_vox = 1.0f / (float)(1 << L2);
+                            inv_vox = pow2_neg(L2);
                         }
                     }
                 }
@@ -445,12 +449,14 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
                     }
                     return true;
                 };
+                // estimate of the last sample in the node (fast divisions: the exact per-sample
+                // tests below decide)
                 float te = fminf(tl_limit, t1 - dt);
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    if (d[a] != 0.0f) te = fminf(te, (bnd[a] - cp.eye[a]) / d[a]);
+                    if (d[a] != 0.0f) te = fminf(te, __fdividef(bnd[a] - cp.eye[a], d[a]));
                 }
-                const float steps = floorf((te - tk) / dt);
+                const float steps = floorf(__fdividef(te - tk, dt));
                 int ke = k + (steps > 0.0f ? (int)fminf(steps, 16777216.0f) : 0);
                 int aa = k, bb;
                 if (ke > k && in_run(ke)) {
