@@ -136,6 +136,7 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
                                            const RNode* __restrict__ rn, const CamParam& cp, const float d[3], float t0,
                                            float t1, F& f, const CacheArgs* ca = nullptr, int k0 = 0) {
     const float dt = cp.dt;
+    const float eye[3] = {cp.eye[0], cp.eye[1], cp.eye[2]}; // in registers: cp lives in global memory
     const int N = g.N, M = g.M, S = g.S;
     const int mlog = __ffs(M) - 1; // log2(M) when POW2
     int Lstar = 0;
@@ -261,7 +262,7 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
         const float ell = fminf(dt, __fsub_rn(t1, tk));
         float p[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) p[a] = __fadd_rn(cp.eye[a], __fmul_rn(tk, d[a]));
+        for (int a = 0; a < 3; ++a) p[a] = __fadd_rn(eye[a], __fmul_rn(tk, d[a]));
         while (tk >= tnext) {
             ++Lstar;
             tnext = (Lstar < N) ? cp.tl[Lstar + 1] : CUDART_INF_F;
@@ -391,7 +392,7 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
                         float p2[3];
                         bool in = true;
 #pragma unroll
-                        for (int a = 0; a < 3; ++a) p2[a] = __fadd_rn(cp.eye[a], __fmul_rn(tk2, d[a]));
+                        for (int a = 0; a < 3; ++a) p2[a] = __fadd_rn(eye[a], __fmul_rn(tk2, d[a]));
                         if (POW2) {
 #pragma unroll
                             for (int a = 0; a < 3; ++a) in = in && ((p2[a] < bnd[a]) != neg[a]);
@@ -437,7 +438,7 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
                     if (!(t < t1) || !(t < tl_limit) || !(__fsub_rn(t1, t) >= dt)) return false;
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
-                        const float pa = __fadd_rn(cp.eye[a], __fmul_rn(t, d[a]));
+                        const float pa = __fadd_rn(eye[a], __fmul_rn(t, d[a]));
                         if (POW2) {
                             if ((pa < bnd[a]) == neg[a]) return false;
                         } else {
@@ -454,7 +455,7 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
                 float te = fminf(tl_limit, t1 - dt);
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    if (d[a] != 0.0f) te = fminf(te, __fdividef(bnd[a] - cp.eye[a], d[a]));
+                    if (d[a] != 0.0f) te = fminf(te, __fdividef(bnd[a] - eye[a], d[a]));
                 }
                 const float steps = floorf(__fdividef(te - tk, dt));
                 int ke = k + (steps > 0.0f ? (int)fminf(steps, 16777216.0f) : 0);
