@@ -566,7 +566,24 @@ __device__ __forceinline__ long long march_xf(const Geo& g, const uint16_t* __re
             if (!valid) {
                 int lev = N;
                 int idx[3] = {0, 0, 0};
-                RNode nd = rn[g.noff[N]];
+                if (POW2 && nlev[c] >= 0) {
+                    // restart at the lowest ancestor of the channel's cached node that holds q
+                    const int mlog = __ffs(M) - 1;
+                    for (int A = nlev[c] + 1 > Lstar ? nlev[c] + 1 : Lstar; A < N; ++A) {
+                        const int sh = A - nlev[c];
+                        const float inv = pow2_neg(mlog + A);
+                        bool in = true;
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) in = in && ((int)floorf(__fmul_rn(q[a], inv)) == (cidx[c][a] >> sh));
+                        if (in) {
+                            lev = A;
+#pragma unroll
+                            for (int a = 0; a < 3; ++a) idx[a] = cidx[c][a] >> sh;
+                            break;
+                        }
+                    }
+                }
+                RNode nd = rn[g.noff[lev] + ((long long)idx[2] * g.nb[lev][1] + idx[1]) * g.nb[lev][0] + idx[0]];
                 while (lev > Lstar && (nd.flags & F_CHILDREN)) {
                     --lev;
                     const float size = (float)(M << lev);
