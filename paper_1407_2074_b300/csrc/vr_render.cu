@@ -7,13 +7,16 @@
 //   setup      pinhole ray, slab test against the real volume box, clip half-spaces, t >= 0;
 //   march      t_k = t0 + k dt while t_k < t1, last segment l = t1 - t_k;
 //   LOD        L* = largest L with t_k >= t_L (thresholds precomputed per camera);
-//   node       descent from the root to level L* through the dense node tables, stopping at a
-//              node without children; the node is cached until the sample leaves its box or L*
-//              rises above its level;
+//   node       descent to level L* through the dense node tables, stopping at a node without
+//              children; the node is cached until the sample leaves its box or L* rises above its
+//              level, and the next lookup restarts at the lowest cached ancestor holding the sample
+//              (the same node as a descent from the root);
 //   intensity  AVG of a brick-less node, else trilinear inside the node's slot (the border
-//              voxels make the eight corners one slot), corners re-read at every sample;
+//              voxels make the eight corners one slot), corners re-read at every sample; two
+//              consecutive samples of one brick node are shaded together before compositing;
+//              a run of equal samples through a brick-less node is composited in closed form;
 //   TF         x = sat(I s / 65535), entry i = min(floor(255 x), 254), linear (smem table);
-//   composite  a = 1 - (1 - alpha)^l, C += (1 - A) a rgb, A += (1 - A) a per channel in order;
+//   composite  a = 1 - (1 - alpha)^l, C += T a rgb, T <- T (1 - a) per channel in order (T = 1 - A);
 //   ERT        stop once A >= ert after a sample.
 // Geometry (ray direction, interval, t_k, sample positions, level and node choice) uses only
 // correctly rounded single-precision operations (_rn intrinsics, never contracted) in a fixed
