@@ -144,9 +144,10 @@ def cpu_baseline(w, vol, n_rays, seed=0, threads=0):
         py = rng.integers(0, cam["height"], size=n_rays).astype(np.int32)
         pix = (px, py)
     t = time.time()
-    _, _, samples = O.render(vol, cam, w.tf(), [1.0, 1.0, 1.0], pix, 0, threads)
+    nc, cand, samples = O.render(vol, cam, w.tf(), [1.0, 1.0, 1.0], pix, 0, threads)
     dt = time.time() - t
     cores = threads if threads > 0 else os.cpu_count()
+    cpu_baseline.last = (nc, cand, samples, pix)
     return float(samples.sum()), dt, cores
 
 
@@ -644,6 +645,11 @@ def main():
                          "frac": ach / ipeak, "thread_instructions_per_sample": ips,
                          "peak_from": "148 SMs x 4 schedulers x 32 lanes x median SM clock"}
 
+    # the GPU's orbit frame 0 (host copy) for the parity report against the oracle's frame
+    r.render([w.cameras[0]], [images[0]])
+    frame0 = images[0].cpu().numpy()
+    samples0 = r.stats().last_render_samples
+
     batched = adjoint = table1 = streamed = None
     if args.suite and rank == 0:
         del blocks
@@ -654,11 +660,20 @@ def main():
         table1 = table1_leg(torch, vr, S)
         streamed = streamed_leg(torch, vr, S)
 
-    cpu = None
+    cpu = parity = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         ovol = oracle_volume(w, torch)
         s, t, cores = cpu_baseline(w, ovol, args.cpu_rays)
         del ovol
+        from oracle import oracle as O
+
+        nc, cand, osamp, pix = cpu_baseline.last
+        g0 = frame0.reshape(-1, 4) if pix is None else frame0[pix[1], pix[0]]
+        err = O.admissible_error(g0, nc, cand)
+        parity = {"frame": 0, "pixels": int(err.size), "max_abs": float(err.max()), "mean_abs": float(err.mean()),
+                  "tolerance": 2e-3, "pixels_over_tolerance": int((err > 2e-3).sum()),
+                  "knife_edge_pixels": int((nc > 1).sum()),
+                  "samples_gpu": int(samples0), "samples_oracle": int(osamp.sum())}
         what = "every pixel" if args.cpu_rays <= 0 else f"{args.cpu_rays} random pixels"
         cpu = {"value": s / t, "unit": "samples/s", "cores": cores, "kind": "oracle",
                "sample": f"{what} of orbit frame 0 (1920x1080) against a streamed oracle volume of the full "
@@ -675,12 +690,13 @@ def main():
                 "pixel_rays_per_s": H * W / (render_ms / 1e3),
                 "volume_rays_per_s": rays_per_frame / (render_ms / 1e3),
                 "logical_gather_bytes_per_s": 48.0 * samples / args.steps / ws / (render_ms / 1e3),
-                "insert_ms_per_8_slices": insert_ms,
+                "insert_ms_per_8_slices": insert_ms, "insert_slices_per_s": SLICES_PER_STEP / (insert_ms / 1e3),
                 "insert_roofline": {"bound": "hbm", "algorithmic_bytes": ins_bytes,
                                     "achieved": ins_bytes / (insert_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                                     "frac": ins_bytes / (insert_ms / 1e3) / 1e9 / peak},
                 "samples_per_frame": samples / args.steps / ws, "build_s_full_volume": build_s,
-                "roofline": roof, "issue_roofline": issue, "cpu_baseline": cpu, "e2e": e2e, "fp16": fp16,
+                "roofline": roof, "issue_roofline": issue, "cpu_baseline": cpu, "parity_vs_oracle": parity,
+                "e2e": e2e, "fp16": fp16,
                 "next_rows": variants,
                 "batched": batched, "adjoint": adjoint, "out_of_core": table1, "streamed": streamed,
                 "gpu_launches": launches_per_step * args.steps, "clocks": clk.summary()}

@@ -240,6 +240,14 @@ vr_status vr_read_node(vr_ctx* ctx, int level, int64_t i, int64_t j, int64_t k, 
 
 vr_status vr_stats(vr_ctx* ctx, vr_stats_t* out);
 
+/* Test hook (no counterpart in the paper): writes code (!= 0) into the context's device error
+ * word, exactly as a failed device-side check of a kernel would (the kernels never trap; they set
+ * this word and return).  The next call that polls the word (vr_read_level, vr_read_voxels,
+ * vr_read_node) returns VR_ERR_DEVICE_ASSERT and every later call VR_ERR_STATE, until
+ * vr_destroy, which still releases everything.  Lets the error path be tested without a fault.
+ * Errors: VR_ERR_INVALID_ARG (NULL context or code 0), VR_ERR_STATE, VR_ERR_CUDA. */
+vr_status vr_debug_raise_error(vr_ctx* ctx, int code);
+
 /* Render plan: a fixed batch of views of uneven resolution rendered by ONE persistent launch,
  * captured once into a CUDA graph (queue reset + kernel) and replayed by vr_plan_launch.  The
  * plan owns the per-camera constants; images, the context's brick pool and its transfer

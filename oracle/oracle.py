@@ -241,6 +241,16 @@ class LazyVolume(Volume):
         self.C = channels
 
 
+def admissible_error(gpu_rgba: np.ndarray, n_cand: np.ndarray, cand: np.ndarray) -> np.ndarray:
+    """Per-pixel max-abs error of gpu_rgba [n][4] to the nearest admissible oracle state (the
+    FP64 result, or one of the stopping states near the early-termination threshold)."""
+    g = np.asarray(gpu_rgba, dtype=np.float64).reshape(-1, 1, 4)
+    c = cand.reshape(g.shape[0], MAXCAND, 4)
+    e = np.abs(c - g).max(axis=-1)
+    valid = np.arange(MAXCAND)[None, :] < n_cand.reshape(-1, 1)
+    return np.where(valid, e, np.inf).min(axis=-1)
+
+
 def image_pixels(width, height):
     py, px = np.meshgrid(np.arange(height, dtype=np.int32), np.arange(width, dtype=np.int32), indexing="ij")
     return px.ravel().copy(), py.ravel().copy()

@@ -977,6 +977,14 @@ vr_status vr_read_node(vr_ctx* c, int level, int64_t i, int64_t j, int64_t k, ui
     return poll_error(c, st);
 }
 
+vr_status vr_debug_raise_error(vr_ctx* c, int code) {
+    vr_status s = check_ctx(c);
+    if (s != VR_OK) return s;
+    if (code == 0) return fail(c, VR_ERR_INVALID_ARG, "code must be non-zero");
+    CK(c, cudaMemcpy(c->err, &code, sizeof(int), cudaMemcpyHostToDevice));
+    return VR_OK;
+}
+
 vr_status vr_stats(vr_ctx* c, vr_stats_t* out) {
     if (!c || !out) return VR_ERR_INVALID_ARG;
     cudaSetDevice(c->dev);

@@ -78,6 +78,7 @@ def lib():
         L.vr_read_node.argtypes = [vp, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                    ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint16), vp]
         L.vr_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+        L.vr_debug_raise_error.argtypes = [vp, ctypes.c_int]
         L.vr_last_error.restype = ctypes.c_char_p
         L.vr_last_error.argtypes = [vp]
         L.vr_set_tile_shape.argtypes = [vp, ctypes.c_int, ctypes.c_int]
@@ -351,6 +352,10 @@ class Renderer:
     def refine(self, cam, image=None):
         """Refinement session of one view; call .pass_() and cache_update(refinement=True) until done."""
         return RefineSession(self, cam, image)
+
+    def debug_raise_error(self, code=1):
+        """Test hook: sets the device error word as a failed kernel check would (vr_debug_raise_error)."""
+        self._check(lib().vr_debug_raise_error(self._ctx, code))
 
     def stats(self) -> Stats:
         s = Stats()

@@ -6,13 +6,7 @@ from oracle import oracle as O
 RGBA_TOL = 2e-3  # max-abs RGBA, every pixel, against some admissible oracle result
 
 
-def admissible_error(gpu_rgba: np.ndarray, n_cand: np.ndarray, cand: np.ndarray) -> np.ndarray:
-    """Per-pixel max-abs error of gpu_rgba [n][4] to the nearest admissible oracle state."""
-    g = np.asarray(gpu_rgba, dtype=np.float64).reshape(-1, 1, 4)
-    c = cand.reshape(g.shape[0], O.MAXCAND, 4)
-    e = np.abs(c - g).max(axis=-1)
-    valid = np.arange(O.MAXCAND)[None, :] < n_cand.reshape(-1, 1)
-    return np.where(valid, e, np.inf).min(axis=-1)
+admissible_error = O.admissible_error  # per-pixel error to the nearest admissible oracle state
 
 
 def oracle_dense(volume: np.ndarray, brick, bg=0, tau=0, z_hi=None):
