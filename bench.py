@@ -275,7 +275,7 @@ def streamed_leg(torch, vr, S):
     return out
 
 
-def adjoint_leg(torch, vr, S, steps=200):
+def adjoint_leg(torch, vr, S, steps=200, check_grad=True):
     """512^3 x 3 SPIM-like volume, 512x512 view: fit TF tables [3,256,4] + scales [3] to a target
     rendered with other tables (seeds 201-203) and scales (0.8, 1, 1.25); mean-L2 loss, Adam lr 1e-2,
     hand-written adjoint with per-ray recompute."""
@@ -326,10 +326,35 @@ def adjoint_leg(torch, vr, S, steps=200):
     ((img - target) ** 2).mean().backward()
     f2.record()
     torch.cuda.synchronize()
+    grad = None
+    if check_grad:
+        # the adjoint against the oracle's FP64 gradient at the trained tables: dL/dImage random on
+        # 4096 random pixels (zero elsewhere), both sides on the same pixels
+        from oracle import oracle as O
+
+        vol = oracle_volume(w, torch)
+        cam = cams[0]
+        rng = np.random.default_rng(17)
+        n_px = 4096
+        px = rng.integers(0, cam["width"], n_px).astype(np.int32)
+        py = rng.integers(0, cam["height"], n_px).astype(np.int32)
+        dl = np.zeros((cam["height"], cam["width"], 4), np.float32)
+        g = rng.normal(size=(n_px, 4)).astype(np.float32)
+        dl[py, px] = g
+        tf_np, sc_np = tf.detach().cpu().numpy(), sc.detach().cpu().numpy()
+        r.set_transfer_functions(tf.detach(), sc.detach())
+        dtf, dsc = r.render_backward([cam], [torch.from_numpy(dl).cuda()])
+        torch.cuda.synchronize()
+        g_used = dl[py, px].astype(np.float64)  # duplicates keep the last write on both sides
+        u, first_idx = np.unique(py.astype(np.int64) * cam["width"] + px, return_index=True)
+        rtf, rsc = O.render_grad(vol, cam, tf_np, sc_np, (px[first_idx], py[first_idx]), g_used[first_idx])
+        dtf, dsc = dtf.cpu().numpy().astype(np.float64), dsc.cpu().numpy().astype(np.float64)
+        grad = {"pixels": int(first_idx.size), "tf_rel_err": float(np.linalg.norm(dtf - rtf) / np.linalg.norm(rtf)),
+                "scale_rel_err": float(np.linalg.norm(dsc - rsc) / np.linalg.norm(rsc)), "tolerance": 1e-3}
     r.close()
     return {"workload": w.name, "image": [cams[0]["width"], cams[0]["height"]], "adam_steps": steps,
             "ms_per_step": ms, "forward_ms": f0.elapsed_time(f1), "backward_ms": f1.elapsed_time(f2),
-            "loss_first": first, "loss_last": float(loss.item())}
+            "loss_first": first, "loss_last": float(loss.item()), "gradient_vs_oracle": grad}
 
 
 def table1_leg(torch, vr, S, frames=36, budget=64):
