@@ -674,6 +674,8 @@ def main():
     r.render([w.cameras[0]], [images[0]])
     frame0 = images[0].cpu().numpy()
     samples0 = r.stats().last_render_samples
+    r.render([w.cameras[0]], [images[0]], mode=vr.vr.VR_MODE_DVR | vr.vr.VR_RENDER_FP16)
+    frame0_fp16 = images[0].cpu().numpy()
 
     batched = adjoint = table1 = streamed = None
     if args.suite and rank == 0:
@@ -695,10 +697,14 @@ def main():
         nc, cand, osamp, pix = cpu_baseline.last
         g0 = frame0.reshape(-1, 4) if pix is None else frame0[pix[1], pix[0]]
         err = O.admissible_error(g0, nc, cand)
+        g16 = frame0_fp16.reshape(-1, 4) if pix is None else frame0_fp16[pix[1], pix[0]]
+        err16 = O.admissible_error(g16, nc, cand)
         parity = {"frame": 0, "pixels": int(err.size), "max_abs": float(err.max()), "mean_abs": float(err.mean()),
                   "tolerance": 2e-3, "pixels_over_tolerance": int((err > 2e-3).sum()),
                   "knife_edge_pixels": int((nc > 1).sum()),
-                  "samples_gpu": int(samples0), "samples_oracle": int(osamp.sum())}
+                  "samples_gpu": int(samples0), "samples_oracle": int(osamp.sum()),
+                  "fp16": {"max_abs": float(err16.max()), "mean_abs": float(err16.mean()),
+                           "bound": "max 2e-2, mean 2e-3"}}
         what = "every pixel" if args.cpu_rays <= 0 else f"{args.cpu_rays} random pixels"
         cpu = {"value": s / t, "unit": "samples/s", "cores": cores, "kind": "oracle",
                "sample": f"{what} of orbit frame 0 (1920x1080) against a streamed oracle volume of the full "
