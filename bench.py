@@ -664,11 +664,12 @@ def main():
                 # instructions per composited sample on the captured frames, at the live sample rate
                 ips = sum(d["thread_instructions_per_frame"]) / sum(samples_of[f] for f in fr)
                 mhz = clk.summary().get("sm_mhz") or 2032.0
-                ipeak = 148 * 4 * 32 * mhz * 1e6 / 1e12
+                sms = torch.cuda.get_device_properties(local).multi_processor_count
+                ipeak = sms * 4 * 32 * mhz * 1e6 / 1e12
                 ach = ips * (samples / args.steps / ws) / (render_ms / 1e3) / 1e12
                 issue = {"bound": "issue", "achieved": ach, "peak": ipeak, "unit": "T thread-instructions/s",
                          "frac": ach / ipeak, "thread_instructions_per_sample": ips,
-                         "peak_from": "148 SMs x 4 schedulers x 32 lanes x median SM clock"}
+                         "peak_from": f"{sms} SMs x 4 schedulers x 32 lanes x median SM clock"}
 
     # the GPU's orbit frame 0 (host copy) for the parity report against the oracle's frame
     r.render([w.cameras[0]], [images[0]])
