@@ -475,6 +475,7 @@ def main():
         w.cameras = [S.streamed(tau=3277, frame=f).cameras[0] for f in frames]
     else:
         w = S.large(tau=3277, frames=frames, dims=(1024, 1024, 256), nuclei=10000)
+        w.name = "medium-1024x1024x256x3"
     r = vr.Renderer(w.dims, 3, w.brick, tau=w.tau)
     build_s, spec = build_volume(w, r, torch)
     pool_gb = r.stats().pool_bytes / 1e9
