@@ -266,6 +266,18 @@ vr_status vr_plan_destroy(vr_render_plan* plan);
  * or 256) and CTAs per SM of the persistent grid.  Defaults 8 x 4, 256, 8. */
 vr_status vr_set_launch_shape(vr_ctx* ctx, int tile_w, int tile_h, int threads_per_cta, int ctas_per_sm);
 
+/* Order of the ray-tile queue of vr_render for DVR (FP32 or FP16; passes that read the store
+ * directly).  0: raster order.  1 (default): when the previous DVR vr_render call of this context
+ * had the same tile grid (the same number of views, image sizes and tile shape), its tiles are
+ * queued by the SM clock cycles each took there, costliest first (longest-processing-time-first
+ * list scheduling in 128 cost classes, four per power of two); the first call of a grid is in
+ * raster order.  Early ray termination makes tile costs very uneven, and in raster order a frame
+ * ends with a tail in which a few warps finish the longest rays while the rest of the GPU has run
+ * out of tiles.  A pixel does not depend on when its tile runs: images and sample counts are the
+ * same in either order.  MIP stays in raster order (its rays all run to the end; the cost order
+ * measured slower there).  Not part of the paper's method. */
+vr_status vr_set_tile_order(vr_ctx* ctx, int mode);
+
 /* Ray-tile shape of the render queue: each warp renders tile_w x tile_h pixels (tile_w * tile_h
  * must be 32).  Default 8 x 4.  Chosen per workload by the autotuner of the Python package. */
 vr_status vr_set_tile_shape(vr_ctx* ctx, int tile_w, int tile_h);

@@ -60,6 +60,14 @@ struct vr_ctx {
     float clip_default[VR_MAX_CLIP][4] = {};
     int tile_w = 8, tile_h = 4;
     int threads = 256, ctas_per_sm = 8; // render launch shape (autotuned per workload)
+    // tile queue order from the previous render of the same tile grid (costliest tiles first)
+    int tile_order_mode = 1;
+    unsigned int* lpt_cost = nullptr;
+    unsigned int* lpt_order = nullptr;
+    unsigned int* lpt_aux = nullptr;
+    long long lpt_cap = 0;
+    unsigned long long lpt_sig = 0;
+    bool lpt_have = false;
     // out-of-core render cache (cache_cap slots; 0 = renders read the store directly)
     long long cache_cap = 0;
     uint16_t* cache = nullptr;
@@ -121,10 +129,53 @@ static void dfree(vr_ctx* c, void* p) {
         cudaFree(p);
 }
 
+// Tile order of a vr_render call: when the previous call had the same tile grid, its measured tile
+// costs order the queue (costliest first); this call's costs are kept for the next.
+static vr_status order_prepare(vr_ctx* c, RenderArgs& a, const CamParam* cams, int n, long long tiles, cudaStream_t st) {
+    if (!c->tile_order_mode) return VR_OK;
+    unsigned long long sig = 1469598103934665603ull; // FNV-1a over the grid
+    auto mix = [&](long long v) {
+        sig ^= (unsigned long long)v;
+        sig *= 1099511628211ull;
+    };
+    mix(n);
+    mix(c->tile_w);
+    mix(c->tile_h);
+    for (int i = 0; i < n; ++i) {
+        mix(cams[i].W);
+        mix(cams[i].H);
+    }
+    if (tiles > c->lpt_cap) {
+        if (st) CK(c, cudaStreamSynchronize(st)); // the old buffers may still be in use
+        else CK(c, cudaDeviceSynchronize());
+        dfree(c, c->lpt_cost);
+        dfree(c, c->lpt_order);
+        dfree(c, c->lpt_aux);
+        c->lpt_cap = 0;
+        c->lpt_have = false;
+        c->lpt_cost = (unsigned int*)dalloc(c, sizeof(unsigned int) * (size_t)tiles);
+        c->lpt_order = (unsigned int*)dalloc(c, sizeof(unsigned int) * (size_t)tiles);
+        c->lpt_aux = (unsigned int*)dalloc(c, sizeof(unsigned int) * 256);
+        if (!c->lpt_cost || !c->lpt_order || !c->lpt_aux) return fail(c, VR_ERR_OUT_OF_MEMORY, "tile order buffers");
+        c->lpt_cap = tiles;
+    }
+    if (c->lpt_have && sig == c->lpt_sig) {
+        CK(c, launch_tile_order(c->lpt_cost, tiles, c->lpt_aux, c->lpt_order, st));
+        a.tile_order = c->lpt_order;
+    }
+    a.tile_cost = c->lpt_cost;
+    c->lpt_sig = sig;
+    c->lpt_have = true;
+    return VR_OK;
+}
+
 static void destroy_all(vr_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->dev);
     cudaDeviceSynchronize();
+    dfree(c, c->lpt_cost);
+    dfree(c, c->lpt_order);
+    dfree(c, c->lpt_aux);
     if (c->store_host) {
         if (c->pool) cudaFreeHost(c->pool);
     } else {
@@ -633,6 +684,10 @@ vr_status vr_render(vr_ctx* c, const vr_camera* cams, int n, float* const* image
     CK(c, cudaMemsetAsync(c->counter, 0, sizeof(unsigned long long), st));
     CK(c, cudaMemsetAsync(c->stats, 0, 2 * sizeof(unsigned long long), st));
     RenderArgs a = make_args(c, n, tiles);
+    if (mode == VR_MODE_DVR && !a.cache.cslot && !a.has_xf) {
+        s = order_prepare(c, a, c->h_cams, n, tiles, st);
+        if (s != VR_OK) return s;
+    }
     CK(c, launch_render(a, mode, fp16 && mode == VR_MODE_DVR, grid_for(c, tiles, c->threads, c->ctas_per_sm),
                         c->threads, st));
     return VR_OK;
@@ -1014,6 +1069,13 @@ vr_status vr_set_tile_shape(vr_ctx* c, int tw, int th) {
     if (!c || tw <= 0 || th <= 0 || tw * th != 32) return VR_ERR_INVALID_ARG;
     c->tile_w = tw;
     c->tile_h = th;
+    return VR_OK;
+}
+
+vr_status vr_set_tile_order(vr_ctx* c, int mode) {
+    if (!c || (mode != 0 && mode != 1)) return VR_ERR_INVALID_ARG;
+    c->tile_order_mode = mode;
+    c->lpt_have = false;
     return VR_OK;
 }
 

@@ -109,6 +109,8 @@ struct RenderArgs {
     float xf[MAXC][12];                 // channel c samples at xf[c] (3x4, row-major) applied to p
     unsigned int* vmark[MAXL];          // footprint mode: one bit per level-L voxel
     unsigned int* nmark;                // footprint mode: one bit per node
+    const unsigned int* tile_order;     // queue position -> tile (nullptr: raster order)
+    unsigned int* tile_cost;            // per tile: SM clock cycles / 64 it took (nullptr: not kept)
     float* dtf;                         // backward: [C][256][4]
     float* dscale;                      // backward: [C]
     int* err;
@@ -128,6 +130,8 @@ cudaError_t launch_read_voxels(const Geo& g, int L, const uint16_t* pool, const 
 cudaError_t launch_prepare_tf(int C, const float* tf, const float* scale, float4* tf2, float* scl, cudaStream_t st);
 cudaError_t launch_render(const RenderArgs& a, int mode, int fp16, int blocks, int threads, cudaStream_t st);
 cudaError_t launch_render_backward(const RenderArgs& a, int blocks, int threads, cudaStream_t st);
+cudaError_t launch_tile_order(const unsigned int* cost, long long tiles, unsigned int* aux, unsigned int* order,
+                              cudaStream_t st);
 cudaError_t launch_cache_gather(const uint16_t* store, uint16_t* cache, const int2* list, int n, long long slot_elems,
                                 cudaStream_t st);
 

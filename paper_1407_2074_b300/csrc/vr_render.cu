@@ -971,11 +971,26 @@ __global__ void __launch_bounds__(256, VR_RENDER_MIN_CTAS) render_kernel(RenderA
     const int lane = threadIdx.x & 31;
     unsigned long long* counter = reinterpret_cast<unsigned long long*>(a.counter);
     unsigned long long my_samples = 0, my_rays = 0;
+    // per-tile cost (optional): lane 0 notes the tile and the SM clock when it takes a tile and
+    // stores the difference when it takes the next one (the warp has converged there)
+    __shared__ unsigned s_ct_tile[8];
+    __shared__ long long s_ct_clk[8];
+    const int wib = threadIdx.x >> 5;
+    if (lane == 0) s_ct_tile[wib] = 0xffffffffu;
     for (;;) {
         unsigned long long tile = 0;
         if (lane == 0) tile = atomicAdd(counter, 1ull);
         tile = __shfl_sync(0xffffffffu, tile, 0);
+        if (a.tile_cost && lane == 0 && s_ct_tile[wib] != 0xffffffffu) {
+            const long long cyc = (clock64() - s_ct_clk[wib]) >> 6;
+            a.tile_cost[s_ct_tile[wib]] = cyc < 0xffffffffLL ? (unsigned)cyc : 0xffffffffu;
+        }
         if ((long long)tile >= a.total_tiles) break;
+        if (a.tile_order) tile = a.tile_order[tile];
+        if (a.tile_cost && lane == 0) {
+            s_ct_tile[wib] = (unsigned)tile;
+            s_ct_clk[wib] = clock64();
+        }
         const int ci = find_camera(a.cams, a.n_cams, (long long)tile);
         const CamParam* cp = &a.cams[ci];
         const long long lt = (long long)tile - cp->tile_begin;
@@ -1235,6 +1250,55 @@ __global__ void __launch_bounds__(128, 5) render_backward_kernel(RenderArgs a) {
         if (s_dtf[i] != 0.0f) atomicAdd(&a.dtf[i], s_dtf[i]);
 }
 
+// Queue order from the tile costs of an earlier frame of the same tile grid: costliest first
+// (longest-processing-time-first list scheduling), in NCLS classes of cost, four per power of
+// two (exponent and the two bits below the leading one); the order inside a class is whatever the
+// atomics give (a pixel does not depend on when its tile runs).
+// aux: [0, NCLS) class sizes, [NCLS, 2 NCLS) class cursors, zeroed before.
+constexpr int NCLS = 128;
+__device__ __forceinline__ int cost_class(unsigned c) {
+    if (c < 4u) return (int)c;
+    const int e = 31 - __clz(c);
+    return e * 4 + (int)((c >> (e - 2)) & 3u);
+}
+
+__global__ void tile_hist_kernel(const unsigned* __restrict__ cost, long long n, unsigned* aux) {
+    __shared__ unsigned h[NCLS];
+    if (threadIdx.x < NCLS) h[threadIdx.x] = 0;
+    __syncthreads();
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        atomicAdd(&h[cost_class(cost[i])], 1u);
+    __syncthreads();
+    if (threadIdx.x < NCLS && h[threadIdx.x]) atomicAdd(&aux[threadIdx.x], h[threadIdx.x]);
+}
+
+__global__ void tile_scatter_kernel(const unsigned* __restrict__ cost, long long n, unsigned* aux,
+                                    unsigned* __restrict__ order) {
+    __shared__ unsigned base[NCLS], cnt[NCLS];
+    if (threadIdx.x == 0) {
+        unsigned acc = 0;
+        for (int c = NCLS - 1; c >= 0; --c) {
+            base[c] = acc;
+            acc += aux[c];
+        }
+    }
+    if (threadIdx.x < NCLS) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        atomicAdd(&cnt[cost_class(cost[i])], 1u);
+    __syncthreads();
+    if (threadIdx.x < NCLS) {
+        base[threadIdx.x] += cnt[threadIdx.x] ? atomicAdd(&aux[NCLS + threadIdx.x], cnt[threadIdx.x]) : 0u;
+        cnt[threadIdx.x] = 0;
+    }
+    __syncthreads();
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int c = cost_class(cost[i]);
+        order[base[c] + atomicAdd(&cnt[c], 1u)] = (unsigned)i;
+    }
+}
+
 // One refinement pass over the pixels of a single camera: every unfinished ray resumes from its
 // saved sample index and compositing state, and either ends (pixel written) or stops again at its
 // next missing brick (state saved, counted in *pending).
@@ -1404,6 +1468,16 @@ static cudaError_t launch_bwd_c(const RenderArgs& a, int blocks, int threads, cu
         if (a.has_xf) launch_bwd_one<C, VS, false, true>(a, blocks, threads, st);
         else launch_bwd_one<C, VS, false, false>(a, blocks, threads, st);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tile_order(const unsigned* cost, long long tiles, unsigned* aux, unsigned* order, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(aux, 0, 2 * NCLS * sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    const long long b = (tiles + 1023) / 1024;
+    const int blocks = (int)(b < 1 ? 1 : (b > 148 ? 148 : b));
+    tile_hist_kernel<<<blocks, 1024, 0, st>>>(cost, tiles, aux);
+    tile_scatter_kernel<<<blocks, 1024, 0, st>>>(cost, tiles, aux, order);
     return cudaGetLastError();
 }
 

@@ -206,6 +206,36 @@ def test_tile_shapes_give_identical_images(tiny):
         assert np.array_equal(_render(r, w.cameras, tf, sc)[0], ref)
 
 
+def test_tile_order_from_previous_costs_changes_no_pixel(tiny):
+    from paper_1407_2074_b300 import vr as V
+
+    w, vol, ov = tiny
+    r = _build(vol, 16)
+    tf, sc = w.tf(), [1.0, 1.0, 1.0]
+    cams = S.batch_cameras(w.dims)[:9]
+    r.set_tile_order(0)
+    ref = _render(r, cams, tf, sc)
+    counts = (r.stats().last_render_samples, r.stats().last_render_rays)
+    ref1 = _render(r, w.cameras, tf, sc)[0]
+    r.set_tile_order(1)
+    for _ in range(3):  # raster order and costs first, then queued by the costs of the call before
+        for a, b in zip(_render(r, cams, tf, sc), ref):
+            assert np.array_equal(a, b)
+        assert (r.stats().last_render_samples, r.stats().last_render_rays) == counts
+    for _ in range(2):  # another grid starts over in raster order
+        assert np.array_equal(_render(r, w.cameras, tf, sc)[0], ref1)
+    fp16 = V.VR_MODE_DVR | V.VR_RENDER_FP16
+    r.set_tile_order(0)
+    ref16 = _render(r, cams, tf, sc, mode=fp16)
+    r.set_tile_order(1)
+    for _ in range(2):
+        for a, b in zip(_render(r, cams, tf, sc, mode=fp16), ref16):
+            assert np.array_equal(a, b)
+    with pytest.raises(V.VRError):
+        r.set_tile_order(2)
+    r.close()
+
+
 def _full_size_render(w, frames, tau, n_px, seed):
     import torch
     import paper_1407_2074_b300 as vr
