@@ -504,8 +504,9 @@ def main():
         st_ = r.stats()
         samples_of[f] = st_.last_render_samples
         rays_of[f] = st_.last_render_rays
-    # per-kernel launch count per step: level updates (N + 1) + the render kernel
-    launches_per_step = r.levels + 1
+    # per-kernel launch count per step: level updates (N + 1) + the two tile-order kernels (every
+    # timed render follows a render of the same tile grid) + the render kernel
+    launches_per_step = r.levels + 3
 
     def step(i, host=False, image_free=None):
         z0, b = blocks[i % len(blocks)]
