@@ -266,6 +266,17 @@ vr_status vr_plan_destroy(vr_render_plan* plan);
  * or 256) and CTAs per SM of the persistent grid.  Defaults 8 x 4, 256, 8. */
 vr_status vr_set_launch_shape(vr_ctx* ctx, int tile_w, int tile_h, int threads_per_cta, int ctas_per_sm);
 
+/* MIP ray segments (vr_render and render plans in VR_MODE_MIP that read the store directly, no
+ * per-channel transforms): with samples = n > 0, the samples k in [j n, (j+1) n) of every ray form
+ * segment j, the segments are separate work items (so the longest rays no longer run in one warp
+ * each), and a merge takes the per-channel maximum over them before the transfer functions.  A
+ * maximum does not round: the image and sample counts are the whole-ray ones bit for bit.  Used
+ * when some ray can be longer than one segment; the segment buffers (20 bytes per pixel and
+ * segment, 4 per tile and segment) are allocated through the context's allocator on first use.
+ * 0 turns segments off; otherwise 4 <= n <= 2^24.  Default 1024.  Not a step of the paper's
+ * method: a work decomposition of the MIP ray loop (Sec. "Basic Ray-Casting"). */
+vr_status vr_set_mip_segment_length(vr_ctx* ctx, int samples);
+
 /* Order of the ray-tile queue of vr_render for DVR (FP32 or FP16; passes that read the store
  * directly).  0: raster order.  1 (default): when the previous DVR vr_render call of this context
  * had the same tile grid (the same number of views, image sizes and tile shape), its tiles are

@@ -19,6 +19,15 @@
 
 using namespace vrk;
 
+// Buffers of MIP ray segments (grown on demand; a render plan owns its own).
+struct SegBuf {
+    float4* v = nullptr;
+    unsigned int* meta = nullptr;
+    unsigned int* done = nullptr;
+    long long cap_entries = 0; // (segment, tile, lane) entries of v and meta
+    long long cap_done = 0;    // (segment, tile) flags
+};
+
 struct vr_ctx {
     int dev = 0;
     Geo g{};
@@ -62,6 +71,8 @@ struct vr_ctx {
     int threads = 256, ctas_per_sm = 8; // render launch shape (autotuned per workload)
     // tile queue order from the previous render of the same tile grid (costliest tiles first)
     int tile_order_mode = 1;
+    int kseg_mip = 1024; // MIP: samples per ray segment (0: rays marched whole)
+    SegBuf seg;
     unsigned int* lpt_cost = nullptr;
     unsigned int* lpt_order = nullptr;
     unsigned int* lpt_aux = nullptr;
@@ -169,10 +180,56 @@ static vr_status order_prepare(vr_ctx* c, RenderArgs& a, const CamParam* cams, i
     return VR_OK;
 }
 
+static void seg_free(vr_ctx* c, SegBuf& b) {
+    dfree(c, b.v);
+    dfree(c, b.meta);
+    dfree(c, b.done);
+    b = SegBuf();
+}
+
+// MIP segments for these cameras (a ray inside the volume box is at most its diagonal long); fills
+// the segment fields of `a` and grows `b`, or leaves nseg = 0 when every ray fits one segment.
+static vr_status seg_prepare(vr_ctx* c, SegBuf& b, RenderArgs& a, const CamParam* cams, int n, long long tiles,
+                             cudaStream_t st) {
+    a.nseg = 0;
+    if (c->kseg_mip <= 0 || a.cache.cslot || a.has_xf) return VR_OK;
+    const double dx = (double)c->g.ldim[0][0], dy = (double)c->g.ldim[0][1], dz = (double)c->g.ldim[0][2];
+    const double diag = std::sqrt(dx * dx + dy * dy + dz * dz);
+    long long ns = 0;
+    for (int i = 0; i < n; ++i) {
+        double k = std::ceil(diag / (double)cams[i].dt) + 2.0;
+        if (k > (double)(1 << 24)) k = (double)(1 << 24);
+        ns = std::max(ns, ((long long)k + c->kseg_mip - 1) / c->kseg_mip);
+    }
+    if (ns <= 1 || ns * tiles >= 0xffffffffLL) return VR_OK;
+    const long long entries = ns * tiles * 32, done = ns * tiles;
+    if (entries > b.cap_entries || done > b.cap_done) {
+        if (st) CK(c, cudaStreamSynchronize(st)); // the old buffers may still be in use
+        else CK(c, cudaDeviceSynchronize());
+        seg_free(c, b);
+        b.v = (float4*)dalloc(c, sizeof(float4) * (size_t)entries);
+        b.meta = (unsigned int*)dalloc(c, sizeof(unsigned int) * (size_t)entries);
+        b.done = (unsigned int*)dalloc(c, sizeof(unsigned int) * (size_t)done);
+        if (!b.v || !b.meta || !b.done) {
+            seg_free(c, b);
+            return fail(c, VR_ERR_OUT_OF_MEMORY, "ray segment buffers");
+        }
+        b.cap_entries = entries;
+        b.cap_done = done;
+    }
+    a.kseg = c->kseg_mip;
+    a.nseg = (int)ns;
+    a.seg_v = b.v;
+    a.seg_meta = b.meta;
+    a.seg_done = b.done;
+    return VR_OK;
+}
+
 static void destroy_all(vr_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->dev);
     cudaDeviceSynchronize();
+    seg_free(c, c->seg);
     dfree(c, c->lpt_cost);
     dfree(c, c->lpt_order);
     dfree(c, c->lpt_aux);
@@ -688,6 +745,10 @@ vr_status vr_render(vr_ctx* c, const vr_camera* cams, int n, float* const* image
         s = order_prepare(c, a, c->h_cams, n, tiles, st);
         if (s != VR_OK) return s;
     }
+    if (mode == VR_MODE_MIP) {
+        s = seg_prepare(c, c->seg, a, c->h_cams, n, tiles, st);
+        if (s != VR_OK) return s;
+    }
     CK(c, launch_render(a, mode, fp16 && mode == VR_MODE_DVR, grid_for(c, tiles, c->threads, c->ctas_per_sm),
                         c->threads, st));
     return VR_OK;
@@ -1072,6 +1133,12 @@ vr_status vr_set_tile_shape(vr_ctx* c, int tw, int th) {
     return VR_OK;
 }
 
+vr_status vr_set_mip_segment_length(vr_ctx* c, int samples) {
+    if (!c || samples < 0 || (samples > 0 && samples < 4) || samples > (1 << 24)) return VR_ERR_INVALID_ARG;
+    c->kseg_mip = samples;
+    return VR_OK;
+}
+
 vr_status vr_set_tile_order(vr_ctx* c, int mode) {
     if (!c || (mode != 0 && mode != 1)) return VR_ERR_INVALID_ARG;
     c->tile_order_mode = mode;
@@ -1092,6 +1159,7 @@ vr_status vr_set_launch_shape(vr_ctx* c, int tw, int th, int threads, int ctas_p
 
 struct vr_render_plan {
     vr_ctx* c = nullptr;
+    SegBuf seg;
     CamParam* d_cams = nullptr;
     unsigned int* counter = nullptr;
     unsigned long long* stats = nullptr;
@@ -1103,6 +1171,7 @@ static void plan_free(vr_render_plan* p) {
     if (!p) return;
     if (p->exec) cudaGraphExecDestroy(p->exec);
     if (p->graph) cudaGraphDestroy(p->graph);
+    seg_free(p->c, p->seg);
     dfree(p->c, p->d_cams);
     dfree(p->c, p->counter);
     dfree(p->c, p->stats);
@@ -1146,6 +1215,13 @@ vr_status vr_plan_create(vr_ctx* c, const vr_camera* cams, int n, float* const* 
     a.cams = p->d_cams;
     a.counter = p->counter;
     a.stats = p->stats;
+    if (e == cudaSuccess && mode == VR_MODE_MIP) {
+        s = seg_prepare(c, p->seg, a, h.data(), n, tiles, nullptr);
+        if (s != VR_OK) {
+            plan_free(p);
+            return s;
+        }
+    }
     cudaStream_t cs = nullptr;
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);

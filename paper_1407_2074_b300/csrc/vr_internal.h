@@ -109,6 +109,11 @@ struct RenderArgs {
     float xf[MAXC][12];                 // channel c samples at xf[c] (3x4, row-major) applied to p
     unsigned int* vmark[MAXL];          // footprint mode: one bit per level-L voxel
     unsigned int* nmark;                // footprint mode: one bit per node
+    // MIP ray segments: samples k in [j kseg, (j+1) kseg) of a ray are segment j (nseg == 0: whole rays)
+    int kseg, nseg;
+    float4* seg_v;                      // [nseg][total_tiles][32] per-channel maxima of the segment
+    unsigned int* seg_meta;             // [nseg][total_tiles][32] samples << 2 | 2 when the ray goes on
+    unsigned int* seg_done;             // [nseg][total_tiles] 0 pending, 1 done, 3 done and rays go on
     const unsigned int* tile_order;     // queue position -> tile (nullptr: raster order)
     unsigned int* tile_cost;            // per tile: SM clock cycles / 64 it took (nullptr: not kept)
     float* dtf;                         // backward: [C][256][4]

@@ -137,8 +137,11 @@ struct TFLookup {
 template <int C, int VS, bool POW2, bool H, class F>
 __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restrict__ pool,
                                            const RNode* __restrict__ rn, const CamParam& cp, const float d[3], float t0,
-                                           float t1, F& f, const CacheArgs* ca = nullptr, int k0 = 0) {
+                                           float t1, F& f, const CacheArgs* ca = nullptr, int k0 = 0,
+                                           int kend = MAX_SAMPLES) {
+    // samples k0 <= k < min(kend, MAX_SAMPLES) inside [t0, t1)
     const float dt = cp.dt;
+    const int klim = kend < MAX_SAMPLES ? kend : MAX_SAMPLES;
     const float eye[3] = {cp.eye[0], cp.eye[1], cp.eye[2]}; // in registers: cp lives in global memory
     const int N = g.N, M = g.M, S = g.S;
     const int mlog = __ffs(M) - 1; // log2(M) when POW2
@@ -261,7 +264,7 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
     float kf = (float)k0; // == (float)k, exact below 2^24
     for (;; ++k, kf += 1.0f) {
         const float tk = __fadd_rn(t0, __fmul_rn(kf, dt));
-        if (!(tk < t1) || k >= MAX_SAMPLES) break;
+        if (!(tk < t1) || k >= klim) break;
         const float ell = fminf(dt, __fsub_rn(t1, tk));
         float p[3];
 #pragma unroll
@@ -388,7 +391,7 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
                 // the next sample too when it lies in the same brick node at the same level with a
                 // full segment: both are shaded before the two are composited in order, so the
                 // gathers and lookups of the second overlap those of the first
-                if (ell == dt && k + 1 < MAX_SAMPLES) {
+                if (ell == dt && k + 1 < klim) {
                     const float kf2 = kf + 1.0f;
                     const float tk2 = __fadd_rn(t0, __fmul_rn(kf2, dt));
                     if (tk2 < t1 && __fsub_rn(t1, tk2) >= dt && tk2 < tnext && tk2 < tl_limit) {
@@ -436,7 +439,7 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
                 // k..k+n-1 that stay in this node with a full segment, using the same per-sample
                 // single-precision tests as above (monotone in k), and composite it in one step.
                 auto in_run = [&](int kk) -> bool {
-                    if (kk >= MAX_SAMPLES) return false;
+                    if (kk >= klim) return false;
                     const float t = __fadd_rn(t0, __fmul_rn((float)kk, dt));
                     if (!(t < t1) || !(t < tl_limit) || !(__fsub_rn(t1, t) >= dt)) return false;
 #pragma unroll
@@ -1299,6 +1302,134 @@ __global__ void tile_scatter_kernel(const unsigned* __restrict__ cost, long long
     }
 }
 
+// ---- MIP ray segments ----
+// A MIP ray is the per-channel maximum over its samples, so it splits without approximation: the
+// samples k in [j kseg, (j+1) kseg) of every ray of a tile are work item j * total_tiles + tile
+// (segment-major), each records its per-channel maxima and sample count, and a merge takes the
+// maximum over the segments and applies the transfer functions.  The image is the whole-ray
+// image bit for bit; the longest rays no longer run in one warp each.
+constexpr unsigned SEG_END_RAY = 0u, SEG_GOES_ON = 2u;
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// seg_done[segment][tile]: 0 pending, 1 done and no ray of the tile goes on, 3 done and some do
+template <int C, int VS, bool POW2>
+__global__ void __launch_bounds__(256, VR_RENDER_MIN_CTAS) mip_seg_kernel(RenderArgs a) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long* counter = reinterpret_cast<unsigned long long*>(a.counter);
+    unsigned long long my_rays = 0;
+    const unsigned long long items = (unsigned long long)(a.total_tiles * a.nseg);
+    for (;;) {
+        unsigned long long q = 0;
+        if (lane == 0) q = atomicAdd(counter, 1ull);
+        q = __shfl_sync(0xffffffffu, q, 0);
+        if (q >= items) break;
+        const int seg = (int)(q / (unsigned long long)a.total_tiles);
+        const long long tile = (long long)q - (long long)seg * a.total_tiles;
+        const CamParam* cp = &a.cams[find_camera(a.cams, a.n_cams, tile)];
+        int px, py;
+        tile_pixel(tile - cp->tile_begin, cp->tiles_x, a.tile_w, a.tile_h, lane, px, py);
+        const bool inimg = px < cp->W && py < cp->H;
+        const long long slot = ((long long)seg * a.total_tiles + tile) * 32 + lane;
+        bool work = inimg;
+        if (seg > 0) {
+            unsigned pd = 0;
+            if (lane == 0) pd = ld_acquire_u32(&a.seg_done[(long long)(seg - 1) * a.total_tiles + tile]);
+            pd = __shfl_sync(0xffffffffu, pd, 0);
+            __syncwarp();
+            if (pd == 1u) { // every ray of the tile ended before this segment
+                if (lane == 0) st_release_u32(&a.seg_done[(long long)seg * a.total_tiles + tile], 1u);
+                continue;
+            }
+            // previous segment done: only the rays that went on; not done yet: every ray (a ray
+            // that ended before this segment finds no sample in it)
+            if (pd == 3u && work) work = (__ldcg(&a.seg_meta[slot - a.total_tiles * 32]) & 3u) == SEG_GOES_ON;
+        }
+        float4 part = make_float4(-1.0f, -1.0f, -1.0f, -1.0f);
+        unsigned meta = SEG_END_RAY;
+        float dd[3], r0, r1;
+        if (work && ray_setup(*cp, a.g, px, py, dd, r0, r1)) {
+            if (seg == 0) ++my_rays;
+            MIPMax<C> f;
+            const int k0 = seg * a.kseg, k1 = k0 + a.kseg;
+            const long long k = march<C, VS, POW2, false>(a.g, a.pool, a.rnodes, *cp, dd, r0, r1, f, nullptr, k0, k1);
+            const bool cont = k == k1 && __fadd_rn(r0, __fmul_rn((float)k1, cp->dt)) < r1;
+            meta = ((unsigned)(k - k0) << 2) | (cont ? SEG_GOES_ON : SEG_END_RAY);
+#pragma unroll
+            for (int c = 0; c < C; ++c) (&part.x)[c] = f.mx[c];
+        }
+        if (inimg) {
+            a.seg_v[slot] = part;
+            a.seg_meta[slot] = meta;
+        }
+        const bool any = __ballot_sync(0xffffffffu, (meta & 3u) == SEG_GOES_ON) != 0u;
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence();
+            st_release_u32(&a.seg_done[(long long)seg * a.total_tiles + tile], any ? 3u : 1u);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) my_rays += __shfl_xor_sync(0xffffffffu, my_rays, o);
+    if (lane == 0 && a.stats) atomicAdd(&a.stats[1], my_rays);
+}
+
+// merge: one warp per tile (grid-stride), a lane per pixel; the same transfer-function step as
+// the whole-ray MIP pass
+template <int C>
+__global__ void __launch_bounds__(256) mip_merge_kernel(RenderArgs a) {
+    extern __shared__ float4 s_tf[];
+    __shared__ float s_scl[MAXC];
+    load_tables(a, C, s_tf, s_scl);
+    const int lane = threadIdx.x & 31;
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    unsigned long long my_samples = 0;
+    for (long long tile = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); tile < a.total_tiles;
+         tile += nwarps) {
+        const CamParam* cp = &a.cams[find_camera(a.cams, a.n_cams, tile)];
+        int px, py;
+        tile_pixel(tile - cp->tile_begin, cp->tiles_x, a.tile_w, a.tile_h, lane, px, py);
+        if (px >= cp->W || py >= cp->H) continue;
+        float mx[C];
+        unsigned long long n = 0;
+        for (int j = 0; j < a.nseg; ++j) {
+            const long long slot = ((long long)j * a.total_tiles + tile) * 32 + lane;
+            const unsigned m = a.seg_meta[slot];
+            const float4 v = a.seg_v[slot];
+#pragma unroll
+            for (int c = 0; c < C; ++c) mx[c] = j == 0 ? (&v.x)[c] : fmaxf(mx[c], (&v.x)[c]);
+            n += m >> 2;
+            if ((m & 3u) != SEG_GOES_ON) break;
+        }
+        float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (n > 0) {
+            float A = 0.f, Cr = 0.f, Cg = 0.f, Cb = 0.f;
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                TFLookup<C> t;
+                t.eval(s_tf, s_scl, c, mx[c]);
+                const float al = fminf(fmaxf(t.al, 0.0f), ALPHA_MAX);
+                const float w = (1.0f - A) * al;
+                Cr = fmaf(w, t.r, Cr);
+                Cg = fmaf(w, t.g, Cg);
+                Cb = fmaf(w, t.b, Cb);
+                A += w;
+            }
+            out = make_float4(Cr, Cg, Cb, A);
+        }
+        reinterpret_cast<float4*>(cp->img)[(long long)py * cp->W + px] = out;
+        my_samples += n;
+    }
+    for (int o = 16; o > 0; o >>= 1) my_samples += __shfl_xor_sync(0xffffffffu, my_samples, o);
+    if (lane == 0 && a.stats) atomicAdd(&a.stats[0], my_samples);
+}
+
 // One refinement pass over the pixels of a single camera: every unfinished ray resumes from its
 // saved sample index and compositing state, and either ends (pixel written) or stops again at its
 // next missing brick (state saved, counted in *pending).
@@ -1425,6 +1556,17 @@ static cudaError_t launch_fwd_c(const RenderArgs& a, int mode, int fp16, int blo
             if (p2) launch_one<C, VS, 1, true, false, true>(a, blocks, threads, st);
             else launch_one<C, VS, 1, false, false, true>(a, blocks, threads, st);
         }
+        return cudaGetLastError();
+    }
+    if (mode == 1 && a.nseg > 0) { // MIP in ray segments: segments, then the merge
+        cudaMemsetAsync(a.seg_done, 0, sizeof(unsigned) * (size_t)a.nseg * (size_t)a.total_tiles, st);
+        if (p2) mip_seg_kernel<C, VS, true><<<blocks, threads, 0, st>>>(a);
+        else mip_seg_kernel<C, VS, false><<<blocks, threads, 0, st>>>(a);
+        const long long mb = (a.total_tiles + 7) / 8;
+        const int mblocks = (int)(mb < 1 ? 1 : (mb > 4096 ? 4096 : mb));
+        const size_t smem = (size_t)C * 512 * sizeof(float4);
+        cudaFuncSetAttribute(mip_merge_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        mip_merge_kernel<C><<<mblocks, 256, smem, st>>>(a);
         return cudaGetLastError();
     }
     if (mode == 0 && fp16) {
