@@ -206,6 +206,21 @@ def test_tile_shapes_give_identical_images(tiny):
         assert np.array_equal(_render(r, w.cameras, tf, sc)[0], ref)
 
 
+def test_tile_order_buffers_grow_and_shrink_with_the_grid(tiny):
+    w, vol, ov = tiny
+    r = _build(vol, 16)
+    tf, sc = w.tf(), [1.0, 1.0, 1.0]
+    small = dict(w.cameras[0], width=40, height=24)
+    large = dict(w.cameras[0], width=333, height=197)  # ragged tiles
+    r.set_tile_order(0)
+    ref_s, ref_l = _render(r, [small], tf, sc)[0], _render(r, [large], tf, sc)[0]
+    r.set_tile_order(1)
+    for cam, ref in ((small, ref_s), (small, ref_s), (large, ref_l), (large, ref_l), (small, ref_s),
+                     (large, ref_l), (large, ref_l), (small, ref_s), (small, ref_s)):
+        assert np.array_equal(_render(r, [cam], tf, sc)[0], ref)
+    r.close()
+
+
 def test_tile_order_from_previous_costs_changes_no_pixel(tiny):
     from paper_1407_2074_b300 import vr as V
 
