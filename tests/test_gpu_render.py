@@ -427,10 +427,11 @@ def test_graph_plan_matches_render_and_sees_updates(tiny, tmp_path, monkeypatch)
     tf, sc = w.tf(), [1.0, 1.0, 1.0]
     ref = _render(r, cams, tf, sc)
     plan = r.plan(cams)
-    plan.launch()
-    torch.cuda.synchronize()
-    for a, b in zip(plan.images, ref):
-        assert np.array_equal(a.cpu().numpy(), b)
+    for _ in range(3):  # from the second replay on, tiles are queued by the previous replay's costs
+        plan.launch()
+        torch.cuda.synchronize()
+        for a, b in zip(plan.images, ref):
+            assert np.array_equal(a.cpu().numpy(), b)
     s_plan, rays = plan.samples()
     r.render(cams)
     assert s_plan == r.stats().last_render_samples and rays > 0
