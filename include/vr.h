@@ -17,7 +17,9 @@
  *   - Stream-ordered calls take a cudaStream_t passed as void* (NULL = the legacy default
  *     stream).  Borrowed input pointers must stay valid until the stream reaches the call.
  *   - The library owns its device memory (brick pool, node tables, staging); callers own
- *     images and gradient buffers.  A context is not thread-safe.
+ *     images and gradient buffers.  A context is not thread-safe, and its render calls share
+ *     the context's work queue and scratch buffers: calls of one context issued on different
+ *     streams must not overlap on the GPU (use one stream, or order the streams).
  *   - Coordinates are level-0 voxel units; voxel i is centred at i + 0.5.
  *   - There is no CPU fallback: without a CUDA device vr_create fails with VR_ERR_CUDA.
  */

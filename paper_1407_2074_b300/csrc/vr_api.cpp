@@ -157,8 +157,7 @@ static vr_status order_prepare(vr_ctx* c, RenderArgs& a, const CamParam* cams, i
         mix(cams[i].H);
     }
     if (tiles > c->lpt_cap) {
-        if (st) CK(c, cudaStreamSynchronize(st)); // the old buffers may still be in use
-        else CK(c, cudaDeviceSynchronize());
+        CK(c, cudaDeviceSynchronize()); // the old buffers may still be in use (any stream)
         dfree(c, c->lpt_cost);
         dfree(c, c->lpt_order);
         dfree(c, c->lpt_aux);
@@ -204,8 +203,7 @@ static vr_status seg_prepare(vr_ctx* c, SegBuf& b, RenderArgs& a, const CamParam
     if (ns <= 1 || ns * tiles >= 0xffffffffLL) return VR_OK;
     const long long entries = ns * tiles * 32, done = ns * tiles;
     if (entries > b.cap_entries || done > b.cap_done) {
-        if (st) CK(c, cudaStreamSynchronize(st)); // the old buffers may still be in use
-        else CK(c, cudaDeviceSynchronize());
+        CK(c, cudaDeviceSynchronize()); // the old buffers may still be in use (any stream)
         seg_free(c, b);
         b.v = (float4*)dalloc(c, sizeof(float4) * (size_t)entries);
         b.meta = (unsigned int*)dalloc(c, sizeof(unsigned int) * (size_t)entries);
