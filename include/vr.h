@@ -279,8 +279,8 @@ vr_status vr_set_launch_shape(vr_ctx* ctx, int tile_w, int tile_h, int threads_p
  * method: a work decomposition of the MIP ray loop (Sec. "Basic Ray-Casting"). */
 vr_status vr_set_mip_segment_length(vr_ctx* ctx, int samples);
 
-/* Order of the ray-tile queue of vr_render for DVR (FP32 or FP16; passes that read the store
- * directly).  0: raster order.  1 (default): when the previous DVR vr_render call of this context
+/* Order of the ray-tile queue of vr_render for DVR (FP32 or FP16, with or without per-channel
+ * transforms or the out-of-core render cache).  0: raster order.  1 (default): when the previous DVR vr_render call of this context
  * had the same tile grid (the same number of views, image sizes and tile shape), its tiles are
  * queued by the SM clock cycles each took there, costliest first (longest-processing-time-first
  * list scheduling in 128 cost classes, four per power of two); the first call of a grid is in

@@ -739,7 +739,7 @@ vr_status vr_render(vr_ctx* c, const vr_camera* cams, int n, float* const* image
     CK(c, cudaMemsetAsync(c->counter, 0, sizeof(unsigned long long), st));
     CK(c, cudaMemsetAsync(c->stats, 0, 2 * sizeof(unsigned long long), st));
     RenderArgs a = make_args(c, n, tiles);
-    if (mode == VR_MODE_DVR && !a.cache.cslot && !a.has_xf) {
+    if (mode == VR_MODE_DVR) { // whole-ray, per-channel-transform and render-cache passes alike
         s = order_prepare(c, a, c->h_cams, n, tiles, st);
         if (s != VR_OK) return s;
     }
