@@ -114,7 +114,9 @@ typedef struct {
 vr_status vr_create(const int64_t dims[3], int channels, int brick_size, const vr_options* opts,
                     const vr_allocator* alloc, vr_ctx** out);
 
-/* Release every resource of the context (synchronises the device first). */
+/* Release every resource of the context (synchronises the device first).  A library utility, not
+ * a step of the method: the paper's renderer lives as long as its application.  Also the one call
+ * that still succeeds after a device error (VR_ERR_STATE).  Errors: VR_ERR_INVALID_ARG (NULL). */
 vr_status vr_destroy(vr_ctx* ctx);
 
 /* Insert the cuboid block [origin, origin + extent) of values block[ez][ey][ex][C] (uint16, the
@@ -172,11 +174,14 @@ vr_status vr_render(vr_ctx* ctx, const vr_camera* cams, int n_cams, float* const
  * and transfer functions must exist already), but the ray-tile queue, the sample counters and the
  * per-camera constants live in one fixed device array of libvr (about 15 KB, held by every GPU
  * that loads the library until the process exits) instead of buffers the library allocates.
+ * The launch shape is the context's (vr_set_launch_shape); DVR tiles run in raster order (no
+ * cost-ordered queue, whose order buffers are allocated), which changes no pixel.
  * At most VR_NOALLOC_MAX_CAMERAS cameras per call (VR_ERR_INVALID_ARG beyond).  The first call on
- * a device looks the array up (cudaGetSymbolAddress); make that first call before any stream
- * capture.  Every call reuses the same array: calls that can overlap on the GPU (other streams,
- * other contexts on the same device) race and must be serialised by the caller.  The call does not
- * update vr_stats' last_render_* counters. */
+ * a device looks the array up (cudaGetSymbolAddress).  The per-camera constants are copied from the
+ * caller's host stack by cudaMemcpyAsync, so a call must not be recorded into a CUDA graph by
+ * stream capture (render plans, vr_plan_*, are the capturable form).  Every call reuses the same
+ * array: calls that can overlap on the GPU (other streams, other contexts on the same device) race
+ * and must be serialised by the caller.  The call does not update vr_stats' last_render_* counters. */
 #define VR_NOALLOC_MAX_CAMERAS 64
 vr_status vr_render_noalloc(vr_ctx* ctx, const vr_camera* cams, int n_cams, float* const* images, int mode,
                             void* cuda_stream);
@@ -228,7 +233,11 @@ vr_status vr_refine_pass(vr_refine* r, void* cuda_stream, int64_t* pending, int6
 vr_status vr_refine_end(vr_refine* r);
 
 /* Test hook: level L of the volume as out[Z_L][Y_L][X_L][C] (host buffer), gathered from the
- * brick pool (never-touched bricks read as the background).  Synchronises the stream. */
+ * brick pool (never-touched bricks read as the background).  Synchronises the stream.  Reads back
+ * the state the paper defines in Sec. "CPU Data Structure" (level L is the iterated 2x2x2
+ * half-sampling of level 0, Eq. 1) so that it can be checked voxel for voxel; not a step of the
+ * method.  Errors: VR_ERR_INVALID_ARG (level outside 0..N, NULL out), VR_ERR_DEVICE_ASSERT,
+ * VR_ERR_STATE, VR_ERR_CUDA. */
 vr_status vr_read_level(vr_ctx* ctx, int level, uint16_t* out, void* cuda_stream);
 
 /* Test hook: values of n level-L voxels, xyz[n][3] (host) -> out[n][C] (host).  Synchronises.
@@ -240,6 +249,9 @@ vr_status vr_read_voxels(vr_ctx* ctx, int level, int64_t n, const int64_t* xyz, 
 vr_status vr_read_node(vr_ctx* ctx, int level, int64_t i, int64_t j, int64_t k, uint32_t* flags, uint16_t* avg,
                        void* cuda_stream);
 
+/* Library utility (no counterpart in the paper): sizes of the tree and the pool, and the sample
+ * and ray counts of the last vr_render (the work units of the measurement).  Host-side, does not
+ * synchronise.  Errors: VR_ERR_INVALID_ARG (NULL). */
 vr_status vr_stats(vr_ctx* ctx, vr_stats_t* out);
 
 /* Test hook (no counterpart in the paper): writes code (!= 0) into the context's device error
@@ -295,7 +307,9 @@ vr_status vr_set_tile_order(vr_ctx* ctx, int mode);
  * must be 32).  Default 8 x 4.  Chosen per workload by the autotuner of the Python package. */
 vr_status vr_set_tile_shape(vr_ctx* ctx, int tile_w, int tile_h);
 
-/* Message of the last error of this context (or of the last failed vr_create when ctx is NULL). */
+/* Library utility (no counterpart in the paper): message of the last error of this context (or of
+ * the last failed vr_create when ctx is NULL).  The string is owned by the library and valid
+ * until the next call on the same context. */
 const char* vr_last_error(const vr_ctx* ctx);
 
 #ifdef __cplusplus

@@ -23,12 +23,23 @@
  *
  * Precision: values, interpolation, transfer functions, compositing and
  * gradients are FP64.  Ray GEOMETRY (directions, entry/exit, sample
- * positions, level and node choice) is evaluated in IEEE single precision in
- * a fixed operation order, because those quantities decide integers (the
- * level, the node) and the CUDA path takes the same decisions in single
- * precision.  The ERT decision (A >= ert) compares accumulated opacity and
- * cannot be mirrored; the oracle reports every admissible stopping state in
- * the band |A - ert| < OR_ERT_BAND.
+ * positions, level and node choice) is evaluated in one of two ways:
+ *   OR_GEOM_FP64 (or_render, or_render_xf, or_render_check): in double
+ *     precision, the definition.  Some decisions are discontinuous -- the
+ *     level floor at t_L and the child choice at a split plane -- and a
+ *     single-precision implementation may correctly take either branch when
+ *     the quantity lies within its rounding error of the threshold.  Such
+ *     decisions (whose two branches also sample differently) are flagged;
+ *     or_render_check marches every combination of the first OR_MAXFLAG of
+ *     them per ray and compares a given pixel with the nearest admissible
+ *     result; a ray with more flagged decisions is "unresolved".
+ *   OR_GEOM_FP32 (or_render_geo, or_render_cache and the adjoint): in IEEE
+ *     single precision in a fixed operation order, mirroring a single-
+ *     precision implementation decision for decision (the brick-cache flags
+ *     are compared bit for bit; the adjoint is the derivative of the render at
+ *     the forward's own decisions).
+ * The ERT decision (A >= ert) compares accumulated opacity; every state in
+ * the band |A - ert| < OR_ERT_BAND is an admissible stopping state.
  *
  * Parity pins: see tests/test_oracle_*.py (closed forms, hand-computed
  * golden values, invariants, brute force on tiny inputs).
@@ -45,6 +56,9 @@ extern "C" {
 #define OR_MAXC 4
 #define OR_MAXCAND 4
 #define OR_ERT_BAND 2e-4
+#define OR_MAXFLAG 3 /* knife-edge decisions enumerated per ray: up to 2^3 variants */
+#define OR_GEOM_FP32 0
+#define OR_GEOM_FP64 1
 
 typedef struct {
     int64_t dim[3];          /* level-0 extent X, Y, Z */
@@ -118,7 +132,8 @@ typedef struct {
     int64_t samples;                 /* samples composited with the natural decisions */
 } or_pixel;
 
-/* Renders the listed pixels.  tf: [C][256][4] (table entries in [0,1]), scale: [C].
+/* Renders the listed pixels with double-precision geometry and the natural branch of every
+ * decision.  tf: [C][256][4] (table entries in [0,1]), scale: [C].
  * mode 0 = emission-absorption (Algorithm 1), mode 1 = maximum intensity projection. */
 int or_render(or_volume* v, const or_camera* cam, const float* tf, const float* scale, int mode, int64_t n,
               const int32_t* px, const int32_t* py, or_pixel* out, int threads);
@@ -127,6 +142,28 @@ int or_render(or_volume* v, const or_camera* cam, const float* tf, const float* 
  * Aberration"): channel c samples the volume at xf[c] * p, xf [C][3][4] (NULL = identity). */
 int or_render_xf(or_volume* v, const or_camera* cam, const float* tf, const float* scale, const float* xf, int mode,
                  int64_t n, const int32_t* px, const int32_t* py, or_pixel* out, int threads);
+/* As or_render_xf with the geometry chosen: OR_GEOM_FP64 or OR_GEOM_FP32. */
+int or_render_geo(or_volume* v, const or_camera* cam, const float* tf, const float* scale, const float* xf, int mode,
+                  int geometry, int64_t n, const int32_t* px, const int32_t* py, or_pixel* out, int threads);
+
+/* Parity check of rendered pixels (A16 reading: several results are correct).  For pixel i,
+ * err = the smallest max-abs difference between rgba[i] (RGBA, e.g. a GPU image's pixel) and an
+ * admissible result: any stopping state within the early-termination band, on any combination of
+ * branches of the ray's first OR_MAXFLAG knife-edge decisions (OR_GEOM_FP64; with OR_GEOM_FP32 the
+ * mirrored decisions only).  Enumeration of a ray stops once a variant is within stop_err (0:
+ * march every variant). */
+typedef struct {
+    double err;        /* smallest max-abs RGBA difference to an admissible result */
+    double rgba[4];    /* natural result */
+    int64_t samples;   /* natural sample count */
+    int flagged;       /* knife-edge decisions met on the natural march */
+    int variants;      /* decision variants marched */
+    int unresolved;    /* some march met more than OR_MAXFLAG knife-edge decisions */
+} or_check;
+int or_render_check(or_volume* v, const or_camera* cam, const float* tf, const float* scale, const float* xf, int mode,
+                    int geometry, int64_t n, const int32_t* px, const int32_t* py, const float* rgba, double stop_err,
+                    or_check* out, int threads);
+
 int or_render_grad_xf(or_volume* v, const or_camera* cam, const float* tf, const float* scale, const float* xf,
                       int64_t n, const int32_t* px, const int32_t* py, const double* dl, double* dtf, double* dscale,
                       int threads);
@@ -142,8 +179,17 @@ int or_render_cache(or_volume* v, const or_camera* cam, const float* tf, const f
 int64_t or_node_count(const or_geom* g);
 int64_t or_node_index(const or_geom* g, int L, int64_t i, int64_t j, int64_t k);
 
-/* Gradient of sum_pixels sum_k dl[p][k] * I[p][k] with respect to tf and scale (FP64, natural
- * decisions).  dl: [n][4].  Outputs are overwritten. */
+/* As or_render_grad_xf; also marks in ert_edge[n] (optional) the rays whose opacity after some
+ * sample up to the stopping one lies within ert_margin of the early-termination threshold: there
+ * a single-precision accumulation may stop a sample earlier or later, and the gradient of the ray
+ * changes discontinuously (A16 reading for the adjoint). */
+int or_render_grad_edges(or_volume* v, const or_camera* cam, const float* tf, const float* scale, const float* xf,
+                         int64_t n, const int32_t* px, const int32_t* py, const double* dl, double* dtf,
+                         double* dscale, uint8_t* ert_edge, double ert_margin, int threads);
+
+/* Gradient of sum_pixels sum_k dl[p][k] * I[p][k] with respect to tf and scale (FP64 values,
+ * single-precision decisions as the forward's, the natural stop).  dl: [n][4].  Outputs are
+ * overwritten. */
 int or_render_grad(or_volume* v, const or_camera* cam, const float* tf, const float* scale, int64_t n,
                    const int32_t* px, const int32_t* py, const double* dl, double* dtf, double* dscale, int threads);
 

@@ -15,6 +15,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB = os.path.join(_HERE, "liboracle.so")
 
 MAXL, MAXC, MAXCAND = 16, 4, 4
+MAXFLAG = 3
+GEOMETRY = {"fp32": 0, "fp64": 1}
 
 
 class Camera(ctypes.Structure):
@@ -90,6 +92,17 @@ def lib():
         L.or_render_grad_xf.argtypes = [ctypes.c_void_p, ctypes.POINTER(Camera), ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+        L.or_render_geo.argtypes = [ctypes.c_void_p, ctypes.POINTER(Camera), ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+        L.or_render_check.argtypes = [ctypes.c_void_p, ctypes.POINTER(Camera), ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
+                                      ctypes.c_int]
+        L.or_render_grad_edges.argtypes = [ctypes.c_void_p, ctypes.POINTER(Camera), ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_double, ctypes.c_int]
         L.or_render_cache.argtypes = [ctypes.c_void_p, ctypes.POINTER(Camera), ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -256,9 +269,10 @@ def image_pixels(width, height):
     return px.ravel().copy(), py.ravel().copy()
 
 
-def render(vol: Volume, cam: dict, tf: np.ndarray, scale, pixels=None, mode=0, threads=0, xf=None):
+def render(vol: Volume, cam: dict, tf: np.ndarray, scale, pixels=None, mode=0, threads=0, xf=None, geometry="fp64"):
     """Returns (n_cand [n], cand [n][MAXCAND][4], samples [n]); pixels = (px, py) arrays or None (all).
-    xf: optional per-channel affine sample transforms [C][3][4]."""
+    xf: optional per-channel affine sample transforms [C][3][4].  geometry: "fp64" (the definition,
+    natural branch of every decision) or "fp32" (single-precision decisions in a fixed order)."""
     if pixels is None:
         px, py = image_pixels(cam["width"], cam["height"])
     else:
@@ -270,9 +284,9 @@ def render(vol: Volume, cam: dict, tf: np.ndarray, scale, pixels=None, mode=0, t
     out = (Pixel * max(n, 1))()
     cs = camera_struct(cam)
     xfa = None if xf is None else np.ascontiguousarray(xf, dtype=np.float32).reshape(-1, 3, 4)
-    rc = lib().or_render_xf(vol.handle, ctypes.byref(cs), tf.ctypes.data, sc.ctypes.data,
-                            None if xfa is None else xfa.ctypes.data, mode, n, px.ctypes.data, py.ctypes.data,
-                            ctypes.addressof(out), threads)
+    rc = lib().or_render_geo(vol.handle, ctypes.byref(cs), tf.ctypes.data, sc.ctypes.data,
+                             None if xfa is None else xfa.ctypes.data, mode, GEOMETRY[geometry], n, px.ctypes.data,
+                             py.ctypes.data, ctypes.addressof(out), threads)
     if rc != 0:
         raise ValueError("oracle render: invalid arguments")
     arr = np.ctypeslib.as_array(ctypes.cast(out, ctypes.POINTER(ctypes.c_uint8)),
@@ -284,6 +298,36 @@ def render(vol: Volume, cam: dict, tf: np.ndarray, scale, pixels=None, mode=0, t
     return rec["n_cand"].copy(), rec["rgba"].copy(), rec["samples"].copy()
 
 
+CHECK_DTYPE = np.dtype([("err", np.float64), ("rgba", np.float64, (4,)), ("samples", np.int64), ("flagged", np.int32),
+                        ("variants", np.int32), ("unresolved", np.int32), ("pad", np.int32)])
+
+
+def check(vol: Volume, cam: dict, tf, scale, rgba, pixels=None, mode=0, threads=0, xf=None, geometry="fp64",
+          stop_err=0.0):
+    """Parity check of rendered pixels against every admissible oracle result (knife-edge decision
+    variants x early-termination band; see or_render_check).  rgba: [n][4] (or an image [H][W][4]
+    with pixels=None).  Returns a record array with fields err (smallest max-abs difference), rgba
+    (natural result), samples, flagged, variants, unresolved."""
+    if pixels is None:
+        px, py = image_pixels(cam["width"], cam["height"])
+    else:
+        px = np.ascontiguousarray(pixels[0], dtype=np.int32)
+        py = np.ascontiguousarray(pixels[1], dtype=np.int32)
+    n = px.shape[0]
+    target = np.ascontiguousarray(np.asarray(rgba, dtype=np.float32).reshape(n, 4))
+    tf = np.ascontiguousarray(tf, dtype=np.float32)
+    sc = np.ascontiguousarray(scale, dtype=np.float32)
+    out = np.zeros(max(n, 1), dtype=CHECK_DTYPE)
+    cs = camera_struct(cam)
+    xfa = None if xf is None else np.ascontiguousarray(xf, dtype=np.float32).reshape(-1, 3, 4)
+    rc = lib().or_render_check(vol.handle, ctypes.byref(cs), tf.ctypes.data, sc.ctypes.data,
+                               None if xfa is None else xfa.ctypes.data, mode, GEOMETRY[geometry], n, px.ctypes.data,
+                               py.ctypes.data, target.ctypes.data, float(stop_err), out.ctypes.data, threads)
+    if rc != 0:
+        raise ValueError("oracle render_check: invalid arguments")
+    return out[:n]
+
+
 def render_image(vol, cam, tf, scale, mode=0, threads=0, xf=None):
     """Natural-decision image [H][W][4] (float64) plus the candidate arrays."""
     nc, cand, samples = render(vol, cam, tf, scale, None, mode, threads, xf)
@@ -291,8 +335,10 @@ def render_image(vol, cam, tf, scale, mode=0, threads=0, xf=None):
     return cand[:, 0, :].reshape(H, W, 4), nc.reshape(H, W), cand.reshape(H, W, MAXCAND, 4), samples.reshape(H, W)
 
 
-def render_grad(vol, cam, tf, scale, pixels, dl, threads=0, xf=None):
-    """d(sum dl * I)/d(tf, scale) over the listed pixels; dl [n][4]."""
+def render_grad(vol, cam, tf, scale, pixels, dl, threads=0, xf=None, ert_margin=None):
+    """d(sum dl * I)/d(tf, scale) over the listed pixels; dl [n][4].  With ert_margin, also returns
+    a per-pixel bool array marking the rays whose opacity comes within ert_margin of the
+    early-termination threshold after some sample (up to the stopping one)."""
     px = np.ascontiguousarray(pixels[0], dtype=np.int32)
     py = np.ascontiguousarray(pixels[1], dtype=np.int32)
     n = px.shape[0]
@@ -304,11 +350,16 @@ def render_grad(vol, cam, tf, scale, pixels, dl, threads=0, xf=None):
     dsc = np.zeros(C, dtype=np.float64)
     cs = camera_struct(cam)
     xfa = None if xf is None else np.ascontiguousarray(xf, dtype=np.float32).reshape(-1, 3, 4)
-    rc = lib().or_render_grad_xf(vol.handle, ctypes.byref(cs), tf.ctypes.data, sc.ctypes.data,
-                                 None if xfa is None else xfa.ctypes.data, n, px.ctypes.data, py.ctypes.data,
-                                 dl.ctypes.data, dtf.ctypes.data, dsc.ctypes.data, threads)
+    edge = np.zeros(max(n, 1), np.uint8)
+    rc = lib().or_render_grad_edges(vol.handle, ctypes.byref(cs), tf.ctypes.data, sc.ctypes.data,
+                                    None if xfa is None else xfa.ctypes.data, n, px.ctypes.data, py.ctypes.data,
+                                    dl.ctypes.data, dtf.ctypes.data, dsc.ctypes.data,
+                                    edge.ctypes.data if ert_margin is not None else None,
+                                    float(ert_margin or 0.0), threads)
     if rc != 0:
         raise ValueError("oracle render_grad: invalid arguments")
+    if ert_margin is not None:
+        return dtf, dsc, edge[:n].astype(bool)
     return dtf, dsc
 
 

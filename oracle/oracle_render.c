@@ -25,8 +25,13 @@
  *                  a = 1 - (1 - alpha)^l, C += (1-A) a rgb, A += (1-A) a;
  *   ERT            stop after a sample once A >= ert.
  *
- * Geometry is single precision in the operation order written here (see
- * oracle.h); everything downstream of the sample position is double.
+ * Geometry (ray direction, interval, sample parameter and position, level
+ * and node choice) is evaluated either in double precision (OR_GEOM_FP64, the
+ * definition; decisions that lie within the single-precision error of their
+ * threshold are flagged and both branches enumerated by or_render_check) or
+ * in IEEE single precision in the operation order written here
+ * (OR_GEOM_FP32, a mirror of a single-precision implementation); everything
+ * downstream of the sample position is double.  See oracle.h.
  * This file must be compiled with -ffp-contract=off.
  */
 #include <math.h>
@@ -38,9 +43,10 @@
 #include "oracle_internal.h"
 
 typedef struct {
-    float ff[3], rr[3], uu[3]; /* forward, right, up (unit) */
+    float ff[3], rr[3], uu[3]; /* forward, right, up (unit), rounded to single precision */
     float kx, ky;              /* tan(fov/2) * W/H, tan(fov/2) */
     float tl[OR_MAXL];         /* level thresholds, tl[0] = 0 */
+    double f64[3], r64[3], u64[3], kx64, ky64, tl64[OR_MAXL]; /* the same, unrounded */
 } cam_derived;
 
 static void cam_setup(const or_geom* g, const or_camera* cam, cam_derived* cd) {
@@ -64,12 +70,107 @@ static void cam_setup(const or_geom* g, const or_camera* cam, cam_derived* cd) {
         cd->ff[a] = (float)f[a];
         cd->rr[a] = (float)r[a];
         cd->uu[a] = (float)u[a];
+        cd->f64[a] = f[a];
+        cd->r64[a] = r[a];
+        cd->u64[a] = u[a];
     }
-    cd->kx = (float)((th * (double)cam->width) / (double)cam->height);
+    cd->kx64 = (th * (double)cam->width) / (double)cam->height;
+    cd->ky64 = th;
+    cd->kx = (float)cd->kx64;
     cd->ky = (float)th;
     cd->tl[0] = 0.0f;
-    for (int L = 1; L <= g->N; ++L)
-        cd->tl[L] = (float)(ldexp((double)cam->height, L) / ((2.0 * (double)cam->lod_error_px) * th));
+    cd->tl64[0] = 0.0;
+    for (int L = 1; L <= g->N; ++L) {
+        cd->tl64[L] = ldexp((double)cam->height, L) / ((2.0 * (double)cam->lod_error_px) * th);
+        cd->tl[L] = (float)cd->tl64[L];
+    }
+}
+
+/* ---- double-precision geometry and its knife-edge decisions (A16 reading) ----
+ *
+ * The quantities a single-precision implementation computes from the same camera differ from the
+ * double-precision ones by rounding.  For each ray we bound that difference by forward error
+ * analysis with unit roundoff u = 2^-24: the unit direction within OR_DIR_ULPS u per component
+ * (the sum f + x r + y u, the norm and the division, with headroom for approximate square roots and
+ * divisions), the entry parameter t0 within |t0| (ddir / |d_a| + 4u) for a box face of axis a (and
+ * the corresponding bound for a clip plane), the sample parameter t_k = t0 + k dt within
+ * dt0 + 2u t_k, and the sample position p = eye + t_k d within
+ * dt_k |d_a| + t_k ddir + 2u (|eye_a| + t_k |d_a|) + u |p_a| per axis; OR_EDGE_SAFETY multiplies both.
+ * A decision whose double-precision quantity lies within that bound of its threshold -- the level
+ * choice t_k >= t_L, or the child choice at the parent's split plane -- is a knife edge when its
+ * two branches sample differently (a different level or brick state, or a different AVG); either
+ * branch is then a correct result. */
+static const double U32 = 5.9604644775390625e-08; /* 2^-24 */
+#define OR_DIR_ULPS 32.0
+#define OR_EDGE_SAFETY 2.0
+
+typedef struct {
+    const unsigned char* force; /* forced branches of the first nforce flagged decisions (1 = other) */
+    int nforce;
+    int nflag; /* flagged decisions met (output) */
+} edge_ctl;
+
+static int edge_take_other(edge_ctl* e) {
+    int j = e->nflag++;
+    return j < e->nforce ? (int)e->force[j] : 0;
+}
+
+/* Ray direction and [t0, t1) in double precision; *dt0 bounds the single-precision error of t0. */
+static int ray_setup64(const or_geom* g, const or_camera* cam, const cam_derived* cd, int px, int py, double dir[3],
+                       double* t0o, double* t1o, double* dt0) {
+    double x = ((double)(2 * px + 1) / (double)cam->width - 1.0) * cd->kx64;
+    double y = (1.0 - (double)(2 * py + 1) / (double)cam->height) * cd->ky64;
+    double d[3];
+    for (int i = 0; i < 3; ++i) d[i] = cd->f64[i] + x * cd->r64[i] + y * cd->u64[i];
+    double s = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    for (int i = 0; i < 3; ++i) dir[i] = d[i] / s;
+    const double ddir = OR_DIR_ULPS * U32;
+    double t0 = 0.0, t1 = INFINITY, e0 = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        double o = (double)cam->eye[i], D = (double)g->dim[i];
+        if (dir[i] != 0.0) {
+            double ta = (0.0 - o) / dir[i], tb = (D - o) / dir[i];
+            double lo = fmin(ta, tb), hi = fmax(ta, tb);
+            double e = fabs(lo) * (ddir / fabs(dir[i]) + 4.0 * U32);
+            if (lo > t0) {
+                t0 = lo;
+                e0 = e;
+            } else if (lo == t0 && e > e0) {
+                e0 = e;
+            }
+            t1 = fmin(t1, hi);
+        } else if (o < 0.0 || o > D) {
+            return 0;
+        }
+    }
+    for (int p = 0; p < cam->n_clip; ++p) {
+        const float* n = cam->clip[p];
+        double sv = (double)n[0] * cam->eye[0] + (double)n[1] * cam->eye[1] + (double)n[2] * cam->eye[2] + (double)n[3];
+        double q = (double)n[0] * dir[0] + (double)n[1] * dir[1] + (double)n[2] * dir[2];
+        if (q == 0.0) {
+            if (sv < 0.0) return 0;
+        } else {
+            double tc = -sv / q;
+            double n1 = fabs((double)n[0]) + fabs((double)n[1]) + fabs((double)n[2]);
+            double X = fabs((double)n[0] * cam->eye[0]) + fabs((double)n[1] * cam->eye[1]) +
+                       fabs((double)n[2] * cam->eye[2]) + fabs((double)n[3]);
+            double e = fabs(tc) * (n1 * ddir + 4.0 * U32) / fabs(q) + 4.0 * U32 * X / fabs(q);
+            if (q > 0.0) {
+                if (tc > t0) {
+                    t0 = tc;
+                    e0 = e;
+                } else if (tc == t0 && e > e0) {
+                    e0 = e;
+                }
+            } else {
+                t1 = fmin(t1, tc);
+            }
+        }
+    }
+    *t0o = t0;
+    *t1o = t1;
+    *dt0 = e0;
+    return t0 < t1;
 }
 
 /* Ray direction and [t0, t1); returns 0 for an empty interval. */
@@ -159,6 +260,87 @@ static int descend_path(or_volume* v, const float p[3], int Lstar, or_node* nd, 
 
 static int descend(or_volume* v, const float p[3], int Lstar, or_node* nd) { return descend_path(v, p, Lstar, nd, NULL); }
 
+/* What a sample takes from the node a descent ends at: the level's trilinear value when the node
+ * has a brick (the same value for every node of that level holding p: borders make the level one
+ * continuous field), else the node's AVG. */
+typedef struct {
+    int lev, brick;
+    uint16_t avg[OR_MAXC];
+} outcome_t;
+
+static int outcome_same(const outcome_t* a, const outcome_t* b, int C) {
+    if (a->brick != b->brick) return 0;
+    if (a->brick) return a->lev == b->lev;
+    for (int c = 0; c < C; ++c)
+        if (a->avg[c] != b->avg[c]) return 0;
+    return 1;
+}
+
+/* The descent of getNodeAtPosition in double precision from node (lev, idx) towards Lstar.  With
+ * ctl != NULL, a child choice along axis a whose coordinate lies within dp[a] of the parent's split
+ * plane, with both children in the real node grid and sampling differently, is a knife edge:
+ * ctl decides the branch. */
+static int descend64(or_volume* v, const double p[3], const double dp[3], int Lstar, int lev, const int64_t idx0[3],
+                     edge_ctl* ctl, outcome_t* oc) {
+    const or_geom* g = or_volume_geom(v);
+    int64_t idx[3] = {idx0[0], idx0[1], idx0[2]};
+    or_node nd;
+    or_node_info(v, lev, idx[0], idx[1], idx[2], &nd);
+    while (lev > Lstar && nd.has_children) {
+        --lev;
+        double size = (double)((int64_t)g->M << lev);
+        int64_t q[3];
+        for (int a = 0; a < 3; ++a) {
+            int64_t c0 = 2 * idx[a];
+            q[a] = (p[a] < (double)(c0 + 1) * size) ? c0 : c0 + 1;
+            if (q[a] > g->nb[lev][a] - 1) q[a] = g->nb[lev][a] - 1;
+        }
+        if (ctl) {
+            for (int a = 0; a < 3; ++a) {
+                int64_t c0 = 2 * idx[a];
+                if (c0 + 1 > g->nb[lev][a] - 1) continue; /* one child only along this axis */
+                if (fabs(p[a] - (double)(c0 + 1) * size) > dp[a]) continue;
+                int64_t qo[3] = {q[0], q[1], q[2]};
+                qo[a] = (q[a] == c0) ? c0 + 1 : c0;
+                outcome_t o1, o2;
+                descend64(v, p, dp, Lstar, lev, q, NULL, &o1);
+                descend64(v, p, dp, Lstar, lev, qo, NULL, &o2);
+                if (outcome_same(&o1, &o2, g->C)) continue;
+                if (edge_take_other(ctl)) q[a] = qo[a];
+            }
+        }
+        for (int a = 0; a < 3; ++a) idx[a] = q[a];
+        or_node_info(v, lev, idx[0], idx[1], idx[2], &nd);
+    }
+    oc->lev = lev;
+    oc->brick = nd.has_brick;
+    for (int c = 0; c < g->C; ++c) oc->avg[c] = nd.avg[c];
+    return lev;
+}
+
+/* The level choice L* = max{L <= N : t >= t_L} in double precision; a threshold within dtk of t
+ * whose two levels sample differently is a knife edge (ctl decides). */
+static int lod64(or_volume* v, const cam_derived* cd, double t, double dtk, const double p[3], const double dp[3],
+                 edge_ctl* ctl) {
+    const or_geom* g = or_volume_geom(v);
+    int Lstar = 0;
+    for (int L = 1; L <= g->N; ++L)
+        if (t >= cd->tl64[L]) Lstar = L;
+    if (!ctl) return Lstar;
+    const int64_t root[3] = {0, 0, 0};
+    for (int L = 1; L <= g->N; ++L) {
+        if (fabs(t - cd->tl64[L]) > dtk + 2.0 * U32 * cd->tl64[L]) continue;
+        int alt = (t >= cd->tl64[L]) ? L - 1 : L;
+        if (alt == Lstar) continue;
+        outcome_t o1, o2;
+        descend64(v, p, dp, Lstar, g->N, root, NULL, &o1);
+        descend64(v, p, dp, alt, g->N, root, NULL, &o2);
+        if (outcome_same(&o1, &o2, g->C)) continue;
+        if (edge_take_other(ctl)) Lstar = alt;
+    }
+    return Lstar;
+}
+
 int64_t or_node_count(const or_geom* g) {
     int64_t n = 0;
     for (int L = 0; L <= g->N; ++L) n += g->nb[L][0] * g->nb[L][1] * g->nb[L][2];
@@ -174,12 +356,12 @@ int64_t or_node_index(const or_geom* g, int L, int64_t i, int64_t j, int64_t k) 
 }
 
 /* Trilinear interpolation of level L at p (level-0 units; voxel i centred at (i+0.5) 2^L). */
-static double trilinear(or_volume* v, int L, const float p[3], int c) {
+static double trilinear(or_volume* v, int L, const double p[3], int c) {
     const or_geom* g = or_volume_geom(v);
     int64_t i0[3], i1[3];
     double f[3];
     for (int a = 0; a < 3; ++a) {
-        double u = ldexp((double)p[a], -L) - 0.5;
+        double u = ldexp(p[a], -L) - 0.5;
         double fl = floor(u);
         f[a] = u - fl;
         int64_t i = (int64_t)fl, hi = g->ldim[L][a] - 1;
@@ -196,7 +378,10 @@ static double trilinear(or_volume* v, int L, const float p[3], int c) {
     return s;
 }
 
-double or_sample_trilinear(or_volume* v, int L, const float p[3], int c) { return trilinear(v, L, p, c); }
+double or_sample_trilinear(or_volume* v, int L, const float p[3], int c) {
+    const double q[3] = {p[0], p[1], p[2]};
+    return trilinear(v, L, q, c);
+}
 
 /* Transfer function (Alg. 1 applyTF): x = clamp(s I / 65535, 0, 1) indexes the 256 entries
  * at x * 255; the value is linear between the two neighbouring entries. */
@@ -254,14 +439,44 @@ typedef struct {
     uint8_t* req;       /* per node: its brick was requested (output) */
 } cache_io;
 
+/* Admissible results of one march, for or_render_check: with target != NULL, *best receives the
+ * smallest max-abs RGBA difference between target and a state the ray may correctly end in. */
+typedef struct {
+    const float* target;
+    double best;
+} adm_t;
+
+static void adm_offer(adm_t* ad, const double st[4]) {
+    if (!ad || !ad->target) return;
+    double e = 0.0;
+    for (int q = 0; q < 4; ++q) {
+        double d = fabs(st[q] - (double)ad->target[q]);
+        if (d > e) e = d;
+    }
+    if (e < ad->best) ad->best = e;
+}
+
+/* One ray.  mode 0: emission-absorption with ERT candidates; mode 1: MIP.  geometry: OR_GEOM_FP64
+ * (ctl != NULL decides the knife edges met, see ray_setup64) or OR_GEOM_FP32 (the mirrored
+ * single-precision decisions; required with a brick cache).  rec != NULL records the
+ * natural-decision forward for the adjoint; ad != NULL collects the admissible end states. */
 static void march(or_volume* v, const or_camera* cam, const cam_derived* cd, const float* tf, const float* scale,
-                  const float* xf, int mode, int px, int py, or_pixel* out, recbuf* rec, const cache_io* cio) {
+                  const float* xf, int mode, int geometry, int px, int py, or_pixel* out, recbuf* rec,
+                  const cache_io* cio, edge_ctl* ctl, adm_t* ad) {
     const or_geom* g = or_volume_geom(v);
     int C = g->C;
+    const int fp64 = geometry == OR_GEOM_FP64;
     memset(out, 0, sizeof(*out));
     out->n_cand = 1;
-    float dir[3], t0, t1;
-    if (!ray_setup(g, cam, cd, px, py, dir, &t0, &t1)) return;
+    float dirf[3], t0f = 0.0f, t1f = 0.0f;
+    double dir[3], t0 = 0.0, t1 = 0.0, dt0 = 0.0;
+    int hit = fp64 ? ray_setup64(g, cam, cd, px, py, dir, &t0, &t1, &dt0)
+                   : ray_setup(g, cam, cd, px, py, dirf, &t0f, &t1f);
+    if (!hit) {
+        const double zero[4] = {0, 0, 0, 0};
+        adm_offer(ad, zero);
+        return;
+    }
     const float dt = cam->step_voxels;
     const double ert = (double)cam->ert_alpha;
     double Cacc[3] = {0, 0, 0}, A = 0.0;
@@ -272,23 +487,47 @@ static void march(or_volume* v, const or_camera* cam, const cam_derived* cd, con
     int have_prev = 0, have_late = 0;
     int64_t nsamp = 0;
     for (int64_t k = 0;; ++k) {
-        float tk = t0 + (float)k * dt;
-        if (!(tk < t1) || k >= ((int64_t)1 << 24)) break; /* at most 2^24 samples per ray */
-        float ell = fminf(dt, t1 - tk);
-        float p[3];
-        for (int a = 0; a < 3; ++a) p[a] = cam->eye[a] + tk * dir[a];
-        int Lstar = 0;
-        for (int L = 1; L <= g->N; ++L)
-            if (tk >= cd->tl[L]) Lstar = L;
+        double p[3], dp[3] = {0, 0, 0};
+        float pf[3];
+        double ell;
+        int Lstar = 0, lev;
         or_node nd;
         int64_t path[OR_MAXL][3];
-        int lev = descend_path(v, p, Lstar, &nd, path);
+        outcome_t oc;
+        if (fp64) {
+            double tk = t0 + (double)k * (double)dt;
+            if (!(tk < t1) || k >= ((int64_t)1 << 24)) break; /* at most 2^24 samples per ray */
+            ell = fmin((double)dt, t1 - tk);
+            double dtk = OR_EDGE_SAFETY * (dt0 + 2.0 * U32 * tk);
+            for (int a = 0; a < 3; ++a) {
+                p[a] = (double)cam->eye[a] + tk * dir[a];
+                dp[a] = OR_EDGE_SAFETY * (dtk * fabs(dir[a]) + tk * OR_DIR_ULPS * U32 +
+                                          2.0 * U32 * (fabs((double)cam->eye[a]) + tk * fabs(dir[a])) +
+                                          U32 * fabs(p[a]));
+            }
+            Lstar = lod64(v, cd, tk, dtk, p, dp, ctl);
+            const int64_t root[3] = {0, 0, 0};
+            lev = descend64(v, p, dp, Lstar, g->N, root, ctl, &oc);
+            nd.has_brick = oc.brick;
+            for (int c = 0; c < C; ++c) nd.avg[c] = oc.avg[c];
+        } else {
+            float tk = t0f + (float)k * dt;
+            if (!(tk < t1f) || k >= ((int64_t)1 << 24)) break;
+            ell = (double)fminf(dt, t1f - tk);
+            for (int a = 0; a < 3; ++a) {
+                pf[a] = cam->eye[a] + tk * dirf[a];
+                p[a] = (double)pf[a];
+            }
+            for (int L = 1; L <= g->N; ++L)
+                if (tk >= cd->tl[L]) Lstar = L;
+            lev = descend_path(v, pf, Lstar, &nd, path);
+        }
         /* Full-frame ray casting with a partial brick cache (Sec. "Full-Frame Ray-Casting"): a
          * missing brick is requested; the brick of the parent or grandparent on the descent path,
          * if present, stands in (nearest first), else the node's AVG; those missing are requested
          * as well. */
         int samp_lev = nd.has_brick ? lev : -1;
-        if (cio && cio->res && nd.has_brick) {
+        if (!fp64 && cio && cio->res && nd.has_brick) {
             const or_geom* gg = or_volume_geom(v);
             int64_t nid = or_node_index(gg, lev, path[lev][0], path[lev][1], path[lev][2]);
             if (cio->res[nid]) {
@@ -315,11 +554,31 @@ static void march(or_volume* v, const or_camera* cam, const cam_derived* cd, con
         }
         or_node ndc[OR_MAXC];
         int levc[OR_MAXC];
-        float pc[OR_MAXC][3];
+        double pc[OR_MAXC][3];
         if (xf) /* every channel descends from its own transformed point */
             for (int c = 0; c < C; ++c) {
-                channel_point(xf + 12 * c, p, pc[c]);
-                levc[c] = descend(v, pc[c], Lstar, &ndc[c]);
+                const float* m = xf + 12 * c;
+                if (fp64) {
+                    double dq[3];
+                    for (int i = 0; i < 3; ++i) {
+                        pc[c][i] = m[4 * i] * p[0] + m[4 * i + 1] * p[1] + m[4 * i + 2] * p[2] + (double)m[4 * i + 3];
+                        dq[i] = fabs((double)m[4 * i]) * dp[0] + fabs((double)m[4 * i + 1]) * dp[1] +
+                                fabs((double)m[4 * i + 2]) * dp[2] +
+                                OR_EDGE_SAFETY * 4.0 * U32 *
+                                    (fabs(m[4 * i] * p[0]) + fabs(m[4 * i + 1] * p[1]) + fabs(m[4 * i + 2] * p[2]) +
+                                     fabs((double)m[4 * i + 3]));
+                    }
+                    const int64_t root[3] = {0, 0, 0};
+                    outcome_t occ;
+                    levc[c] = descend64(v, pc[c], dq, Lstar, g->N, root, ctl, &occ);
+                    ndc[c].has_brick = occ.brick;
+                    for (int cc = 0; cc < C; ++cc) ndc[c].avg[cc] = occ.avg[cc];
+                } else {
+                    float qf[3];
+                    channel_point(m, pf, qf);
+                    for (int i = 0; i < 3; ++i) pc[c][i] = (double)qf[i];
+                    levc[c] = descend(v, qf, Lstar, &ndc[c]);
+                }
             }
         if (!have_nat || mode == 1) ++nsamp;
         for (int c = 0; c < C; ++c) {
@@ -345,9 +604,9 @@ static void march(or_volume* v, const or_camera* cam, const cam_derived* cd, con
                 alpha = 0.0;
                 acl = 1;
             }
-            double aa = 1.0 - pow(1.0 - alpha, (double)ell);
+            double aa = 1.0 - pow(1.0 - alpha, ell);
             if (rec && !have_nat) {
-                rec_t r = {I, lam, alpha, aa, (double)ell, A, i, (xr > 0.0 && xr < 1.0), acl, c};
+                rec_t r = {I, lam, alpha, aa, ell, A, i, (xr > 0.0 && xr < 1.0), acl, c};
                 rec_push(rec, &r);
             }
             for (int q = 0; q < 3; ++q) Cacc[q] += (1.0 - A) * aa * rgba[q];
@@ -355,6 +614,7 @@ static void march(or_volume* v, const or_camera* cam, const cam_derived* cd, con
         }
         if (mode == 1) continue;
         double st[4] = {Cacc[0], Cacc[1], Cacc[2], A};
+        if (A >= ert - OR_ERT_BAND) adm_offer(ad, st); /* every state in the band is a correct stop */
         if (!have_early && A >= ert - OR_ERT_BAND) {
             have_early = 1;
             memcpy(st_early, st, sizeof st);
@@ -376,7 +636,11 @@ static void march(or_volume* v, const or_camera* cam, const cam_derived* cd, con
     }
     if (mode == 1) {
         out->samples = nsamp;
-        if (nsamp == 0) return;
+        if (nsamp == 0) {
+            const double zero[4] = {0, 0, 0, 0};
+            adm_offer(ad, zero);
+            return;
+        }
         double Cm[3] = {0, 0, 0}, Am = 0.0;
         for (int c = 0; c < C; ++c) {
             double rgba[4];
@@ -389,9 +653,11 @@ static void march(or_volume* v, const or_camera* cam, const cam_derived* cd, con
         out->rgba[0][1] = Cm[1];
         out->rgba[0][2] = Cm[2];
         out->rgba[0][3] = Am;
+        adm_offer(ad, out->rgba[0]);
         return;
     }
     double fin[4] = {Cacc[0], Cacc[1], Cacc[2], A};
+    if (!have_late) adm_offer(ad, fin); /* the ray ran to its end */
     if (!have_nat) {
         out->samples = nsamp;
         memcpy(out->rgba[0], fin, sizeof fin);
@@ -420,16 +686,20 @@ typedef struct {
     const float* scale;
     const float* xf; /* NULL or [C][3][4] per-channel transforms */
     cache_io cio;
-    int mode;
+    int mode, geometry;
     const int32_t* px;
     const int32_t* py;
     or_pixel* out;
+    const float* target; /* or_render_check: the pixels to compare [n][4] */
+    or_check* chk;
+    double stop_err; /* or_render_check: stop enumerating once a variant is this close */
 } render_job;
 
 static void render_range(void* p, int64_t b, int64_t e) {
     render_job* j = (render_job*)p;
     for (int64_t i = b; i < e; ++i)
-        march(j->v, j->cam, &j->cd, j->tf, j->scale, j->xf, j->mode, j->px[i], j->py[i], &j->out[i], NULL, &j->cio);
+        march(j->v, j->cam, &j->cd, j->tf, j->scale, j->xf, j->mode, j->geometry, j->px[i], j->py[i], &j->out[i],
+              NULL, &j->cio, NULL, NULL);
 }
 
 static int cam_valid(const or_camera* cam) {
@@ -439,30 +709,92 @@ static int cam_valid(const or_camera* cam) {
     return 1;
 }
 
-int or_render_xf(or_volume* v, const or_camera* cam, const float* tf, const float* scale, const float* xf, int mode,
-                 int64_t n, const int32_t* px, const int32_t* py, or_pixel* out, int threads) {
-    if (!v || !cam_valid(cam) || !tf || !scale || !px || !py || !out || (mode != 0 && mode != 1)) return -1;
+static void job_init(render_job* j, or_volume* v, const or_camera* cam, const float* tf, const float* scale,
+                     const float* xf, int mode, int geometry, const int32_t* px, const int32_t* py) {
+    memset(j, 0, sizeof *j);
+    j->v = v;
+    j->cam = cam;
+    cam_setup(or_volume_geom(v), cam, &j->cd);
+    j->tf = tf;
+    j->scale = scale;
+    j->xf = xf;
+    j->mode = mode;
+    j->geometry = geometry;
+    j->px = px;
+    j->py = py;
+}
+
+int or_render_geo(or_volume* v, const or_camera* cam, const float* tf, const float* scale, const float* xf, int mode,
+                  int geometry, int64_t n, const int32_t* px, const int32_t* py, or_pixel* out, int threads) {
+    if (!v || !cam_valid(cam) || !tf || !scale || !px || !py || !out || (mode != 0 && mode != 1) ||
+        (geometry != OR_GEOM_FP32 && geometry != OR_GEOM_FP64))
+        return -1;
     render_job j;
-    j.v = v;
-    j.cam = cam;
-    cam_setup(or_volume_geom(v), cam, &j.cd);
-    j.tf = tf;
-    j.scale = scale;
-    j.xf = xf;
-    j.cio.res = NULL;
-    j.cio.used = NULL;
-    j.cio.req = NULL;
-    j.mode = mode;
-    j.px = px;
-    j.py = py;
+    job_init(&j, v, cam, tf, scale, xf, mode, geometry, px, py);
     j.out = out;
     or_parallel_for(n, 16, threads, render_range, &j);
     return 0;
 }
 
+int or_render_xf(or_volume* v, const or_camera* cam, const float* tf, const float* scale, const float* xf, int mode,
+                 int64_t n, const int32_t* px, const int32_t* py, or_pixel* out, int threads) {
+    return or_render_geo(v, cam, tf, scale, xf, mode, OR_GEOM_FP64, n, px, py, out, threads);
+}
+
 int or_render(or_volume* v, const or_camera* cam, const float* tf, const float* scale, int mode, int64_t n,
               const int32_t* px, const int32_t* py, or_pixel* out, int threads) {
     return or_render_xf(v, cam, tf, scale, NULL, mode, n, px, py, out, threads);
+}
+
+/* Every variant of the ray's knife-edge decisions, depth first: the march with the branches in
+ * script[0..len) forced and the natural branch beyond, then, for each later flagged decision j
+ * (up to OR_MAXFLAG), the march that takes the other branch there and the natural one between. */
+static void explore(render_job* j, int64_t i, const unsigned char* script, int len, or_check* out) {
+    edge_ctl e = {script, len, 0};
+    adm_t ad = {j->target + 4 * i, INFINITY};
+    or_pixel pix;
+    march(j->v, j->cam, &j->cd, j->tf, j->scale, j->xf, j->mode, j->geometry, j->px[i], j->py[i], &pix, NULL, NULL,
+          j->geometry == OR_GEOM_FP64 ? &e : NULL, &ad);
+    out->variants++;
+    if (ad.best < out->err) out->err = ad.best;
+    if (len == 0) {
+        memcpy(out->rgba, pix.rgba[0], sizeof out->rgba);
+        out->samples = pix.samples;
+        out->flagged = e.nflag;
+    }
+    if (e.nflag > OR_MAXFLAG) out->unresolved = 1;
+    int lim = e.nflag < OR_MAXFLAG ? e.nflag : OR_MAXFLAG;
+    for (int k = len; k < lim && out->err > j->stop_err; ++k) {
+        unsigned char s2[OR_MAXFLAG] = {0};
+        if (len > 0) memcpy(s2, script, (size_t)len);
+        s2[k] = 1;
+        explore(j, i, s2, k + 1, out);
+    }
+}
+
+static void check_range(void* p, int64_t b, int64_t e) {
+    render_job* j = (render_job*)p;
+    for (int64_t i = b; i < e; ++i) {
+        or_check* o = &j->chk[i];
+        memset(o, 0, sizeof *o);
+        o->err = INFINITY;
+        explore(j, i, NULL, 0, o);
+    }
+}
+
+int or_render_check(or_volume* v, const or_camera* cam, const float* tf, const float* scale, const float* xf, int mode,
+                    int geometry, int64_t n, const int32_t* px, const int32_t* py, const float* rgba, double stop_err,
+                    or_check* out, int threads) {
+    if (!v || !cam_valid(cam) || !tf || !scale || !px || !py || !rgba || !out || (mode != 0 && mode != 1) ||
+        (geometry != OR_GEOM_FP32 && geometry != OR_GEOM_FP64))
+        return -1;
+    render_job j;
+    job_init(&j, v, cam, tf, scale, xf, mode, geometry, px, py);
+    j.target = rgba;
+    j.chk = out;
+    j.stop_err = stop_err;
+    or_parallel_for(n, 16, threads, check_range, &j);
+    return 0;
 }
 
 int or_render_cache(or_volume* v, const or_camera* cam, const float* tf, const float* scale, int mode, int64_t n,
@@ -472,18 +804,11 @@ int or_render_cache(or_volume* v, const or_camera* cam, const float* tf, const f
         (mode != 0 && mode != 1))
         return -1;
     render_job j;
-    j.v = v;
-    j.cam = cam;
-    cam_setup(or_volume_geom(v), cam, &j.cd);
-    j.tf = tf;
-    j.scale = scale;
-    j.xf = NULL;
+    /* single-precision (mirrored) geometry: the used/requested flags are compared bit for bit */
+    job_init(&j, v, cam, tf, scale, NULL, mode, OR_GEOM_FP32, px, py);
     j.cio.res = resident;
     j.cio.used = used;
     j.cio.req = requested;
-    j.mode = mode;
-    j.px = px;
-    j.py = py;
     j.out = out;
     or_parallel_for(n, 16, threads, render_range, &j);
     return 0;
@@ -497,7 +822,23 @@ typedef struct {
     double* dscale; /* [threads][C] */
     int64_t next, n;
     int nthreads;
+    uint8_t* ert_edge; /* optional [n]: some sample state lies within ert_margin of the threshold */
+    double ert_margin;
 } grad_job;
+
+/* Whether the opacity after some sample of the recorded (natural) march -- up to and including
+ * the stopping sample -- lies within margin of the termination threshold: there a single-precision
+ * accumulation may stop one sample earlier or later (A16 reading). */
+static int ert_knife_edge(const recbuf* rb, double ert, double margin) {
+    for (int64_t n = 1; n < rb->n; ++n)
+        if (rb->r[n].c == 0 && fabs(rb->r[n].A_before - ert) < margin) return 1;
+    if (rb->n > 0) {
+        const rec_t* r = &rb->r[rb->n - 1];
+        double A = r->A_before + (1.0 - r->A_before) * r->a;
+        if (fabs(A - ert) < margin) return 1;
+    }
+    return 0;
+}
 
 typedef struct {
     grad_job* g;
@@ -548,17 +889,18 @@ static void* grad_worker(void* p) {
         if (i >= j->n) break;
         rb.n = 0;
         or_pixel px;
-        march(j->rj.v, j->rj.cam, &j->rj.cd, j->rj.tf, j->rj.scale, j->rj.xf, 0, j->rj.px[i], j->rj.py[i], &px, &rb,
-              NULL);
+        march(j->rj.v, j->rj.cam, &j->rj.cd, j->rj.tf, j->rj.scale, j->rj.xf, 0, OR_GEOM_FP32, j->rj.px[i],
+              j->rj.py[i], &px, &rb, NULL, NULL, NULL);
         ray_grad(g, j->rj.tf, &rb, j->dl + 4 * i, dtf, dsc);
+        if (j->ert_edge) j->ert_edge[i] = (uint8_t)ert_knife_edge(&rb, (double)j->rj.cam->ert_alpha, j->ert_margin);
     }
     free(rb.r);
     return NULL;
 }
 
-int or_render_grad_xf(or_volume* v, const or_camera* cam, const float* tf, const float* scale, const float* xf,
-                      int64_t n, const int32_t* px, const int32_t* py, const double* dl, double* dtf, double* dscale,
-                      int threads) {
+int or_render_grad_edges(or_volume* v, const or_camera* cam, const float* tf, const float* scale, const float* xf,
+                         int64_t n, const int32_t* px, const int32_t* py, const double* dl, double* dtf,
+                         double* dscale, uint8_t* ert_edge, double ert_margin, int threads) {
     if (!v || !cam_valid(cam) || !tf || !scale || !px || !py || !dl || !dtf || !dscale) return -1;
     const or_geom* g = or_volume_geom(v);
     int C = g->C;
@@ -576,6 +918,8 @@ int or_render_grad_xf(or_volume* v, const or_camera* cam, const float* tf, const
     j.n = n;
     j.dl = dl;
     j.nthreads = threads;
+    j.ert_edge = ert_edge;
+    j.ert_margin = ert_margin;
     j.dtf = (double*)calloc((size_t)threads * (size_t)C * 1024, sizeof(double));
     j.dscale = (double*)calloc((size_t)threads * (size_t)C, sizeof(double));
     pthread_t th[256];
@@ -595,6 +939,12 @@ int or_render_grad_xf(or_volume* v, const or_camera* cam, const float* tf, const
     free(j.dtf);
     free(j.dscale);
     return 0;
+}
+
+int or_render_grad_xf(or_volume* v, const or_camera* cam, const float* tf, const float* scale, const float* xf,
+                      int64_t n, const int32_t* px, const int32_t* py, const double* dl, double* dtf, double* dscale,
+                      int threads) {
+    return or_render_grad_edges(v, cam, tf, scale, xf, n, px, py, dl, dtf, dscale, NULL, 0.0, threads);
 }
 
 int or_render_grad(or_volume* v, const or_camera* cam, const float* tf, const float* scale, int64_t n,

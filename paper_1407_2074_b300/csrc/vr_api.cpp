@@ -1271,11 +1271,16 @@ vr_status vr_plan_destroy(vr_render_plan* p) {
 namespace vrk {
 
 vr_status prepare_render_noalloc(vr_ctx* c, const vr_camera* cams, int n, float* const* images, int mode,
-                                 CamParam* params, RenderArgs* args, int* blocks) {
+                                 CamParam* params, RenderArgs* args, int* blocks, int* threads, int* fp16) {
     vr_status s = check_ctx(c);
     if (s != VR_OK) return s;
-    if (!cams || n <= 0 || !images || !params || !args || !blocks) return fail(c, VR_ERR_INVALID_ARG, "no cameras or images");
+    if (!cams || n <= 0 || !images || !params || !args || !blocks || !threads || !fp16)
+        return fail(c, VR_ERR_INVALID_ARG, "no cameras or images");
+    // the same mode word as vr_render: DVR or MIP, optionally | VR_RENDER_FP16 (DVR only)
+    const int want_fp16 = (mode & VR_RENDER_FP16) || c->opt.precision == VR_FP16_INTERP;
+    mode &= ~VR_RENDER_FP16;
     if (mode != VR_MODE_DVR && mode != VR_MODE_MIP) return fail(c, VR_ERR_INVALID_ARG, "unknown mode");
+    *fp16 = want_fp16 && mode == VR_MODE_DVR;
     if (!c->tf_set) return fail(c, VR_ERR_INVALID_ARG, "transfer functions not set");
     long long tiles = 0;
     for (int i = 0; i < n; ++i) {
@@ -1290,12 +1295,12 @@ vr_status prepare_render_noalloc(vr_ctx* c, const vr_camera* cams, int n, float*
     }
     if (tiles >= 0xffffffffLL) return fail(c, VR_ERR_INVALID_ARG, "too many pixels in one call");
     *args = make_args(c, n, tiles);
-    *blocks = grid_for(c, tiles, 256, 8);
+    // the context's launch shape (vr_set_launch_shape), as vr_render uses it
+    *threads = c->threads;
+    *blocks = grid_for(c, tiles, c->threads, c->ctas_per_sm);
     return VR_OK;
 }
 
 vr_status noalloc_fail(vr_ctx* c, vr_status s, const char* msg) { return fail(c, s, msg); }
-
-int noalloc_fp16(const vr_ctx* c) { return c->opt.precision == VR_FP16_INTERP; }
 
 } // namespace vrk

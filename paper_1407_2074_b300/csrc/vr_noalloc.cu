@@ -18,9 +18,8 @@
 
 namespace vrk {
 vr_status prepare_render_noalloc(vr_ctx* c, const vr_camera* cams, int n, float* const* images, int mode,
-                                 CamParam* params, RenderArgs* args, int* blocks);
+                                 CamParam* params, RenderArgs* args, int* blocks, int* threads, int* fp16);
 vr_status noalloc_fail(vr_ctx* c, vr_status s, const char* msg);
-int noalloc_fp16(const vr_ctx* c);
 } // namespace vrk
 
 using namespace vrk;
@@ -47,8 +46,9 @@ extern "C" vr_status vr_render_noalloc(vr_ctx* ctx, const vr_camera* cams, int n
         return noalloc_fail(ctx, VR_ERR_INVALID_ARG, "vr_render_noalloc: more than VR_NOALLOC_MAX_CAMERAS (64) cameras");
     CamParam params[VR_NOALLOC_MAX_CAMERAS]; // host stack, no heap
     RenderArgs a;
-    int blocks = 0;
-    vr_status s = prepare_render_noalloc(ctx, cams, n_cams, images, mode, params, &a, &blocks); // makes ctx's device current
+    int blocks = 0, threads = 0, fp16 = 0;
+    // validates like vr_render and makes ctx's device current
+    vr_status s = prepare_render_noalloc(ctx, cams, n_cams, images, mode, params, &a, &blocks, &threads, &fp16);
     if (s != VR_OK) return s;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
@@ -79,7 +79,7 @@ extern "C" vr_status vr_render_noalloc(vr_ctx* ctx, const vr_camera* cams, int n
     a.cams = sc->cams;
     a.counter = sc->counter;
     a.stats = sc->stats;
-    e = launch_render(a, mode, noalloc_fp16(ctx), blocks, 256, st);
+    e = launch_render(a, mode & ~VR_RENDER_FP16, fp16, blocks, threads, st);
     if (e != cudaSuccess) return noalloc_fail(ctx, VR_ERR_CUDA, cudaGetErrorString(e));
     return VR_OK;
 }

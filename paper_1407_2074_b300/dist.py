@@ -27,5 +27,9 @@ def aggregate(elapsed_ms: float, work: float, device=None):
 
 
 def frames_for_rank(rank: int, steps: int, n_frames: int):
-    """Orbit frames of one rank: ranks take disjoint, consecutive blocks of the orbit."""
+    """Orbit frames of one rank: rank r renders frames r*steps, r*steps + 1, ... of the orbit, wrapping
+    around it.  The ranks' frames are disjoint while ranks x steps <= n_frames; beyond that the
+    orbit repeats and ranks render some of the same views.  Each rank holds its own replica of the
+    volume on its own GPU, so a repeated view is still a full render there (nothing is shared or
+    cached across ranks); only the mix of view angles in the timed region changes."""
     return [(rank * steps + i) % n_frames for i in range(steps)]

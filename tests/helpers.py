@@ -4,9 +4,27 @@ import numpy as np
 from oracle import oracle as O
 
 RGBA_TOL = 2e-3  # max-abs RGBA, every pixel, against some admissible oracle result
+UNRESOLVED_FRAC = 1e-4  # rays with more knife-edge decisions than the oracle enumerates, at most
 
 
-admissible_error = O.admissible_error  # per-pixel error to the nearest admissible oracle state
+admissible_error = O.admissible_error  # per-pixel error to the nearest candidate of an oracle render
+
+
+def parity(vol, cam, tf, scale, rgba, pixels=None, mode=0, xf=None, tol=RGBA_TOL):
+    """Every GPU pixel against the oracle's admissible results (double-precision geometry, every
+    combination of branches of the ray's knife-edge decisions, any stop in the early-termination
+    band).  Gate: every pixel within tol, except unresolved rays (more knife-edge decisions than
+    enumerated), which may number at most UNRESOLVED_FRAC of the pixels.  Returns the oracle's
+    per-pixel record (err, natural rgba, samples, flagged, variants, unresolved)."""
+    n = len(pixels[0]) if pixels is not None else cam["width"] * cam["height"]
+    r = O.check(vol, cam, tf, scale, np.asarray(rgba, dtype=np.float32).reshape(n, 4), pixels, mode, xf=xf,
+                stop_err=tol)
+    unres = r["unresolved"] != 0
+    bad = (r["err"] > tol) & ~unres
+    worst = int(np.argmax(np.where(unres, 0.0, r["err"]))) if n else 0
+    assert not bad.any(), f"{bad.sum()} pixels over {tol:g}; max err {r['err'][worst]:.3e} at index {worst}"
+    assert unres.sum() <= UNRESOLVED_FRAC * n, f"{unres.sum()} unresolved rays of {n}"
+    return r
 
 
 def oracle_dense(volume: np.ndarray, brick, bg=0, tau=0, z_hi=None):

@@ -47,3 +47,15 @@ def test_single_process_aggregation_is_identity():
 
     assert D.aggregate(3.5, 7.0) == (3.5, 7.0)
     assert D.env()[0] >= 1
+
+
+def test_frames_disjoint_until_the_orbit_wraps():
+    from paper_1407_2074_b300 import dist as D
+
+    for ranks, steps in ((2, 30), (4, 15), (8, 7)):  # ranks x steps <= 60: disjoint
+        sets = [set(D.frames_for_rank(r, steps, 60)) for r in range(ranks)]
+        assert sum(len(s) for s in sets) == len(set().union(*sets)) == ranks * steps
+    # 8 ranks x 23 steps (3 warm-up + 20 timed) > 60: the orbit wraps and views repeat
+    frames = [D.frames_for_rank(r, 23, 60) for r in range(8)]
+    assert all(len(f) == 23 and all(0 <= x < 60 for x in f) for f in frames)
+    assert len(set().union(*map(set, frames))) == 60

@@ -6,7 +6,7 @@ import pytest
 
 from oracle import oracle as O
 from synth import synth as S
-from tests.helpers import RGBA_TOL, admissible_error, oracle_dense
+from tests.helpers import RGBA_TOL, admissible_error, oracle_dense, parity
 
 pytestmark = pytest.mark.gpu
 
@@ -100,8 +100,7 @@ def test_full_frame_converges_to_the_full_quality_render(tiny):
         if rep["requested"] == 0:
             break
     assert rep["requested"] == 0
-    nc, cand, _ = O.render(ov, cam, tf, sc, None, 0)
-    assert admissible_error(img.reshape(-1, 4), nc, cand).max() <= RGBA_TOL
+    parity(ov, cam, tf, sc, img.reshape(-1, 4))
 
 
 @pytest.mark.parametrize("store_on_host", [False, True])
@@ -128,9 +127,8 @@ def test_refinement_with_a_small_cache(tiny, store_on_host):
     torch.cuda.synchronize()
     img = ses.image.cpu().numpy()
     ses.close()
-    nc, cand, osamples = O.render(ov, cam, tf, sc, None, 0)
     assert passes > 2
-    assert admissible_error(img.reshape(-1, 4), nc, cand).max() <= RGBA_TOL
+    osamples = parity(ov, cam, tf, sc, img.reshape(-1, 4))["samples"]
     assert abs(total - int(osamples.sum())) <= 0.001 * osamples.sum()
 
 
@@ -188,6 +186,40 @@ def test_medium_spim_out_of_core():
     import torch
 
     torch.cuda.synchronize()
-    nc, cand, _ = O.render(ov, cam, tf, sc, None, 0)
-    assert admissible_error(ses.image.cpu().numpy().reshape(-1, 4), nc, cand).max() <= RGBA_TOL
+    parity(ov, cam, tf, sc, ses.image.cpu().numpy().reshape(-1, 4))
     ses.close()
+
+
+def test_cost_ordered_queue_changes_no_pixel_of_a_cache_pass(tiny):
+    """The render-cache pass takes its tiles from the cost-ordered queue as well: three renders in
+    that order give the raster-order images, sample and ray counts and used/requested flags bit for
+    bit, and a render of another tile grid in between does not disturb the order of this one."""
+    w, vol, cam = tiny
+    r = _build(vol, 16, cache_slots=30)
+    tf, sc = w.tf(), [1.0, 1.0, 1.0]
+    _set_tf(r, tf, sc)
+    r.cache_update(max_uploads=12)
+    cams = [cam, dict(cam, width=57, height=33)]  # a ragged second view
+    r.set_tile_order(0)
+    import torch
+
+    def run(cs):
+        imgs = r.render(cs)
+        torch.cuda.synchronize()
+        st = r.stats()
+        _, used, req = r.cache_read()
+        return [im.cpu().numpy() for im in imgs], (st.last_render_samples, st.last_render_rays), used, req
+
+    ref, counts, used0, req0 = run(cams)
+    other = dict(cam, width=40, height=24)
+    r.set_tile_order(1)
+    for i in range(3):
+        imgs, cnt, used, req = run(cams)
+        for a, b in zip(imgs, ref):
+            assert np.array_equal(a, b), i
+        assert cnt == counts, i
+        if i < 2:  # the flags accumulate until the next cache update: compare before `other` adds its own
+            assert np.array_equal(used, used0) and np.array_equal(req, req0), i
+        if i == 1:
+            run([other])  # another grid between two passes of the same grid
+    r.close()

@@ -7,7 +7,7 @@ import pytest
 
 from oracle import oracle as O
 from synth import synth as S
-from tests.helpers import RGBA_TOL, admissible_error, oracle_dense
+from tests.helpers import oracle_dense, parity
 
 pytestmark = pytest.mark.gpu
 
@@ -58,8 +58,8 @@ def test_mip_segments_equal_whole_rays_and_match_the_oracle(spim, kseg):
         (seg,), c1, _ = _render(r, [cam], V.VR_MODE_MIP)
         assert c1 == c0
         assert np.array_equal(seg, whole)
-    nc, cand, samples = O.render(ov, cam, tf, [1.0, 1.2, 0.8], None, V.VR_MODE_MIP)
-    assert admissible_error(seg.reshape(-1, 4), nc, cand).max() <= RGBA_TOL
+    parity(ov, cam, tf, [1.0, 1.2, 0.8], seg.reshape(-1, 4), None, V.VR_MODE_MIP)
+    _, _, samples = O.render(ov, cam, tf, [1.0, 1.2, 0.8], None, V.VR_MODE_MIP, geometry="fp32")
     assert c1[0] == int(samples.sum())
     r.close()
 

@@ -318,7 +318,8 @@ def test_full_frame_cache_semantics():
     # (2) only the root present: a level-0 sample falls back to its grandparent (the root, N = 2),
     # i.e. the image of a camera whose level choice is the root everywhere; every missing brick on
     # the paths is requested; (3) nothing present: a constant volume still renders its closed form
-    # through the AVG values.
+    # through the AVG values.  The cache render takes single-precision (mirrored) decisions, so the
+    # plain renders it is compared with do too.
     w = S.tiny()
     vol = w.spec().volume()
     v = dense(vol)
@@ -330,14 +331,14 @@ def test_full_frame_cache_semantics():
     root = O.node_index(v, v.N, 0, 0, 0)
     allres = np.ones(nn, np.uint8)
     nc, cand, _, used, req = O.render_cache(v, cam, tf, sc, allres)
-    ref = O.render(v, cam, tf, sc, None, 0)[1]
+    ref = O.render(v, cam, tf, sc, None, 0, geometry="fp32")[1]
     assert np.array_equal(cand, ref) and req.sum() == 0 and used.sum() > 0 and used[root] == 0
     onlyroot = np.zeros(nn, np.uint8)
     onlyroot[root] = 1
     _, cand2, _, used2, req2 = O.render_cache(v, cam, tf, sc, onlyroot)
     far = dict(cam)
     far["lod_error_px"] = 1e6  # level N everywhere
-    ref2 = O.render(v, far, tf, sc, None, 0)[1]
+    ref2 = O.render(v, far, tf, sc, None, 0, geometry="fp32")[1]
     assert np.abs(cand2[:, 0] - ref2[:, 0]).max() < 1e-12
     assert used2[root] == 1 and used2.sum() == 1
     lvl1 = [O.node_index(v, 1, i, j, k) for i in range(2) for j in range(2) for k in range(2)]
@@ -347,3 +348,93 @@ def test_full_frame_cache_semantics():
     c1 = cam1()
     _, cc, _, _, rq = O.render_cache(const, c1, tf1, [1.0], np.zeros(O.node_count(const), np.uint8), ([0], [0]))
     assert abs(cc[0, 0, 3] - (1.0 - math.exp(-SIG * 64.0))) < 1e-6 and rq.sum() > 0
+
+
+# ---- double-precision geometry and its knife-edge decisions (A16 reading) ----
+
+def test_fp64_geometry_equals_fp32_geometry_away_from_knife_edges():
+    """The two geometry modes compute the same rays up to rounding: wherever the double-precision
+    march met no knife-edge decision, its result equals the single-precision one to within what a
+    sample-position difference of ~1e-4 voxel can change; and knife edges are rare."""
+    w = S.tiny()
+    v = dense(w.spec().volume(), M=16)
+    for cam in (S.orbit_camera(w.dims, 128.0, 40.0, 25.0, 96, 80, lod_error_px=3.0),
+                S.orbit_camera(w.dims, 100.0, 200.0, -30.0, 96, 80, lod_error_px=0.3,
+                               clip=[S.centre_plane(w.dims, (1.0, 0.5, 0.25))])):
+        _, c32, _ = O.render(v, cam, w.tf(), [1.0, 1.0, 1.0], None, 0, geometry="fp32")
+        chk = O.check(v, cam, w.tf(), [1.0, 1.0, 1.0], c32[:, 0, :].astype(np.float32))
+        calm = chk["flagged"] == 0
+        assert calm.mean() > 0.95
+        assert np.abs(chk["rgba"][calm] - c32[calm, 0, :]).max() < 2e-5
+        assert chk["err"].max() < 2e-3  # the single-precision march is one of the admissible results
+
+
+def _lod_edge_camera(eps):
+    # one pixel looking down +z through the tiny volume from z = -96: sample k at t = 96 + k/2; the
+    # level-1 threshold t_1 = H / (eps tan(22.5 deg)) equals t = 108 (sample 24) when eps = eps0
+    return S.camera((20.3, 40.1, -96.0), (20.3, 40.1, 32.0), (0.0, 1.0, 0.0), 1, 1, fov_y_deg=45.0,
+                    lod_error_px=eps, step_voxels=0.5, ert_alpha=2.0)
+
+
+def test_knife_edge_at_a_level_threshold_admits_both_levels():
+    """A sample exactly at t_L: both the finer and the coarser level are correct.  The two results
+    are those of cameras whose threshold sits just before / just after that sample (every other
+    sample is 0.5 away from t_L), they differ, and the check admits each of them exactly."""
+    w = S.tiny()
+    v = dense(w.spec().volume(), M=16)
+    tf = w.tf()
+    eps0 = 1.0 / (108.0 * math.tan(math.radians(22.5)))
+    lo = O.render(v, _lod_edge_camera(eps0 * (1 + 1e-3)), tf, [1, 1, 1], ([0], [0]))[1][0, 0]  # sample 24: level 1
+    hi = O.render(v, _lod_edge_camera(eps0 * (1 - 1e-3)), tf, [1, 1, 1], ([0], [0]))[1][0, 0]  # sample 24: level 0
+    assert np.abs(lo - hi).max() > 4e-4
+    cam = _lod_edge_camera(eps0)
+    for target in (lo, hi):
+        r = O.check(v, cam, tf, [1, 1, 1], target.astype(np.float32)[None], ([0], [0]))
+        assert r["flagged"][0] == 1 and r["variants"][0] == 2 and r["unresolved"][0] == 0
+        assert r["err"][0] < 1e-6
+    # a threshold half a step away from every sample is no knife edge
+    r = O.check(v, _lod_edge_camera(1.0 / (108.25 * math.tan(math.radians(22.5)))), tf, [1, 1, 1],
+                hi.astype(np.float32)[None], ([0], [0]))
+    assert r["flagged"][0] == 0 and r["variants"][0] == 1
+
+
+def _split_volume():
+    # x < 32 constant (a homogeneous level-1 subtree with AVG 5000 and no brick), x >= 32 the blobs
+    blob = S.tiny().spec().volume()
+    vol = blob.copy()
+    vol[:, :, :32, :] = 5000
+    return dense(vol, M=16, tau=50)
+
+
+def test_knife_edge_at_a_split_plane_admits_both_children():
+    """A sample on the split plane x = 32 between a brick-less node (AVG) and a brick node: either
+    child is correct.  The ray direction is (0.6, 0, 0.8); it crosses x = 32 at its third sample.
+    Shifting the eye by -+1e-3 voxel puts that sample on one side or the other."""
+    v = _split_volume()
+    tf = S.tiny().tf()
+    tf[..., 3] = np.minimum(1.0, tf[..., 3] * 8.0)
+
+    def cam(dx):
+        e = (1.4 + dx, 20.25, -40.0)
+        return S.camera(e, (e[0] + 60.0, e[1], e[2] + 80.0), (0.0, 1.0, 0.0), 1, 1, lod_error_px=1e-3,
+                        step_voxels=0.5, ert_alpha=2.0)
+
+    left = O.render(v, cam(-1e-3), tf, [1, 1, 1], ([0], [0]))[1][0, 0]
+    right = O.render(v, cam(+1e-3), tf, [1, 1, 1], ([0], [0]))[1][0, 0]
+    assert np.abs(left - right).max() > 1e-3
+    for target in (left, right):
+        r = O.check(v, cam(0.0), tf, [1, 1, 1], target.astype(np.float32)[None], ([0], [0]))
+        assert r["flagged"][0] == 1 and r["variants"][0] == 2
+        assert r["err"][0] < 1e-4  # the shifted cameras move every other sample by 1e-3 voxel
+
+
+def test_ray_along_a_split_plane_is_unresolved():
+    """A ray inside the split plane x = 32 meets a knife edge at every sample of that stretch: more
+    than the enumerated decisions, so the ray is reported unresolved."""
+    v = _split_volume()
+    tf = S.tiny().tf()
+    cam = S.camera((32.0, 20.25, -40.0), (32.0, 20.25, 32.0), (0.0, 1.0, 0.0), 1, 1, lod_error_px=1e-3,
+                   step_voxels=0.5, ert_alpha=2.0)
+    nat = O.render(v, cam, tf, [1, 1, 1], ([0], [0]))[1][0, 0]
+    r = O.check(v, cam, tf, [1, 1, 1], nat.astype(np.float32)[None], ([0], [0]))
+    assert r["unresolved"][0] == 1 and r["flagged"][0] > O.MAXFLAG and r["variants"][0] == 2 ** O.MAXFLAG

@@ -2,6 +2,8 @@
 during a call (memory budgeted up front, or no device-wide synchronisation from cudaMalloc /
 cudaFree allowed).  Called through the C ABI, it must give the same images as vr_render, on two
 calls in a row (its fixed scratch array keeps the previous call's contents and must be reset).
+Both entry points run the same kernel and a pixel does not depend on the order in which tiles are
+taken, so the images must be identical bit for bit, in FP32 and with FP16 interpolation.
 This file is collected last on purpose."""
 import ctypes
 
@@ -9,7 +11,6 @@ import numpy as np
 import pytest
 
 from synth import synth as S
-from tests.helpers import RGBA_TOL
 
 pytestmark = pytest.mark.gpu
 
@@ -31,17 +32,20 @@ def test_noalloc_render_matches_vr_render_twice():
         r.insert_slice(z, dev[z])
     r.set_transfer_functions(torch.from_numpy(w.tf()), torch.ones(3))
     stream = torch.cuda.current_stream().cuda_stream
-    for cams in (S.batch_cameras(w.dims)[::4], w.cameras):  # 16 mixed-size views, then one view
+    # 16 mixed-size views, then one view; DVR, DVR with FP16 interpolation, MIP
+    for cams in (S.batch_cameras(w.dims)[::4], w.cameras):
         n = len(cams)
-        ref = r.render(cams)
         cs = (V.Camera * n)(*[V.camera_struct(c) for c in cams])
-        for _ in range(2):
-            out = [torch.full((c["height"], c["width"], 4), -1.0, device="cuda") for c in cams]
-            ptrs = (ctypes.c_void_p * n)(*[o.data_ptr() for o in out])
-            assert L.vr_render_noalloc(r.handle, cs, n, ptrs, V.VR_MODE_DVR, ctypes.c_void_p(stream)) == V.VR_OK
-            torch.cuda.synchronize()
-            for a, b in zip(out, ref):
-                assert (a - b).abs().max().item() <= RGBA_TOL
+        for mode, fp16 in ((V.VR_MODE_DVR, False), (V.VR_MODE_DVR, True), (V.VR_MODE_MIP, False)):
+            word = mode | (V.VR_RENDER_FP16 if fp16 else 0)
+            ref = r.render(cams, mode=word)
+            for _ in range(2):
+                out = [torch.full((c["height"], c["width"], 4), -1.0, device="cuda") for c in cams]
+                ptrs = (ctypes.c_void_p * n)(*[o.data_ptr() for o in out])
+                assert L.vr_render_noalloc(r.handle, cs, n, ptrs, word, ctypes.c_void_p(stream)) == V.VR_OK
+                torch.cuda.synchronize()
+                for a, b in zip(out, ref):
+                    assert torch.equal(a, b)
     too_many = [w.cameras[0]] * 65
     cs = (V.Camera * 65)(*[V.camera_struct(c) for c in too_many])
     out = torch.empty((128, 128, 4), device="cuda")
