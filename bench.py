@@ -516,10 +516,9 @@ def main():
         w.cameras = [S.streamed(tau=3277, frame=f).cameras[0] for f in frames]
     else:
         # the profiling stand-in for the 24 GiB workload: the same generator and nucleus density on a
-        # 1024x1024x256 volume (a 1.2 GB pool), seen from the large orbit's distance (2 x 2048) so
-        # that its samples fall on level 1 like those of the large frames
+        # 1024x1024x256 volume (2.9 GB pool), orbit at twice its extent; a frame reads ~470 MB of
+        # distinct voxels, more than L2 holds
         w = S.large(tau=3277, frames=frames, dims=(1024, 1024, 256), nuclei=10000)
-        w.cameras = [S.orbit_camera(w.dims, 4096.0, 6.0 * f, 20.0, 1920, 1080) for f in frames]
         w.name = "medium-1024x1024x256x3"
     r = vr.Renderer(w.dims, 3, w.brick, tau=w.tau)
     build_s, spec = build_volume(w, r, torch)

@@ -192,6 +192,15 @@ vr_status vr_render_noalloc(vr_ctx* ctx, const vr_camera* cams, int n_cams, floa
 vr_status vr_render_backward(vr_ctx* ctx, const vr_camera* cams, int n_cams, const float* const* dl_dimages,
                              float* dl_dtf, float* dl_dscale, void* cuda_stream);
 
+/* Accumulation precision of vr_render_backward.  0 (default): single precision throughout.
+ * 1 (FP64 gradient-check mode): the per-ray transmittance and colour of the sweep, the gradient
+ * terms and their sums are double precision, for checks of the gradient element by element
+ * against an FP64 reference; the decisions (samples, runs, early termination) stay those of the
+ * single-precision forward.  Much slower on GPUs with few FP64 units; not for training loops.
+ * The double sums (24 KB) are allocated on the first backward call in this mode.  The paper has
+ * no counterpart.  Errors: VR_ERR_INVALID_ARG (fp64 not 0 or 1), VR_ERR_STATE. */
+vr_status vr_set_gradient_precision(vr_ctx* ctx, int fp64);
+
 /* Measurement hook: vr_render (DVR) that also sets, for every distinct level-L voxel read by a
  * trilinear corner, bit (z*Y_L + y)*X_L + x of voxel_marks[L] (device, N+1 bitmaps of
  * ceil(X_L*Y_L*Z_L/32) words, caller-zeroed), and bit n of node_marks for every node entry the

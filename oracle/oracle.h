@@ -160,6 +160,10 @@ typedef struct {
     int variants;      /* decision variants marched */
     int unresolved;    /* some march met more than OR_MAXFLAG knife-edge decisions */
 } or_check;
+/* Knife-edge margins (defaults 8 and 1.5): the bound on the single-precision error of the unit ray
+ * direction, in units of 2^-24 per component, and the factor applied to the resulting bounds on
+ * the sample parameter and position.  Global; set before rendering. */
+void or_set_edge_margins(double dir_ulps, double safety);
 int or_render_check(or_volume* v, const or_camera* cam, const float* tf, const float* scale, const float* xf, int mode,
                     int geometry, int64_t n, const int32_t* px, const int32_t* py, const float* rgba, double stop_err,
                     or_check* out, int threads);

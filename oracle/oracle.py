@@ -328,6 +328,12 @@ def check(vol: Volume, cam: dict, tf, scale, rgba, pixels=None, mode=0, threads=
     return out[:n]
 
 
+def set_edge_margins(dir_ulps=8.0, safety=1.5):
+    """Knife-edge margins of the double-precision geometry (see or_set_edge_margins)."""
+    lib().or_set_edge_margins.argtypes = [ctypes.c_double, ctypes.c_double]
+    lib().or_set_edge_margins(float(dir_ulps), float(safety))
+
+
 def render_image(vol, cam, tf, scale, mode=0, threads=0, xf=None):
     """Natural-decision image [H][W][4] (float64) plus the candidate arrays."""
     nc, cand, samples = render(vol, cam, tf, scale, None, mode, threads, xf)

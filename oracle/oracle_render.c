@@ -101,8 +101,13 @@ static void cam_setup(const or_geom* g, const or_camera* cam, cam_derived* cd) {
  * two branches sample differently (a different level or brick state, or a different AVG); either
  * branch is then a correct result. */
 static const double U32 = 5.9604644775390625e-08; /* 2^-24 */
-#define OR_DIR_ULPS 32.0
-#define OR_EDGE_SAFETY 2.0
+static double OR_DIR_ULPS = 8.0;    /* measured: <= 2.4 u for IEEE-rounded single-precision setup */
+static double OR_EDGE_SAFETY = 1.5;
+
+void or_set_edge_margins(double dir_ulps, double safety) {
+    OR_DIR_ULPS = dir_ulps;
+    OR_EDGE_SAFETY = safety;
+}
 
 typedef struct {
     const unsigned char* force; /* forced branches of the first nforce flagged decisions (1 = other) */

@@ -95,6 +95,8 @@ struct vr_ctx {
     bool store_host = false;
     int has_xf = 0;                     // per-channel sample transforms (identity when 0)
     float xf[VR_MAX_CHANNELS][12] = {};
+    int grad_fp64 = 0;                  // vr_render_backward: FP64 gradient-check mode
+    double* d_gacc = nullptr;           // its double sums [C * 1024 + C]
     bool failed = false;
     std::string msg;
 };
@@ -259,6 +261,7 @@ static void destroy_all(vr_ctx* c) {
     }
     if (c->up_stream) cudaStreamDestroy(c->up_stream);
     dfree(c, c->d_list);
+    dfree(c, c->d_gacc);
     dfree(c, c->d_cams);
     if (c->h_list) cudaFreeHost(c->h_list);
     if (c->h_cams) cudaFreeHost(c->h_cams);
@@ -769,6 +772,15 @@ vr_status vr_render_backward(vr_ctx* c, const vr_camera* cams, int n, const floa
     a.stats = nullptr;
     a.dtf = dtf;
     a.dscale = dscale;
+    if (c->grad_fp64) {
+        const size_t nb = sizeof(double) * (size_t)(c->g.C * 1024 + c->g.C);
+        if (!c->d_gacc) {
+            c->d_gacc = (double*)dalloc(c, nb);
+            if (!c->d_gacc) return fail(c, VR_ERR_OUT_OF_MEMORY, "FP64 gradient buffer");
+        }
+        CK(c, cudaMemsetAsync(c->d_gacc, 0, nb, st));
+        a.dacc = c->d_gacc;
+    }
     CK(c, launch_render_backward(a, grid_for(c, tiles, 128, 5), 128, st));
     return VR_OK;
 }
@@ -1134,6 +1146,14 @@ vr_status vr_set_tile_shape(vr_ctx* c, int tw, int th) {
 vr_status vr_set_mip_segment_length(vr_ctx* c, int samples) {
     if (!c || samples < 0 || (samples > 0 && samples < 4) || samples > (1 << 24)) return VR_ERR_INVALID_ARG;
     c->kseg_mip = samples;
+    return VR_OK;
+}
+
+vr_status vr_set_gradient_precision(vr_ctx* c, int fp64) {
+    vr_status s = check_ctx(c);
+    if (s != VR_OK) return s;
+    if (fp64 != 0 && fp64 != 1) return fail(c, VR_ERR_INVALID_ARG, "gradient precision must be 0 or 1");
+    c->grad_fp64 = fp64;
     return VR_OK;
 }
 

@@ -84,7 +84,7 @@ struct CacheArgs {
 };
 
 struct RefineState { // one pixel of a refinement session
-    float C[3], A;
+    float C[3], T; // premultiplied colour and transmittance (1 - opacity) so far
     int k;      // next sample index
     int status; // 0 = not started, 1 = suspended, 2 = done
     int pad[2];
@@ -118,6 +118,7 @@ struct RenderArgs {
     unsigned int* tile_cost;            // per tile: SM clock cycles / 64 it took (nullptr: not kept)
     float* dtf;                         // backward: [C][256][4]
     float* dscale;                      // backward: [C]
+    double* dacc;                       // backward, FP64 check mode: [C * 1024 + C] sums (zeroed)
     int* err;
 };
 

@@ -676,13 +676,14 @@ struct NoHooks {
 // n samples of one constant intensity, each a per-sample transfer T' = T q, C' = C + T K:
 // after j samples T_j = T q^j and C_j = C + T K (1 - q^j) / (1 - q).  Early termination at the
 // first j with 1 - T q^j >= ert.  ln q and 1 - q^j come from log1p/expm1 (no cancellation).
-__device__ __forceinline__ long long composite_run(float lnq, const float K[3], long long n, float ert, float& A,
+// State in transmittance form (T = 1 - A).
+__device__ __forceinline__ long long composite_run(float lnq, const float K[3], long long n, float ert, float& T,
                                                    float& Cr, float& Cg, float& Cb, bool& stop) {
-    const float T = 1.0f - A;
+    const float T0 = T;
     long long j = n;
     stop = false;
     if (lnq < 0.0f && ert <= 1.0f) {
-        const float target = (1.0f - ert) / T;
+        const float target = (1.0f - ert) / T0;
         float jj = (target >= 1.0f) ? 1.0f : ceilf(logf(target) / lnq);
         if (jj < 1.0f) jj = 1.0f;
         if (jj <= (float)n) {
@@ -691,94 +692,90 @@ __device__ __forceinline__ long long composite_run(float lnq, const float K[3], 
         }
     }
     const float S = (lnq < 0.0f) ? expm1f((float)j * lnq) / expm1f(lnq) : (float)j;
-    Cr = fmaf(T * K[0], S, Cr);
-    Cg = fmaf(T * K[1], S, Cg);
-    Cb = fmaf(T * K[2], S, Cb);
-    A = 1.0f - T * expf((float)j * lnq);
+    Cr = fmaf(T0 * K[0], S, Cr);
+    Cg = fmaf(T0 * K[1], S, Cg);
+    Cb = fmaf(T0 * K[2], S, Cb);
+    T = T0 * expf((float)j * lnq);
     return j;
+}
+
+// Emission-absorption compositing in two steps.  A sample is first shaded on its own, over the
+// channels in order (the composite sits inside the channel loop of Algorithm 1):
+//   P_0 = 1,  rgb_s += P_c a_c rgb_c,  P_{c+1} = P_c (1 - a_c),  q_s = P_C;
+// then composited into the ray: C += T rgb_s, T *= q_s (T = 1 - A, the transmittance), and the ray
+// stops once 1 - T >= ert.  Only the second step depends on the ray's state, so samples shaded by
+// different lanes and composited in order by each of them give the same bits as one lane marching
+// alone, in single steps, in pairs or in any grouping.
+struct Shaded {
+    float r, g, b, q;
+};
+
+__device__ __forceinline__ Shaded shfl_shaded(unsigned mask, const Shaded& s, int src) {
+    return Shaded{__shfl_sync(mask, s.r, src), __shfl_sync(mask, s.g, src), __shfl_sync(mask, s.b, src),
+                  __shfl_sync(mask, s.q, src)};
 }
 
 template <int C, bool RUNS = true, bool PAIRS = RUNS>
 struct DVRComposite : NoHooks {
     static constexpr bool kRuns = RUNS;
+    static constexpr bool kPairs = PAIRS;
     const float4* s_tf;
     const float* s_scl;
     float ert;
-    float A = 0.0f, Cr = 0.0f, Cg = 0.0f, Cb = 0.0f;
+    float T = 1.0f, Cr = 0.0f, Cg = 0.0f, Cb = 0.0f;
+    __device__ __forceinline__ Shaded shade(const float (&I)[C], float ell) const {
+        Shaded s{0.0f, 0.0f, 0.0f, 1.0f};
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            TFLookup<C> t;
+            t.eval(s_tf, s_scl, c, I[c]);
+            const float al = fminf(fmaxf(t.al, 0.0f), ALPHA_MAX);
+            float a, oma;
+            opacity(al, ell, a, oma);
+            const float w = s.q * a;
+            s.r = fmaf(w, t.r, s.r);
+            s.g = fmaf(w, t.g, s.g);
+            s.b = fmaf(w, t.b, s.b);
+            s.q *= oma;
+        }
+        return s;
+    }
+    __device__ __forceinline__ bool update(const Shaded& s) {
+        Cr = fmaf(T, s.r, Cr);
+        Cg = fmaf(T, s.g, Cg);
+        Cb = fmaf(T, s.b, Cb);
+        T *= s.q;
+        return 1.0f - T >= ert;
+    }
     __device__ __forceinline__ long long run(const float (&I)[C], long long n, float ell, bool& stop) {
-        float lnq = 0.0f, qpre = 1.0f, K[3] = {0.0f, 0.0f, 0.0f};
+        float lnq = 0.0f, K[3];
+        const Shaded s = shade(I, ell);
+        K[0] = s.r;
+        K[1] = s.g;
+        K[2] = s.b;
 #pragma unroll
         for (int c = 0; c < C; ++c) {
             TFLookup<C> t;
             t.eval(s_tf, s_scl, c, I[c]);
-            const float al = fminf(fmaxf(t.al, 0.0f), ALPHA_MAX);
-            float a, oma;
-            opacity(al, ell, a, oma);
-            const float w = qpre * a;
-            K[0] = fmaf(w, t.r, K[0]);
-            K[1] = fmaf(w, t.g, K[1]);
-            K[2] = fmaf(w, t.b, K[2]);
-            qpre *= oma;
-            lnq += ell * log1pf(-al);
+            lnq += ell * log1pf(-fminf(fmaxf(t.al, 0.0f), ALPHA_MAX));
         }
-        return composite_run(lnq, K, n, ert, A, Cr, Cg, Cb, stop);
+        return composite_run(lnq, K, n, ert, T, Cr, Cg, Cb, stop);
     }
-    // Two full-segment samples: shading of both first, then compositing in order.  Returns 1 when
-    // the first sample terminates the ray (the second is dropped), 2 when the second does, else 0.
-    static constexpr bool kPairs = PAIRS;
+    // Two full-segment samples: both shaded first (their gathers and lookups overlap), then
+    // composited in order.  Returns 1 when the first sample terminates the ray (the second is
+    // dropped), 2 when the second does, else 0.
     __device__ __forceinline__ int sample2(const float (&I1)[C], const float (&I2)[C], float ell) {
-        float r[2][C], gg[2][C], b[2][C], a[2][C], om[2][C];
-#pragma unroll
-        for (int s2 = 0; s2 < 2; ++s2)
-#pragma unroll
-            for (int c = 0; c < C; ++c) {
-                TFLookup<C> t;
-                t.eval(s_tf, s_scl, c, s2 ? I2[c] : I1[c]);
-                const float al = fminf(fmaxf(t.al, 0.0f), ALPHA_MAX);
-                opacity(al, ell, a[s2][c], om[s2][c]);
-                r[s2][c] = t.r;
-                gg[s2][c] = t.g;
-                b[s2][c] = t.b;
-            }
-        float T = 1.0f - A;
-#pragma unroll
-        for (int s2 = 0; s2 < 2; ++s2) {
-#pragma unroll
-            for (int c = 0; c < C; ++c) {
-                const float w = T * a[s2][c];
-                Cr = fmaf(w, r[s2][c], Cr);
-                Cg = fmaf(w, gg[s2][c], Cg);
-                Cb = fmaf(w, b[s2][c], Cb);
-                T *= om[s2][c];
-            }
-            A = 1.0f - T;
-            if (A >= ert) return s2 + 1;
-        }
-        return 0;
+        const Shaded s1 = shade(I1, ell), s2 = shade(I2, ell);
+        if (update(s1)) return 1;
+        return update(s2) ? 2 : 0;
     }
-    __device__ __forceinline__ bool sample(const float (&I)[C], float ell) {
-        float T = 1.0f - A; // transmittance: w = T a, T <- T (1 - a)
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-            TFLookup<C> t;
-            t.eval(s_tf, s_scl, c, I[c]);
-            const float al = fminf(fmaxf(t.al, 0.0f), ALPHA_MAX);
-            float a, oma;
-            opacity(al, ell, a, oma);
-            const float w = T * a;
-            Cr = fmaf(w, t.r, Cr);
-            Cg = fmaf(w, t.g, Cg);
-            Cb = fmaf(w, t.b, Cb);
-            T *= oma;
-        }
-        A = 1.0f - T;
-        return A >= ert;
-    }
+    __device__ __forceinline__ bool sample(const float (&I)[C], float ell) { return update(shade(I, ell)); }
+    __device__ __forceinline__ float alpha() const { return 1.0f - T; }
 };
 
 // FP16 variant of the DVR functor: I is the FP16-interpolated normalised intensity; the
 // transfer-function lookup reads a half table (entry, next - entry) and interpolates in half2;
-// opacity correction and compositing stay FP32.
+// opacity correction and compositing stay FP32 (the same two steps as above).
 struct __align__(16) HalfEntry {
     __half2 rg, ba, drg, dba;
 };
@@ -786,10 +783,11 @@ struct __align__(16) HalfEntry {
 template <int C>
 struct DVRCompositeH : NoHooks {
     static constexpr bool kRuns = true;
+    static constexpr bool kPairs = true;
     const HalfEntry* s_tfh;
     const __half* s_sh; // per-channel scale s (normalised intensities)
     float ert;
-    float A = 0.0f, Cr = 0.0f, Cg = 0.0f, Cb = 0.0f;
+    float T = 1.0f, Cr = 0.0f, Cg = 0.0f, Cb = 0.0f;
     __device__ __forceinline__ void lookup(int c, float I, float2& rg, float2& ba) const {
         const __half x = __hmul_sat(__float2half_rn(I), s_sh[c]);
         const float w = __half2float(x) * 255.0f;
@@ -799,67 +797,51 @@ struct DVRCompositeH : NoHooks {
         rg = __half22float2(__hfma2(lam, e.drg, e.rg));
         ba = __half22float2(__hfma2(lam, e.dba, e.ba));
     }
+    __device__ __forceinline__ Shaded shade(const float (&I)[C], float ell) const {
+        Shaded s{0.0f, 0.0f, 0.0f, 1.0f};
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            float2 rg, ba;
+            lookup(c, I[c], rg, ba);
+            const float al = fminf(fmaxf(ba.y, 0.0f), ALPHA_MAX);
+            float a, oma;
+            opacity(al, ell, a, oma);
+            const float w = s.q * a;
+            s.r = fmaf(w, rg.x, s.r);
+            s.g = fmaf(w, rg.y, s.g);
+            s.b = fmaf(w, ba.x, s.b);
+            s.q *= oma;
+        }
+        return s;
+    }
+    __device__ __forceinline__ bool update(const Shaded& s) {
+        Cr = fmaf(T, s.r, Cr);
+        Cg = fmaf(T, s.g, Cg);
+        Cb = fmaf(T, s.b, Cb);
+        T *= s.q;
+        return 1.0f - T >= ert;
+    }
     __device__ __forceinline__ long long run(const float (&I)[C], long long n, float ell, bool& stop) {
-        float lnq = 0.0f, qpre = 1.0f, K[3] = {0.0f, 0.0f, 0.0f};
+        float lnq = 0.0f, K[3];
+        const Shaded s = shade(I, ell);
+        K[0] = s.r;
+        K[1] = s.g;
+        K[2] = s.b;
 #pragma unroll
         for (int c = 0; c < C; ++c) {
             float2 rg, ba;
             lookup(c, I[c], rg, ba);
-            const float al = fminf(fmaxf(ba.y, 0.0f), ALPHA_MAX);
-            float a, oma;
-            opacity(al, ell, a, oma);
-            const float w = qpre * a;
-            K[0] = fmaf(w, rg.x, K[0]);
-            K[1] = fmaf(w, rg.y, K[1]);
-            K[2] = fmaf(w, ba.x, K[2]);
-            qpre *= oma;
-            lnq += ell * log1pf(-al);
+            lnq += ell * log1pf(-fminf(fmaxf(ba.y, 0.0f), ALPHA_MAX));
         }
-        return composite_run(lnq, K, n, ert, A, Cr, Cg, Cb, stop);
+        return composite_run(lnq, K, n, ert, T, Cr, Cg, Cb, stop);
     }
-    static constexpr bool kPairs = true;
     __device__ __forceinline__ int sample2(const float (&I1)[C], const float (&I2)[C], float ell) {
-        float2 rg[2][C], ba[2][C];
-        float a[2][C];
-#pragma unroll
-        for (int s2 = 0; s2 < 2; ++s2)
-#pragma unroll
-            for (int c = 0; c < C; ++c) {
-                lookup(c, s2 ? I2[c] : I1[c], rg[s2][c], ba[s2][c]);
-                const float al = fminf(fmaxf(ba[s2][c].y, 0.0f), ALPHA_MAX);
-                float oma;
-                opacity(al, ell, a[s2][c], oma);
-            }
-#pragma unroll
-        for (int s2 = 0; s2 < 2; ++s2) {
-#pragma unroll
-            for (int c = 0; c < C; ++c) {
-                const float wgt = (1.0f - A) * a[s2][c];
-                Cr = fmaf(wgt, rg[s2][c].x, Cr);
-                Cg = fmaf(wgt, rg[s2][c].y, Cg);
-                Cb = fmaf(wgt, ba[s2][c].x, Cb);
-                A += wgt;
-            }
-            if (A >= ert) return s2 + 1;
-        }
-        return 0;
+        const Shaded s1 = shade(I1, ell), s2 = shade(I2, ell);
+        if (update(s1)) return 1;
+        return update(s2) ? 2 : 0;
     }
-    __device__ __forceinline__ bool sample(const float (&I)[C], float ell) {
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-            float2 rg, ba;
-            lookup(c, I[c], rg, ba);
-            const float al = fminf(fmaxf(ba.y, 0.0f), ALPHA_MAX);
-            float a, oma;
-            opacity(al, ell, a, oma);
-            const float wgt = (1.0f - A) * a;
-            Cr = fmaf(wgt, rg.x, Cr);
-            Cg = fmaf(wgt, rg.y, Cg);
-            Cb = fmaf(wgt, ba.x, Cb);
-            A += wgt;
-        }
-        return A >= ert;
-    }
+    __device__ __forceinline__ bool sample(const float (&I)[C], float ell) { return update(shade(I, ell)); }
+    __device__ __forceinline__ float alpha() const { return 1.0f - T; }
 };
 
 // DVR that also records the distinct (level, voxel) pairs read by trilinear corners and the
@@ -1041,7 +1023,7 @@ __global__ void __launch_bounds__(256, VR_RENDER_MIN_CTAS) render_kernel(RenderA
                     out = make_float4(Cr, Cg, Cb, A);
                 }
             } else {
-                out = make_float4(f.Cr, f.Cg, f.Cb, f.A);
+                out = make_float4(f.Cr, f.Cg, f.Cb, f.alpha());
             }
         }
         reinterpret_cast<float4*>(cp->img)[(long long)py * cp->W + px] = out;
@@ -1056,49 +1038,115 @@ __global__ void __launch_bounds__(256, VR_RENDER_MIN_CTAS) render_kernel(RenderA
     }
 }
 
-// Reverse-mode sweep in forward order.  With the final (C_f, A_f) of the ray known, the adjoint
+// One constant sample's shading in double precision (the FP64 gradient-check mode): per channel
+// the opacity a_c, 1 - a_c and rgb_c from the single-precision lookup, the local colour K and
+// transmittance P_C of the sample, and ln q = sum_c l ln(1 - alpha_c) for runs.
+template <int C>
+struct ShadeD {
+    TFLookup<C> t[C];
+    float a[C], oma[C], al[C];
+    double P[C], R[C][3], K[3], q, lnq;
+    __device__ __forceinline__ void eval(const float4* s_tf, const float* s_scl, const float (&I)[C], float ell) {
+        double pre = 1.0;
+        K[0] = K[1] = K[2] = 0.0;
+        lnq = 0.0;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            t[c].eval(s_tf, s_scl, c, I[c]);
+            al[c] = fminf(fmaxf(t[c].al, 0.0f), ALPHA_MAX);
+            opacity(al[c], ell, a[c], oma[c]);
+            P[c] = pre;
+            const double w = pre * (double)a[c];
+            K[0] += w * (double)t[c].r;
+            K[1] += w * (double)t[c].g;
+            K[2] += w * (double)t[c].b;
+            R[c][0] = K[0];
+            R[c][1] = K[1];
+            R[c][2] = K[2];
+            pre *= (double)oma[c];
+            lnq += (double)ell * log1p(-(double)al[c]);
+        }
+        q = pre;
+    }
+};
+
+// The adjoint's forward pass in the FP64 check mode: the single-precision march decides (the
+// same samples, runs and stop as DVRComposite), and the ray's colour and transmittance are
+// accumulated alongside in double precision for the sweep's suffix terms.
+template <int C>
+struct DVRForwardD : DVRComposite<C, true, false> {
+    using B = DVRComposite<C, true, false>;
+    double Cd[3] = {0.0, 0.0, 0.0}, Td = 1.0;
+    __device__ __forceinline__ bool sample(const float (&I)[C], float ell) {
+        ShadeD<C> sd;
+        sd.eval(B::s_tf, B::s_scl, I, ell);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) Cd[i] += Td * sd.K[i];
+        Td *= sd.q;
+        return B::sample(I, ell);
+    }
+    __device__ __forceinline__ long long run(const float (&I)[C], long long n, float ell, bool& stop) {
+        ShadeD<C> sd;
+        sd.eval(B::s_tf, B::s_scl, I, ell);
+        const long long j = B::run(I, n, ell, stop);
+        const double nj = (double)j;
+        const double S = sd.lnq < 0.0 ? expm1(nj * sd.lnq) / expm1(sd.lnq) : nj;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) Cd[i] += Td * sd.K[i] * S;
+        Td *= exp(nj * sd.lnq);
+        return j;
+    }
+};
+
+// Reverse-mode sweep in forward order.  With the final (C_f, T_f) of the ray known, the adjoint
 // of channel-step j of the update C += T a rgb, T <- T (1 - a) (T = 1 - A) is
-//   dL/da_j   = T_j gC.rgb_j + [ -gC.(C_f - C_j+) + gA_f (1 - A_f) ] / (1 - a_j),
+//   dL/da_j   = T_j gC.rgb_j + [ -gC.(C_f - C_j+) + gA_f T_f ] / (1 - a_j),
 //   dL/drgb_j = gC T_j a_j,     da/dalpha = l (1 - a) / (1 - alpha).
-// The sweep repeats the forward arithmetic of DVRComposite (transmittance form, closed-form runs
-// through brick-less nodes, no pairs) so that it stops at the same sample.  A run of n equal
-// samples contributes the sums over its samples in closed form: sample s, channel c has
+// The sweep repeats the forward's single-precision arithmetic (DVRComposite: the two-step
+// composite, closed-form runs through brick-less nodes) so that it stops at the same sample.  A run
+// of n equal samples contributes the sums over its samples in closed form: sample s, channel c has
 // T_{s,c} = T_0 q^s P_c (P_c = prod_{c' < c} (1 - a_c'), q = P_C) and
 // C_(s,c)+ = C_0 + T_0 K (1 - q^s) / (1 - q) + T_0 q^s R_c (R_c = sum_{c' <= c} P_c' a_c' rgb_c',
 // K = R_{C-1}), so every term is a geometric series in q.
-template <int C>
+// D = true (FP64 gradient-check mode): transmittance, colour, the gradient terms and their sums
+// are double precision (the decisions stay those of the single-precision forward); the
+// table-entry sums go to double shared-memory accumulators.
+template <int C, bool D = false>
 struct DVRAdjoint : NoHooks {
+    using R = std::conditional_t<D, double, float>;
     static constexpr bool kRuns = true;
     const float4* s_tf;
     const float* s_scl;
-    float* s_dtf; // [C][256][4]
+    R* s_dtf; // [C][256][4]
     float ert;
-    float gC[3], gAf, Cf[3], Af;
-    float A = 0.0f, Cp[3] = {0.0f, 0.0f, 0.0f};
-    float dsc[C];
+    R gC[3], gAf, Cf[3], Tf;
+    // the forward's single-precision state (decides the stop); in the D mode also a double copy
+    float T = 1.0f, Cp[3] = {0.0f, 0.0f, 0.0f};
+    R Td = 1.0, Cd[3] = {0.0, 0.0, 0.0};
+    R dsc[C];
     // Per channel, the table-entry pair (i, i+1) this lane is accumulating into and the pending
     // sums S = sum g and L = sum lam g (entry i receives S - L, entry i+1 receives L).  Samples
     // of one ray mostly stay on one pair, so shared-memory atomics happen once per change of
     // pair instead of once per sample (32 lanes hitting one entry serialise).
     int pk[C];
-    float pS[C][4], pL[C][4];
+    R pS[C][4], pL[C][4];
     __device__ __forceinline__ void reset() {
 #pragma unroll
         for (int c = 0; c < C; ++c) {
             pk[c] = -1;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) pS[c][q] = pL[c][q] = 0.0f;
+            for (int q = 0; q < 4; ++q) pS[c][q] = pL[c][q] = (R)0;
         }
     }
     __device__ __forceinline__ void flush(int c) {
         if (pk[c] < 0) return;
-        float* e0 = s_dtf + (c * 256 + pk[c]) * 4;
+        R* e0 = s_dtf + (c * 256 + pk[c]) * 4;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const float lo = pS[c][q] - pL[c][q];
-            if (lo != 0.0f) atomicAdd(e0 + q, lo);
-            if (pL[c][q] != 0.0f) atomicAdd(e0 + 4 + q, pL[c][q]);
-            pS[c][q] = pL[c][q] = 0.0f;
+            const R lo = pS[c][q] - pL[c][q];
+            if (lo != (R)0) atomicAdd(e0 + q, lo);
+            if (pL[c][q] != (R)0) atomicAdd(e0 + 4 + q, pL[c][q]);
+            pS[c][q] = pL[c][q] = (R)0;
         }
     }
     __device__ __forceinline__ void flush_all() {
@@ -1106,9 +1154,9 @@ struct DVRAdjoint : NoHooks {
         for (int c = 0; c < C; ++c) flush(c);
     }
     // table gradient gq (rgba) of channel c at lookup t, and the scale gradient
-    __device__ __forceinline__ void accumulate(int c, const TFLookup<C>& t, const float (&gq)[4], float I) {
-        const float4 D = s_tf[(C + c) * 256 + t.i];
-        const float glam = gq[0] * D.x + gq[1] * D.y + gq[2] * D.z + gq[3] * D.w;
+    __device__ __forceinline__ void accumulate(int c, const TFLookup<C>& t, const R (&gq)[4], float I) {
+        const float4 Dv = s_tf[(C + c) * 256 + t.i];
+        const R glam = gq[0] * (R)Dv.x + gq[1] * (R)Dv.y + gq[2] * (R)Dv.z + gq[3] * (R)Dv.w;
         if (t.i != pk[c]) {
             flush(c);
             pk[c] = t.i;
@@ -1116,15 +1164,27 @@ struct DVRAdjoint : NoHooks {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             pS[c][q] += gq[q];
-            pL[c][q] = fmaf(t.lam, gq[q], pL[c][q]);
+            pL[c][q] += (R)t.lam * gq[q];
         }
-        if (t.xr > 0.0f && t.xr < 1.0f) dsc[c] += glam * 255.0f * I * (1.0f / 65535.0f);
+        if (t.xr > 0.0f && t.xr < 1.0f) dsc[c] += glam * (R)255.0f * (R)I * (R)(1.0f / 65535.0f);
     }
-    __device__ __forceinline__ float suffix_term() const {
-        return -(gC[0] * (Cf[0] - Cp[0]) + gC[1] * (Cf[1] - Cp[1]) + gC[2] * (Cf[2] - Cp[2])) + gAf * (1.0f - Af);
+    // the math state: the double copy in the D mode, the forward's own otherwise
+    __device__ __forceinline__ R Tm() const {
+        if constexpr (D) return Td;
+        else return T;
+    }
+    __device__ __forceinline__ R Cm(int i) const {
+        if constexpr (D) return Cd[i];
+        else return Cp[i];
+    }
+    __device__ __forceinline__ R suffix(const R (&Cj)[3]) const {
+        return -(gC[0] * (Cf[0] - Cj[0]) + gC[1] * (Cf[1] - Cj[1]) + gC[2] * (Cf[2] - Cj[2])) + gAf * Tf;
     }
     __device__ __forceinline__ bool sample(const float (&I)[C], float ell) {
-        float T = 1.0f - A;
+        const R T0 = Tm();
+        const R C0[3] = {Cm(0), Cm(1), Cm(2)};
+        Shaded s{0.0f, 0.0f, 0.0f, 1.0f}; // the forward's single-precision shading
+        R P = (R)1, cs[3] = {(R)0, (R)0, (R)0};
 #pragma unroll
         for (int c = 0; c < C; ++c) {
             TFLookup<C> t;
@@ -1133,71 +1193,130 @@ struct DVRAdjoint : NoHooks {
             const float al = fminf(fmaxf(t.al, 0.0f), ALPHA_MAX);
             float a, oma;
             opacity(al, ell, a, oma);
-            const float w = T * a;
-            Cp[0] = fmaf(w, t.r, Cp[0]);
-            Cp[1] = fmaf(w, t.g, Cp[1]);
-            Cp[2] = fmaf(w, t.b, Cp[2]);
-            const float ga = T * (gC[0] * t.r + gC[1] * t.g + gC[2] * t.b) + suffix_term() / oma;
-            const float gq[4] = {gC[0] * w, gC[1] * w, gC[2] * w, clamped ? 0.0f : ga * ell * oma / (1.0f - al)};
+            const float w32 = s.q * a;
+            R Pc, Cj[3];
+            if constexpr (D) {
+                Pc = P;
+                cs[0] += P * (R)a * (R)t.r;
+                cs[1] += P * (R)a * (R)t.g;
+                cs[2] += P * (R)a * (R)t.b;
+                P *= (R)oma;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) Cj[i] = C0[i] + T0 * cs[i];
+            } else {
+                Pc = s.q;
+            }
+            s.r = fmaf(w32, t.r, s.r);
+            s.g = fmaf(w32, t.g, s.g);
+            s.b = fmaf(w32, t.b, s.b);
+            s.q *= oma;
+            if constexpr (!D) {
+                Cj[0] = fmaf(T0, s.r, C0[0]);
+                Cj[1] = fmaf(T0, s.g, C0[1]);
+                Cj[2] = fmaf(T0, s.b, C0[2]);
+            }
+            const R Tc = T0 * Pc;
+            const R w = Tc * (R)a;
+            const R ga = Tc * (gC[0] * (R)t.r + gC[1] * (R)t.g + gC[2] * (R)t.b) + suffix(Cj) / (R)oma;
+            const R gq[4] = {gC[0] * w, gC[1] * w, gC[2] * w,
+                             clamped ? (R)0 : ga * (R)ell * (R)oma / (R)(1.0f - al)};
             accumulate(c, t, gq, I[c]);
-            T *= oma;
         }
-        A = 1.0f - T;
-        return A >= ert;
+        if constexpr (D) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) Cd[i] += Td * cs[i];
+            Td *= P;
+        }
+        Cp[0] = fmaf(T, s.r, Cp[0]);
+        Cp[1] = fmaf(T, s.g, Cp[1]);
+        Cp[2] = fmaf(T, s.b, Cp[2]);
+        T *= s.q;
+        return 1.0f - T >= ert;
     }
     __device__ __forceinline__ long long run(const float (&I)[C], long long n, float ell, bool& stop) {
+        const R T0 = Tm();
+        const R C0[3] = {Cm(0), Cm(1), Cm(2)};
+        const R alpha0 = suffix(C0); // before the run
+        // the forward's single-precision closed form decides the samples used and the stop
+        DVRComposite<C, true, false> fw{{}, s_tf, s_scl, ert};
+        fw.T = T;
+        fw.Cr = Cp[0];
+        fw.Cg = Cp[1];
+        fw.Cb = Cp[2];
+        const long long j = fw.run(I, n, ell, stop);
+        T = fw.T;
+        Cp[0] = fw.Cr;
+        Cp[1] = fw.Cg;
+        Cp[2] = fw.Cb;
+        // geometric sums over the run, in R
         TFLookup<C> t[C];
-        float a[C], oma[C], al[C], P[C], R[C][3];
-        float lnq = 0.0f, qpre = 1.0f, K[3] = {0.0f, 0.0f, 0.0f};
+        float a[C], oma[C], al[C];
+        R Pw[C], Rc[C][3], K[3] = {(R)0, (R)0, (R)0}, pre = (R)1, lnq = (R)0;
 #pragma unroll
         for (int c = 0; c < C; ++c) {
             t[c].eval(s_tf, s_scl, c, I[c]);
             al[c] = fminf(fmaxf(t[c].al, 0.0f), ALPHA_MAX);
             opacity(al[c], ell, a[c], oma[c]);
-            P[c] = qpre;
-            const float w = qpre * a[c];
-            K[0] = fmaf(w, t[c].r, K[0]);
-            K[1] = fmaf(w, t[c].g, K[1]);
-            K[2] = fmaf(w, t[c].b, K[2]);
-            R[c][0] = K[0];
-            R[c][1] = K[1];
-            R[c][2] = K[2];
-            qpre *= oma[c];
-            lnq += ell * log1pf(-al[c]);
+            Pw[c] = pre;
+            const R w = pre * (R)a[c];
+            K[0] += w * (R)t[c].r;
+            K[1] += w * (R)t[c].g;
+            K[2] += w * (R)t[c].b;
+            Rc[c][0] = K[0];
+            Rc[c][1] = K[1];
+            Rc[c][2] = K[2];
+            pre *= (R)oma[c];
+            if constexpr (D) lnq += (R)ell * log1p(-(R)al[c]);
+            else lnq += ell * log1pf(-al[c]);
         }
-        const float T0 = 1.0f - A;
-        const float alpha0 = suffix_term(); // before the run: C_0 = Cp
-        const long long j = composite_run(lnq, K, n, ert, A, Cp[0], Cp[1], Cp[2], stop);
-        const float nj = (float)j;
-        const float Sg = (lnq < 0.0f) ? expm1f(nj * lnq) / expm1f(lnq) : nj; // sum_{s<j} q^s
-        const float beta = (lnq < 0.0f) ? T0 * (gC[0] * K[0] + gC[1] * K[1] + gC[2] * K[2]) / -expm1f(lnq) : 0.0f;
+        const R nj = (R)j;
+        R Sg, em1;
+        if constexpr (D) {
+            em1 = expm1(lnq);
+            Sg = lnq < 0.0 ? expm1(nj * lnq) / em1 : nj; // sum_{s<j} q^s
+        } else {
+            em1 = expm1f(lnq);
+            Sg = lnq < 0.0f ? expm1f(nj * lnq) / em1 : nj;
+        }
+        const R beta = lnq < (R)0 ? T0 * (gC[0] * K[0] + gC[1] * K[1] + gC[2] * K[2]) / -em1 : (R)0;
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-            const float gamma = T0 * (gC[0] * R[c][0] + gC[1] * R[c][1] + gC[2] * R[c][2]);
-            const float ga = T0 * P[c] * (gC[0] * t[c].r + gC[1] * t[c].g + gC[2] * t[c].b) * Sg +
-                             (alpha0 * nj + beta * (nj - Sg) + gamma * Sg) / oma[c];
-            const float wsum = T0 * P[c] * a[c] * Sg;
+            const R gamma = T0 * (gC[0] * Rc[c][0] + gC[1] * Rc[c][1] + gC[2] * Rc[c][2]);
+            const R ga = T0 * Pw[c] * (gC[0] * (R)t[c].r + gC[1] * (R)t[c].g + gC[2] * (R)t[c].b) * Sg +
+                         (alpha0 * nj + beta * (nj - Sg) + gamma * Sg) / (R)oma[c];
+            const R wsum = T0 * Pw[c] * (R)a[c] * Sg;
             const bool clamped = !(t[c].al >= 0.0f && t[c].al <= ALPHA_MAX);
-            const float gq[4] = {gC[0] * wsum, gC[1] * wsum, gC[2] * wsum,
-                                 clamped ? 0.0f : ga * ell * oma[c] / (1.0f - al[c])};
+            const R gq[4] = {gC[0] * wsum, gC[1] * wsum, gC[2] * wsum,
+                             clamped ? (R)0 : ga * (R)ell * (R)oma[c] / (R)(1.0f - al[c])};
             accumulate(c, t[c], gq, I[c]);
+        }
+        if constexpr (D) {
+            // the same double closed form as DVRForwardD::run
+            ShadeD<C> sd;
+            sd.eval(s_tf, s_scl, I, ell);
+            const double S = sd.lnq < 0.0 ? expm1((double)j * sd.lnq) / expm1(sd.lnq) : (double)j;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) Cd[i] += Td * sd.K[i] * S;
+            Td *= exp((double)j * sd.lnq);
         }
         return j;
     }
 };
 
 // 5 resident 128-thread CTAs per SM (96 registers): measured faster than 3 (127 registers) or 6.
-template <int C, int VS, bool POW2, bool XF = false>
+// D: the FP64 gradient-check mode (double sums; per-CTA sums added into a double buffer, a.dacc).
+template <int C, int VS, bool POW2, bool XF = false, bool D = false>
 __global__ void __launch_bounds__(128, 5) render_backward_kernel(RenderArgs a) {
+    using R = std::conditional_t<D, double, float>;
     extern __shared__ float4 s_tf[];
     __shared__ float s_scl[MAXC];
-    float* s_dtf = reinterpret_cast<float*>(s_tf + C * 512);
-    for (int i = threadIdx.x; i < C * 1024; i += blockDim.x) s_dtf[i] = 0.0f;
+    R* s_dtf = reinterpret_cast<R*>(s_tf + C * 512);
+    for (int i = threadIdx.x; i < C * 1024; i += blockDim.x) s_dtf[i] = (R)0;
     load_tables(a, C, s_tf, s_scl);
     const int lane = threadIdx.x & 31;
-    float dsc[C];
+    R dsc[C];
 #pragma unroll
-    for (int c = 0; c < C; ++c) dsc[c] = 0.0f;
+    for (int c = 0; c < C; ++c) dsc[c] = (R)0;
     for (;;) {
         unsigned int tile = 0;
         if (lane == 0) tile = atomicAdd(a.counter, 1u);
@@ -1213,12 +1332,16 @@ __global__ void __launch_bounds__(128, 5) render_backward_kernel(RenderArgs a) {
         if (!ray_setup(cp, a.g, px, py, d, t0, t1)) continue;
         const float4 gl = reinterpret_cast<const float4*>(cp.dimg)[(long long)py * cp.W + px];
         if (gl.x == 0.0f && gl.y == 0.0f && gl.z == 0.0f && gl.w == 0.0f) continue;
-        DVRComposite<C, true, false> fw{{}, s_tf, s_scl, cp.ert}; // the sweep's arithmetic: runs, no pairs
+        // the forward pass: the sweep's arithmetic (runs, no pairs)
+        std::conditional_t<D, DVRForwardD<C>, DVRComposite<C, true, false>> fw;
+        fw.s_tf = s_tf;
+        fw.s_scl = s_scl;
+        fw.ert = cp.ert;
         if constexpr (XF)
             march_xf<C, VS, POW2>(a.g, a.pool, a.rnodes, cp, d, t0, t1, a.xf, fw);
         else
             march<C, VS, POW2, false>(a.g, a.pool, a.rnodes, cp, d, t0, t1, fw);
-        DVRAdjoint<C> bw;
+        DVRAdjoint<C, D> bw;
         bw.s_tf = s_tf;
         bw.s_scl = s_scl;
         bw.s_dtf = s_dtf;
@@ -1227,12 +1350,19 @@ __global__ void __launch_bounds__(128, 5) render_backward_kernel(RenderArgs a) {
         bw.gC[1] = gl.y;
         bw.gC[2] = gl.z;
         bw.gAf = gl.w;
-        bw.Cf[0] = fw.Cr;
-        bw.Cf[1] = fw.Cg;
-        bw.Cf[2] = fw.Cb;
-        bw.Af = fw.A;
+        if constexpr (D) {
+            bw.Cf[0] = fw.Cd[0];
+            bw.Cf[1] = fw.Cd[1];
+            bw.Cf[2] = fw.Cd[2];
+            bw.Tf = fw.Td;
+        } else {
+            bw.Cf[0] = fw.Cr;
+            bw.Cf[1] = fw.Cg;
+            bw.Cf[2] = fw.Cb;
+            bw.Tf = fw.T;
+        }
 #pragma unroll
-        for (int c = 0; c < C; ++c) bw.dsc[c] = 0.0f;
+        for (int c = 0; c < C; ++c) bw.dsc[c] = (R)0;
         bw.reset();
         if constexpr (XF)
             march_xf<C, VS, POW2>(a.g, a.pool, a.rnodes, cp, d, t0, t1, a.xf, bw);
@@ -1244,13 +1374,27 @@ __global__ void __launch_bounds__(128, 5) render_backward_kernel(RenderArgs a) {
     }
 #pragma unroll
     for (int c = 0; c < C; ++c) {
-        float v = dsc[c];
+        R v = dsc[c];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0 && v != 0.0f) atomicAdd(&a.dscale[c], v);
+        if (lane == 0 && v != (R)0) {
+            if constexpr (D) atomicAdd(&a.dacc[C * 1024 + c], v);
+            else atomicAdd(&a.dscale[c], v);
+        }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < C * 1024; i += blockDim.x)
-        if (s_dtf[i] != 0.0f) atomicAdd(&a.dtf[i], s_dtf[i]);
+        if (s_dtf[i] != (R)0) {
+            if constexpr (D) atomicAdd(&a.dacc[i], s_dtf[i]);
+            else atomicAdd(&a.dtf[i], s_dtf[i]);
+        }
+}
+
+// FP64 gradient-check mode: the double sums rounded once to the float outputs.
+__global__ void grad_convert_kernel(int C, const double* __restrict__ acc, float* __restrict__ dtf,
+                                    float* __restrict__ dscale) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < C * 1024) dtf[i] = (float)acc[i];
+    if (i < C) dscale[i] = (float)acc[C * 1024 + i];
 }
 
 // Queue order from the tile costs of an earlier frame of the same tile grid: costliest first
@@ -1468,7 +1612,7 @@ __global__ void __launch_bounds__(256, VR_RENDER_MIN_CTAS) refine_kernel(RenderA
             f.Cr = st.C[0];
             f.Cg = st.C[1];
             f.Cb = st.C[2];
-            f.A = st.A;
+            f.T = st.T;
         }
         const long long r = march<C, VS, POW2, false>(a.g, a.pool, a.rnodes, *cp, dd, r0, r1, f, &a.cache, k0);
         if (r < 0) {
@@ -1476,12 +1620,12 @@ __global__ void __launch_bounds__(256, VR_RENDER_MIN_CTAS) refine_kernel(RenderA
             st.C[0] = f.Cr;
             st.C[1] = f.Cg;
             st.C[2] = f.Cb;
-            st.A = f.A;
+            st.T = f.T;
             st.status = 1;
             my_samples += (unsigned long long)(st.k - k0);
             ++my_pending;
         } else {
-            reinterpret_cast<float4*>(cp->img)[pix] = make_float4(f.Cr, f.Cg, f.Cb, f.A);
+            reinterpret_cast<float4*>(cp->img)[pix] = make_float4(f.Cr, f.Cg, f.Cb, f.alpha());
             st.status = 2;
             my_samples += (unsigned long long)(r - k0);
         }
@@ -1594,22 +1738,30 @@ cudaError_t launch_render(const RenderArgs& a, int mode, int fp16, int blocks, i
     }
 }
 
-template <int C, int VS, bool POW2, bool XF>
+template <int C, int VS, bool POW2, bool XF, bool D>
 static void launch_bwd_one(const RenderArgs& a, int blocks, int threads, cudaStream_t st) {
-    const size_t smem = (size_t)C * 512 * sizeof(float4) + (size_t)C * 1024 * sizeof(float);
-    cudaFuncSetAttribute(render_backward_kernel<C, VS, POW2, XF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    render_backward_kernel<C, VS, POW2, XF><<<blocks, threads, smem, st>>>(a);
+    const size_t smem = (size_t)C * 512 * sizeof(float4) + (size_t)C * 1024 * (D ? sizeof(double) : sizeof(float));
+    cudaFuncSetAttribute(render_backward_kernel<C, VS, POW2, XF, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    render_backward_kernel<C, VS, POW2, XF, D><<<blocks, threads, smem, st>>>(a);
+    if (D) grad_convert_kernel<<<(C * 1024 + 255) / 256, 256, 0, st>>>(C, a.dacc, a.dtf, a.dscale);
+}
+
+template <int C, int VS, bool D>
+static void launch_bwd_d(const RenderArgs& a, int blocks, int threads, cudaStream_t st) {
+    if (a.g.pow2) {
+        if (a.has_xf) launch_bwd_one<C, VS, true, true, D>(a, blocks, threads, st);
+        else launch_bwd_one<C, VS, true, false, D>(a, blocks, threads, st);
+    } else {
+        if (a.has_xf) launch_bwd_one<C, VS, false, true, D>(a, blocks, threads, st);
+        else launch_bwd_one<C, VS, false, false, D>(a, blocks, threads, st);
+    }
 }
 
 template <int C, int VS>
 static cudaError_t launch_bwd_c(const RenderArgs& a, int blocks, int threads, cudaStream_t st) {
-    if (a.g.pow2) {
-        if (a.has_xf) launch_bwd_one<C, VS, true, true>(a, blocks, threads, st);
-        else launch_bwd_one<C, VS, true, false>(a, blocks, threads, st);
-    } else {
-        if (a.has_xf) launch_bwd_one<C, VS, false, true>(a, blocks, threads, st);
-        else launch_bwd_one<C, VS, false, false>(a, blocks, threads, st);
-    }
+    if (a.dacc) launch_bwd_d<C, VS, true>(a, blocks, threads, st);
+    else launch_bwd_d<C, VS, false>(a, blocks, threads, st);
     return cudaGetLastError();
 }
 

@@ -90,6 +90,7 @@ def lib():
         L.vr_refine_end.argtypes = [vp]
         L.vr_set_launch_shape.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.vr_set_tile_order.argtypes = [vp, ctypes.c_int]
+        L.vr_set_gradient_precision.argtypes = [vp, ctypes.c_int]
         L.vr_set_mip_segment_length.argtypes = [vp, ctypes.c_int]
         L.vr_plan_create.argtypes = [vp, ctypes.POINTER(Camera), ctypes.c_int, ctypes.POINTER(vp), ctypes.c_int,
                                      ctypes.POINTER(vp)]
@@ -98,7 +99,8 @@ def lib():
         L.vr_plan_destroy.argtypes = [vp]
         for f in ("vr_create", "vr_destroy", "vr_insert_block", "vr_insert_slice", "vr_set_transfer_functions",
                   "vr_set_clip_planes", "vr_set_channel_transforms", "vr_render", "vr_render_backward", "vr_read_level", "vr_read_voxels", "vr_read_node", "vr_render_footprint",
-                  "vr_stats", "vr_set_tile_shape", "vr_set_launch_shape", "vr_set_tile_order", "vr_set_mip_segment_length", "vr_plan_create",
+                  "vr_stats", "vr_set_tile_shape", "vr_set_launch_shape", "vr_set_tile_order", "vr_set_mip_segment_length",
+                  "vr_set_gradient_precision", "vr_plan_create",
                   "vr_plan_launch",
                   "vr_cache_update", "vr_cache_load", "vr_cache_read", "vr_refine_begin", "vr_refine_pass",
                   "vr_refine_end",
@@ -249,6 +251,10 @@ class Renderer:
     def set_mip_segment_length(self, samples):
         """MIP: samples per ray segment (0: rays marched whole; default 1024)."""
         self._check(lib().vr_set_mip_segment_length(self._ctx, samples))
+
+    def set_gradient_precision(self, fp64):
+        """render_backward accumulation: False (single precision) or True (FP64 gradient-check mode)."""
+        self._check(lib().vr_set_gradient_precision(self._ctx, 1 if fp64 else 0))
 
     def set_tile_order(self, mode):
         """0: raster tile queue; 1 (default): costliest tiles of the previous render of the same grid first."""

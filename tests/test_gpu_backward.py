@@ -1,6 +1,8 @@
 """Adjoint parity: the hand-written backward (per-ray recompute, forward-order reverse sweep)
 against the oracle's exact FP64 gradient and against central finite differences of the GPU
-forward.  Gradient tolerance: relative 1e-3."""
+forward.  Gradient tolerance: relative 1e-3, norm-wise, and element by element wherever
+|g| > 1e-6 max|g| in the FP64 gradient-check mode (vr_set_gradient_precision); the single-precision
+mode is held to 1e-3 relative plus 1e-5 max|g| per element (its sums cancel in FP32)."""
 import numpy as np
 import pytest
 
@@ -30,16 +32,36 @@ def _setup(tau=0, ert=2.0, size=40):
 ERT_MARGIN = 1e-5  # rays whose opacity passes this close to the threshold may stop a sample apart
 
 
-def _grad_close(got, ref, rel=1e-3):
-    """Norm-wise and per element: relative error <= rel wherever |g| > 1e-6 max|g|; smaller entries
-    within 1e-6 max|g|."""
+def _grad_close(got, ref, rel=1e-3, fp64=True):
+    """Norm-wise, and per element: with fp64 (the FP64 gradient-check mode) relative error <= rel
+    wherever |g| > 1e-6 max|g| and smaller entries within 1e-6 max|g|; otherwise (single-precision
+    sums) within rel |g| + 1e-5 max|g|."""
     got, ref = np.asarray(got, np.float64), np.asarray(ref, np.float64)
     scale = np.abs(ref).max()
     assert np.linalg.norm(got - ref) <= rel * np.linalg.norm(ref)
-    big = np.abs(ref) > 1e-6 * scale
     d = np.abs(got - ref)
-    assert (d[big] <= rel * np.abs(ref[big])).all(), f"max rel {np.max(d[big] / np.abs(ref[big])):.3e}"
+    if not fp64:
+        assert (d <= rel * np.abs(ref) + 1e-5 * scale).all()
+        return
+    big = np.abs(ref) > 1e-6 * scale
+    worst = np.argmax(np.where(big, d / np.maximum(np.abs(ref), 1e-300), 0.0))
+    assert (d[big] <= rel * np.abs(ref[big])).all(), \
+        f"max rel {d.flat[worst] / abs(ref.flat[worst]):.3e} at {worst}: |g| / max|g| = {abs(ref.flat[worst]) / scale:.2e}"
     assert (d[~big] <= 1e-6 * scale).all()
+
+
+def _backward_both(r, cam, tf, sc, dl, rtf, rsc):
+    """The GPU adjoint in single precision and in the FP64 gradient-check mode, against the oracle."""
+    import torch
+
+    r.set_transfer_functions(torch.from_numpy(tf), torch.from_numpy(sc))
+    for fp64 in (False, True):
+        r.set_gradient_precision(fp64)
+        dtf, dsc = r.render_backward([cam], [torch.from_numpy(dl).cuda()])
+        torch.cuda.synchronize()
+        _grad_close(dtf.cpu().numpy(), rtf, fp64=fp64)
+        _grad_close(dsc.cpu().numpy(), rsc, fp64=fp64)
+    r.set_gradient_precision(False)
 
 
 def _oracle_grad_ert(ov, cam, tf, sc, dl):
@@ -63,13 +85,9 @@ def test_backward_matches_oracle_gradient():
     sc = np.array([1.0, 0.8, 1.3], np.float32)
     rng = np.random.default_rng(0)
     dl = rng.normal(size=(cam["height"], cam["width"], 4)).astype(np.float32)
-    r.set_transfer_functions(torch.from_numpy(tf), torch.from_numpy(sc))
-    dtf, dsc = r.render_backward([cam], [torch.from_numpy(dl).cuda()])
-    torch.cuda.synchronize()
     px, py = O.image_pixels(cam["width"], cam["height"])
     rtf, rsc = O.render_grad(ov, cam, tf, sc, (px, py), dl.reshape(-1, 4).astype(np.float64))
-    _grad_close(dtf.cpu().numpy(), rtf)
-    _grad_close(dsc.cpu().numpy(), rsc)
+    _backward_both(r, cam, tf, sc, dl, rtf, rsc)
 
 
 def test_backward_with_early_termination():
@@ -85,10 +103,7 @@ def test_backward_with_early_termination():
     dl = np.random.default_rng(1).normal(size=(cam["height"], cam["width"], 4)).astype(np.float32)
     dl, rtf, rsc, excluded = _oracle_grad_ert(ov, cam, tf, sc, dl)
     print(f"ERT knife-edge rays excluded: {excluded} of {dl.shape[0] * dl.shape[1]}")
-    r.set_transfer_functions(torch.from_numpy(tf), torch.from_numpy(sc))
-    dtf, dsc = r.render_backward([cam], [torch.from_numpy(dl).cuda()])
-    _grad_close(dtf.cpu().numpy(), rtf)
-    _grad_close(dsc.cpu().numpy(), rsc)
+    _backward_both(r, cam, tf, sc, dl, rtf, rsc)
 
 
 @pytest.mark.parametrize("ert", [2.0, 0.99])
@@ -116,11 +131,7 @@ def test_backward_through_homogeneous_runs(ert):
     sc = np.array([1.0, 0.9, 1.2], np.float32)
     dl = np.random.default_rng(3).normal(size=(cam["height"], cam["width"], 4)).astype(np.float32)
     dl, rtf, rsc, _ = _oracle_grad_ert(ov, cam, tf, sc, dl)
-    r.set_transfer_functions(torch.from_numpy(tf), torch.from_numpy(sc))
-    dtf, dsc = r.render_backward([cam], [torch.from_numpy(dl).cuda()])
-    torch.cuda.synchronize()
-    _grad_close(dtf.cpu().numpy(), rtf)
-    _grad_close(dsc.cpu().numpy(), rsc)
+    _backward_both(r, cam, tf, sc, dl, rtf, rsc)
 
 
 def test_autograd_function_and_finite_differences():
