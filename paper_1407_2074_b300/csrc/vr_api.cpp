@@ -387,7 +387,7 @@ vr_status vr_create(const int64_t dims[3], int channels, int brick_size, const v
     c->ps = (PStat*)dalloc(c, sizeof(PStat) * (size_t)(cap * brick_size * channels));
     c->err = (int*)dalloc(c, sizeof(int));
     c->tf2 = (float4*)dalloc(c, sizeof(float4) * 512 * channels);
-    c->scl = (float*)dalloc(c, sizeof(float) * 4);
+    c->scl = (float*)dalloc(c, sizeof(float) * 2 * MAXC);
     c->counter = (unsigned int*)dalloc(c, sizeof(unsigned int) * 4);
     c->stats = (unsigned long long*)dalloc(c, sizeof(unsigned long long) * 4);
     if (!c->pool || !c->rn || !c->ns || !c->ps || !c->err || !c->tf2 || !c->scl || !c->counter || !c->stats) {

@@ -587,7 +587,10 @@ __global__ void prepare_tf_kernel(int C, const float* __restrict__ tf, const flo
         tf2[2 * i] = v;
         tf2[2 * i + 1] = make_float4(w.x - v.x, w.y - v.y, w.z - v.z, w.w - v.w);
     }
-    if (i < C) scl[i] = scale[i] / 65535.0f;
+    if (i < C) {
+        scl[i] = scale[i] / 65535.0f; // what the render multiplies raw intensities by
+        scl[MAXC + i] = scale[i];     // unrounded, for the double-precision gradient check
+    }
 }
 
 cudaError_t launch_prepare_tf(int C, const float* tf, const float* scale, float4* tf2, float* scl, cudaStream_t st) {

@@ -95,7 +95,7 @@ struct RenderArgs {
     const uint16_t* pool;
     const RNode* rnodes;
     const float4* tf;    // [C][256][2]: entry, next - entry
-    const float* scl;    // [C]: s / 65535
+    const float* scl;    // [MAXC] s / 65535, then [MAXC] s
     const CamParam* cams;
     int n_cams;
     long long total_tiles;

@@ -208,6 +208,16 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
             v = fmaf(fxz, (v5 - v4) - (v1 - v0), v);
             v = fmaf(fyz, (v6 - v4) - (v2 - v0), v);
             out[c] = fmaf(fxyz, ((v7 - v6) - (v5 - v4)) - ((v3 - v2) - (v1 - v0)), v);
+            if constexpr (F::kExactI) {
+                // the same polynomial in double: its coefficients are exact integers and the
+                // fractions exact floats, so this is the trilinear value to double rounding
+                const double fx = fr[0], fy = fr[1], fz = fr[2];
+                double e = (double)(v0 - VBIAS) + fx * (double)(v1 - v0);
+                e += fy * (double)(v2 - v0) + fz * (double)(v4 - v0);
+                e += fx * fy * (double)((v3 - v2) - (v1 - v0)) + fx * fz * (double)((v5 - v4) - (v1 - v0));
+                e += fy * fz * (double)((v6 - v4) - (v2 - v0));
+                f.Id[c] = e + fx * fy * fz * (double)(((v7 - v6) - (v5 - v4)) - ((v3 - v2) - (v1 - v0)));
+            }
         }
     };
     // FP16 trilinear: corners as normalised half pairs, interpolated in half2
@@ -434,6 +444,10 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
         } else {
 #pragma unroll
             for (int c = 0; c < C; ++c) I[c] = H ? __half2float(__float2half_rn(avg[c] * (1.0f / 65535.0f))) : avg[c];
+            if constexpr (F::kExactI) {
+#pragma unroll
+                for (int c = 0; c < C; ++c) f.Id[c] = (double)avg[c];
+            }
             if constexpr (F::kRuns) if (ell == dt) {
                 // A brick-less node gives every sample the same intensity: find the run of samples
                 // k..k+n-1 that stay in this node with a full segment, using the same per-sample
@@ -654,8 +668,15 @@ __device__ __forceinline__ long long march_xf(const Geo& g, const uint16_t* __re
                 r = fmaf(fr[0] * fr[2], cv[c][5], r);
                 r = fmaf(fr[1] * fr[2], cv[c][6], r);
                 I[c] = fmaf(fr[0] * fr[1] * fr[2], cv[c][7], r);
+                if constexpr (F::kExactI) {
+                    const double fx = fr[0], fy = fr[1], fz = fr[2];
+                    double e = (double)cv[c][0] + fx * (double)cv[c][1] + fy * (double)cv[c][2] + fz * (double)cv[c][4];
+                    e += fx * fy * (double)cv[c][3] + fx * fz * (double)cv[c][5] + fy * fz * (double)cv[c][6];
+                    f.Id[c] = e + fx * fy * fz * (double)cv[c][7];
+                }
             } else {
                 I[c] = avg[c];
+                if constexpr (F::kExactI) f.Id[c] = (double)avg[c];
             }
         }
         if (f.sample(I, ell)) {
@@ -669,6 +690,7 @@ __device__ __forceinline__ long long march_xf(const Geo& g, const uint16_t* __re
 struct NoHooks {
     static constexpr bool kRuns = false; // composites runs of equal samples in closed form
     static constexpr bool kPairs = false; // has sample2 (two samples shaded together)
+    static constexpr bool kExactI = false; // the march also stores the double intensity in Id[C]
     __device__ __forceinline__ void on_node(long long) {}
     __device__ __forceinline__ void on_cell(const Geo&, int, const int*, const int*) {}
 };
@@ -1038,33 +1060,69 @@ __global__ void __launch_bounds__(256, VR_RENDER_MIN_CTAS) render_kernel(RenderA
     }
 }
 
-// One constant sample's shading in double precision (the FP64 gradient-check mode): per channel
-// the opacity a_c, 1 - a_c and rgb_c from the single-precision lookup, the local colour K and
-// transmittance P_C of the sample, and ln q = sum_c l ln(1 - alpha_c) for runs.
+// Opacity correction in double precision: a = 1 - (1 - alpha)^l and its complement.
+__device__ __forceinline__ void opacity_d(double al, float ell, double& a, double& oma) {
+    if (ell == 0.5f) {
+        oma = sqrt(1.0 - al);
+        a = al / (1.0 + oma);
+    } else if (ell == 1.0f) {
+        a = al;
+        oma = 1.0 - al;
+    } else {
+        const double lg = log1p(-al);
+        a = -expm1((double)ell * lg);
+        oma = exp((double)ell * lg);
+    }
+}
+
+constexpr double ALPHA_MAX_D = 1.0 - 1e-6;
+
+// One sample's shading in double precision (the FP64 gradient-check mode): the table entry i and
+// the position lam between entries i and i + 1, the interpolated entry, the opacity correction
+// and the sample's local colour K and transmittance q = P_C, all from the exact intensity Id and
+// the unrounded intensity scale, as in the FP64 definition.  The entry is not a decision of the
+// march (the table is continuous across entries), so it is taken from the double position: with
+// the single-precision one, a position that rounds across an entry would put a gradient of
+// relative size ~1e-5 on the neighbouring entry.
 template <int C>
 struct ShadeD {
-    TFLookup<C> t[C];
-    float a[C], oma[C], al[C];
+    int i[C];
+    bool clamped[C], inside[C];
+    double lam[C], rgb[C][3], dT[C][4], al[C], a[C], oma[C];
     double P[C], R[C][3], K[3], q, lnq;
-    __device__ __forceinline__ void eval(const float4* s_tf, const float* s_scl, const float (&I)[C], float ell) {
+    __device__ __forceinline__ void eval(const float4* s_tf, const float* s_raw, const double (&Id)[C], float ell) {
         double pre = 1.0;
         K[0] = K[1] = K[2] = 0.0;
         lnq = 0.0;
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-            t[c].eval(s_tf, s_scl, c, I[c]);
-            al[c] = fminf(fmaxf(t[c].al, 0.0f), ALPHA_MAX);
-            opacity(al[c], ell, a[c], oma[c]);
+            const double xr = (double)s_raw[c] * Id[c] / 65535.0;
+            inside[c] = xr > 0.0 && xr < 1.0;
+            const double w = (xr < 0.0 ? 0.0 : (xr > 1.0 ? 1.0 : xr)) * 255.0;
+            i[c] = min((int)floor(w), 254);
+            lam[c] = w - (double)i[c];
+            const float4 T0 = s_tf[c * 256 + i[c]], T1 = s_tf[c * 256 + i[c] + 1];
+            dT[c][0] = (double)T1.x - (double)T0.x;
+            dT[c][1] = (double)T1.y - (double)T0.y;
+            dT[c][2] = (double)T1.z - (double)T0.z;
+            dT[c][3] = (double)T1.w - (double)T0.w;
+            rgb[c][0] = (double)T0.x + lam[c] * dT[c][0];
+            rgb[c][1] = (double)T0.y + lam[c] * dT[c][1];
+            rgb[c][2] = (double)T0.z + lam[c] * dT[c][2];
+            const double alr = (double)T0.w + lam[c] * dT[c][3];
+            clamped[c] = !(alr >= 0.0 && alr <= ALPHA_MAX_D);
+            al[c] = alr < 0.0 ? 0.0 : (alr > ALPHA_MAX_D ? ALPHA_MAX_D : alr);
+            opacity_d(al[c], ell, a[c], oma[c]);
             P[c] = pre;
-            const double w = pre * (double)a[c];
-            K[0] += w * (double)t[c].r;
-            K[1] += w * (double)t[c].g;
-            K[2] += w * (double)t[c].b;
+            const double wa = pre * a[c];
+            K[0] += wa * rgb[c][0];
+            K[1] += wa * rgb[c][1];
+            K[2] += wa * rgb[c][2];
             R[c][0] = K[0];
             R[c][1] = K[1];
             R[c][2] = K[2];
-            pre *= (double)oma[c];
-            lnq += (double)ell * log1p(-(double)al[c]);
+            pre *= oma[c];
+            lnq += (double)ell * log1p(-al[c]);
         }
         q = pre;
     }
@@ -1072,14 +1130,17 @@ struct ShadeD {
 
 // The adjoint's forward pass in the FP64 check mode: the single-precision march decides (the
 // same samples, runs and stop as DVRComposite), and the ray's colour and transmittance are
-// accumulated alongside in double precision for the sweep's suffix terms.
+// accumulated alongside in double precision from the double shading.
 template <int C>
 struct DVRForwardD : DVRComposite<C, true, false> {
     using B = DVRComposite<C, true, false>;
+    static constexpr bool kExactI = true;
+    const float* s_raw;
+    double Id[C];
     double Cd[3] = {0.0, 0.0, 0.0}, Td = 1.0;
     __device__ __forceinline__ bool sample(const float (&I)[C], float ell) {
         ShadeD<C> sd;
-        sd.eval(B::s_tf, B::s_scl, I, ell);
+        sd.eval(B::s_tf, s_raw, Id, ell);
 #pragma unroll
         for (int i = 0; i < 3; ++i) Cd[i] += Td * sd.K[i];
         Td *= sd.q;
@@ -1087,7 +1148,7 @@ struct DVRForwardD : DVRComposite<C, true, false> {
     }
     __device__ __forceinline__ long long run(const float (&I)[C], long long n, float ell, bool& stop) {
         ShadeD<C> sd;
-        sd.eval(B::s_tf, B::s_scl, I, ell);
+        sd.eval(B::s_tf, s_raw, Id, ell);
         const long long j = B::run(I, n, ell, stop);
         const double nj = (double)j;
         const double S = sd.lnq < 0.0 ? expm1(nj * sd.lnq) / expm1(sd.lnq) : nj;
@@ -1108,18 +1169,23 @@ struct DVRForwardD : DVRComposite<C, true, false> {
 // T_{s,c} = T_0 q^s P_c (P_c = prod_{c' < c} (1 - a_c'), q = P_C) and
 // C_(s,c)+ = C_0 + T_0 K (1 - q^s) / (1 - q) + T_0 q^s R_c (R_c = sum_{c' <= c} P_c' a_c' rgb_c',
 // K = R_{C-1}), so every term is a geometric series in q.
-// D = true (FP64 gradient-check mode): transmittance, colour, the gradient terms and their sums
-// are double precision (the decisions stay those of the single-precision forward); the
-// table-entry sums go to double shared-memory accumulators.
+// D = true (FP64 gradient-check mode): every value downstream of the sample positions -- the
+// intensity, the table interpolation, the opacity correction, transmittance, colour, the gradient
+// terms and their sums -- is double precision (ShadeD); the decisions (samples, table entries,
+// runs, the stop) stay those of the single-precision forward.  The table-entry sums go to double
+// shared-memory accumulators.
 template <int C, bool D = false>
 struct DVRAdjoint : NoHooks {
     using R = std::conditional_t<D, double, float>;
     static constexpr bool kRuns = true;
+    static constexpr bool kExactI = D;
     const float4* s_tf;
     const float* s_scl;
-    R* s_dtf; // [C][256][4]
+    const float* s_raw; // unrounded scales (D mode)
+    R* s_dtf;           // [C][256][4]
     float ert;
     R gC[3], gAf, Cf[3], Tf;
+    double Id[C]; // the sample's double intensity (D mode; set by the march)
     // the forward's single-precision state (decides the stop); in the D mode also a double copy
     float T = 1.0f, Cp[3] = {0.0f, 0.0f, 0.0f};
     R Td = 1.0, Cd[3] = {0.0, 0.0, 0.0};
@@ -1153,89 +1219,98 @@ struct DVRAdjoint : NoHooks {
 #pragma unroll
         for (int c = 0; c < C; ++c) flush(c);
     }
-    // table gradient gq (rgba) of channel c at lookup t, and the scale gradient
-    __device__ __forceinline__ void accumulate(int c, const TFLookup<C>& t, const R (&gq)[4], float I) {
-        const float4 Dv = s_tf[(C + c) * 256 + t.i];
-        const R glam = gq[0] * (R)Dv.x + gq[1] * (R)Dv.y + gq[2] * (R)Dv.z + gq[3] * (R)Dv.w;
-        if (t.i != pk[c]) {
+    // table gradient gq (rgba) of channel c at entry i, position lam, slope dT = T[i+1] - T[i], and
+    // the scale gradient (x = s I / 65535 inside (0, 1))
+    __device__ __forceinline__ void accumulate(int c, int i, R lam, const R (&dT)[4], bool inside, const R (&gq)[4],
+                                               R I) {
+        const R glam = gq[0] * dT[0] + gq[1] * dT[1] + gq[2] * dT[2] + gq[3] * dT[3];
+        if (i != pk[c]) {
             flush(c);
-            pk[c] = t.i;
+            pk[c] = i;
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             pS[c][q] += gq[q];
-            pL[c][q] += (R)t.lam * gq[q];
+            pL[c][q] += lam * gq[q];
         }
-        if (t.xr > 0.0f && t.xr < 1.0f) dsc[c] += glam * (R)255.0f * (R)I * (R)(1.0f / 65535.0f);
+        if (inside) dsc[c] += glam * (R)255.0f * I * (R)(1.0f / 65535.0f);
     }
-    // the math state: the double copy in the D mode, the forward's own otherwise
-    __device__ __forceinline__ R Tm() const {
-        if constexpr (D) return Td;
-        else return T;
-    }
-    __device__ __forceinline__ R Cm(int i) const {
-        if constexpr (D) return Cd[i];
-        else return Cp[i];
+    __device__ __forceinline__ void accumulate(int c, const TFLookup<C>& t, const R (&gq)[4], float I) {
+        const float4 Dv = s_tf[(C + c) * 256 + t.i];
+        const R dT[4] = {(R)Dv.x, (R)Dv.y, (R)Dv.z, (R)Dv.w};
+        accumulate(c, t.i, (R)t.lam, dT, t.xr > 0.0f && t.xr < 1.0f, gq, (R)I);
     }
     __device__ __forceinline__ R suffix(const R (&Cj)[3]) const {
         return -(gC[0] * (Cf[0] - Cj[0]) + gC[1] * (Cf[1] - Cj[1]) + gC[2] * (Cf[2] - Cj[2])) + gAf * Tf;
     }
-    __device__ __forceinline__ bool sample(const float (&I)[C], float ell) {
-        const R T0 = Tm();
-        const R C0[3] = {Cm(0), Cm(1), Cm(2)};
-        Shaded s{0.0f, 0.0f, 0.0f, 1.0f}; // the forward's single-precision shading
-        R P = (R)1, cs[3] = {(R)0, (R)0, (R)0};
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-            TFLookup<C> t;
-            t.eval(s_tf, s_scl, c, I[c]);
-            const bool clamped = !(t.al >= 0.0f && t.al <= ALPHA_MAX);
-            const float al = fminf(fmaxf(t.al, 0.0f), ALPHA_MAX);
-            float a, oma;
-            opacity(al, ell, a, oma);
-            const float w32 = s.q * a;
-            R Pc, Cj[3];
-            if constexpr (D) {
-                Pc = P;
-                cs[0] += P * (R)a * (R)t.r;
-                cs[1] += P * (R)a * (R)t.g;
-                cs[2] += P * (R)a * (R)t.b;
-                P *= (R)oma;
-#pragma unroll
-                for (int i = 0; i < 3; ++i) Cj[i] = C0[i] + T0 * cs[i];
-            } else {
-                Pc = s.q;
-            }
-            s.r = fmaf(w32, t.r, s.r);
-            s.g = fmaf(w32, t.g, s.g);
-            s.b = fmaf(w32, t.b, s.b);
-            s.q *= oma;
-            if constexpr (!D) {
-                Cj[0] = fmaf(T0, s.r, C0[0]);
-                Cj[1] = fmaf(T0, s.g, C0[1]);
-                Cj[2] = fmaf(T0, s.b, C0[2]);
-            }
-            const R Tc = T0 * Pc;
-            const R w = Tc * (R)a;
-            const R ga = Tc * (gC[0] * (R)t.r + gC[1] * (R)t.g + gC[2] * (R)t.b) + suffix(Cj) / (R)oma;
-            const R gq[4] = {gC[0] * w, gC[1] * w, gC[2] * w,
-                             clamped ? (R)0 : ga * (R)ell * (R)oma / (R)(1.0f - al)};
-            accumulate(c, t, gq, I[c]);
-        }
-        if constexpr (D) {
-#pragma unroll
-            for (int i = 0; i < 3; ++i) Cd[i] += Td * cs[i];
-            Td *= P;
-        }
+    // the forward's single-precision update of one sample (decides the stop)
+    __device__ __forceinline__ bool forward_update(const float (&I)[C], float ell) {
+        const DVRComposite<C, true, false> fw{{}, s_tf, s_scl, ert};
+        const Shaded s = fw.shade(I, ell);
         Cp[0] = fmaf(T, s.r, Cp[0]);
         Cp[1] = fmaf(T, s.g, Cp[1]);
         Cp[2] = fmaf(T, s.b, Cp[2]);
         T *= s.q;
         return 1.0f - T >= ert;
     }
+    __device__ __forceinline__ bool sample(const float (&I)[C], float ell) {
+        if constexpr (D) {
+            ShadeD<C> sd;
+            sd.eval(s_tf, s_raw, Id, ell);
+            const double T0 = Td;
+            const double C0[3] = {Cd[0], Cd[1], Cd[2]};
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                double Cj[3];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) Cj[i] = C0[i] + T0 * sd.R[c][i];
+                const double Tc = T0 * sd.P[c];
+                const double w = Tc * sd.a[c];
+                const double ga = Tc * (gC[0] * sd.rgb[c][0] + gC[1] * sd.rgb[c][1] + gC[2] * sd.rgb[c][2]) +
+                                  suffix(Cj) / sd.oma[c];
+                const double gq[4] = {gC[0] * w, gC[1] * w, gC[2] * w,
+                                      sd.clamped[c] ? 0.0 : ga * (double)ell * sd.oma[c] / (1.0 - sd.al[c])};
+                accumulate(c, sd.i[c], sd.lam[c], sd.dT[c], sd.inside[c], gq, Id[c]);
+            }
+#pragma unroll
+            for (int i = 0; i < 3; ++i) Cd[i] += Td * sd.K[i];
+            Td *= sd.q;
+            return forward_update(I, ell);
+        } else {
+            const float T0 = T;
+            const float C0[3] = {Cp[0], Cp[1], Cp[2]};
+            Shaded s{0.0f, 0.0f, 0.0f, 1.0f}; // the forward's single-precision shading
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                TFLookup<C> t;
+                t.eval(s_tf, s_scl, c, I[c]);
+                const bool clamped = !(t.al >= 0.0f && t.al <= ALPHA_MAX);
+                const float al = fminf(fmaxf(t.al, 0.0f), ALPHA_MAX);
+                float a, oma;
+                opacity(al, ell, a, oma);
+                const float Pc = s.q;
+                const float w32 = s.q * a;
+                s.r = fmaf(w32, t.r, s.r);
+                s.g = fmaf(w32, t.g, s.g);
+                s.b = fmaf(w32, t.b, s.b);
+                s.q *= oma;
+                const float Cj[3] = {fmaf(T0, s.r, C0[0]), fmaf(T0, s.g, C0[1]), fmaf(T0, s.b, C0[2])};
+                const float Tc = T0 * Pc;
+                const float w = Tc * a;
+                const float ga = Tc * (gC[0] * t.r + gC[1] * t.g + gC[2] * t.b) + suffix(Cj) / oma;
+                const float gq[4] = {gC[0] * w, gC[1] * w, gC[2] * w, clamped ? 0.0f : ga * ell * oma / (1.0f - al)};
+                accumulate(c, t, gq, I[c]);
+            }
+            Cp[0] = fmaf(T, s.r, Cp[0]);
+            Cp[1] = fmaf(T, s.g, Cp[1]);
+            Cp[2] = fmaf(T, s.b, Cp[2]);
+            T *= s.q;
+            return 1.0f - T >= ert;
+        }
+    }
     __device__ __forceinline__ long long run(const float (&I)[C], long long n, float ell, bool& stop) {
-        const R T0 = Tm();
-        const R C0[3] = {Cm(0), Cm(1), Cm(2)};
+        const R T0 = D ? Td : (R)T;
+        const R C0[3] = {D ? Cd[0] : (R)Cp[0], D ? Cd[1] : (R)Cp[1], D ? Cd[2] : (R)Cp[2]};
         const R alpha0 = suffix(C0); // before the run
         // the forward's single-precision closed form decides the samples used and the stop
         DVRComposite<C, true, false> fw{{}, s_tf, s_scl, ert};
@@ -1248,56 +1323,63 @@ struct DVRAdjoint : NoHooks {
         Cp[0] = fw.Cr;
         Cp[1] = fw.Cg;
         Cp[2] = fw.Cb;
-        // geometric sums over the run, in R
-        TFLookup<C> t[C];
-        float a[C], oma[C], al[C];
-        R Pw[C], Rc[C][3], K[3] = {(R)0, (R)0, (R)0}, pre = (R)1, lnq = (R)0;
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-            t[c].eval(s_tf, s_scl, c, I[c]);
-            al[c] = fminf(fmaxf(t[c].al, 0.0f), ALPHA_MAX);
-            opacity(al[c], ell, a[c], oma[c]);
-            Pw[c] = pre;
-            const R w = pre * (R)a[c];
-            K[0] += w * (R)t[c].r;
-            K[1] += w * (R)t[c].g;
-            K[2] += w * (R)t[c].b;
-            Rc[c][0] = K[0];
-            Rc[c][1] = K[1];
-            Rc[c][2] = K[2];
-            pre *= (R)oma[c];
-            if constexpr (D) lnq += (R)ell * log1p(-(R)al[c]);
-            else lnq += ell * log1pf(-al[c]);
-        }
         const R nj = (R)j;
-        R Sg, em1;
         if constexpr (D) {
-            em1 = expm1(lnq);
-            Sg = lnq < 0.0 ? expm1(nj * lnq) / em1 : nj; // sum_{s<j} q^s
-        } else {
-            em1 = expm1f(lnq);
-            Sg = lnq < 0.0f ? expm1f(nj * lnq) / em1 : nj;
-        }
-        const R beta = lnq < (R)0 ? T0 * (gC[0] * K[0] + gC[1] * K[1] + gC[2] * K[2]) / -em1 : (R)0;
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-            const R gamma = T0 * (gC[0] * Rc[c][0] + gC[1] * Rc[c][1] + gC[2] * Rc[c][2]);
-            const R ga = T0 * Pw[c] * (gC[0] * (R)t[c].r + gC[1] * (R)t[c].g + gC[2] * (R)t[c].b) * Sg +
-                         (alpha0 * nj + beta * (nj - Sg) + gamma * Sg) / (R)oma[c];
-            const R wsum = T0 * Pw[c] * (R)a[c] * Sg;
-            const bool clamped = !(t[c].al >= 0.0f && t[c].al <= ALPHA_MAX);
-            const R gq[4] = {gC[0] * wsum, gC[1] * wsum, gC[2] * wsum,
-                             clamped ? (R)0 : ga * (R)ell * (R)oma[c] / (R)(1.0f - al[c])};
-            accumulate(c, t[c], gq, I[c]);
-        }
-        if constexpr (D) {
-            // the same double closed form as DVRForwardD::run
+            // geometric sums over the run from the double shading of the (exact) AVG intensity
             ShadeD<C> sd;
-            sd.eval(s_tf, s_scl, I, ell);
-            const double S = sd.lnq < 0.0 ? expm1((double)j * sd.lnq) / expm1(sd.lnq) : (double)j;
+            sd.eval(s_tf, s_raw, Id, ell);
+            const double em1 = expm1(sd.lnq);
+            const double Sg = sd.lnq < 0.0 ? expm1(nj * sd.lnq) / em1 : nj; // sum_{s<j} q^s
+            const double beta = sd.lnq < 0.0 ? T0 * (gC[0] * sd.K[0] + gC[1] * sd.K[1] + gC[2] * sd.K[2]) / -em1 : 0.0;
 #pragma unroll
-            for (int i = 0; i < 3; ++i) Cd[i] += Td * sd.K[i] * S;
-            Td *= exp((double)j * sd.lnq);
+            for (int c = 0; c < C; ++c) {
+                const double gamma = T0 * (gC[0] * sd.R[c][0] + gC[1] * sd.R[c][1] + gC[2] * sd.R[c][2]);
+                const double ga =
+                    T0 * sd.P[c] * (gC[0] * sd.rgb[c][0] + gC[1] * sd.rgb[c][1] + gC[2] * sd.rgb[c][2]) * Sg +
+                    (alpha0 * nj + beta * (nj - Sg) + gamma * Sg) / sd.oma[c];
+                const double wsum = T0 * sd.P[c] * sd.a[c] * Sg;
+                const double gq[4] = {gC[0] * wsum, gC[1] * wsum, gC[2] * wsum,
+                                      sd.clamped[c] ? 0.0 : ga * (double)ell * sd.oma[c] / (1.0 - sd.al[c])};
+                accumulate(c, sd.i[c], sd.lam[c], sd.dT[c], sd.inside[c], gq, Id[c]);
+            }
+#pragma unroll
+            for (int i = 0; i < 3; ++i) Cd[i] += Td * sd.K[i] * Sg;
+            Td *= exp(nj * sd.lnq);
+        } else {
+            // geometric sums over the run, in single precision
+            TFLookup<C> t[C];
+            float a[C], oma[C], al[C];
+            float Pw[C], Rc[C][3], K[3] = {0.0f, 0.0f, 0.0f}, pre = 1.0f, lnq = 0.0f;
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                t[c].eval(s_tf, s_scl, c, I[c]);
+                al[c] = fminf(fmaxf(t[c].al, 0.0f), ALPHA_MAX);
+                opacity(al[c], ell, a[c], oma[c]);
+                Pw[c] = pre;
+                const float w = pre * a[c];
+                K[0] += w * t[c].r;
+                K[1] += w * t[c].g;
+                K[2] += w * t[c].b;
+                Rc[c][0] = K[0];
+                Rc[c][1] = K[1];
+                Rc[c][2] = K[2];
+                pre *= oma[c];
+                lnq += ell * log1pf(-al[c]);
+            }
+            const float em1 = expm1f(lnq);
+            const float Sg = lnq < 0.0f ? expm1f(nj * lnq) / em1 : nj;
+            const float beta = lnq < 0.0f ? T0 * (gC[0] * K[0] + gC[1] * K[1] + gC[2] * K[2]) / -em1 : 0.0f;
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const float gamma = T0 * (gC[0] * Rc[c][0] + gC[1] * Rc[c][1] + gC[2] * Rc[c][2]);
+                const float ga = T0 * Pw[c] * (gC[0] * t[c].r + gC[1] * t[c].g + gC[2] * t[c].b) * Sg +
+                                 (alpha0 * nj + beta * (nj - Sg) + gamma * Sg) / oma[c];
+                const float wsum = T0 * Pw[c] * a[c] * Sg;
+                const bool clamped = !(t[c].al >= 0.0f && t[c].al <= ALPHA_MAX);
+                const float gq[4] = {gC[0] * wsum, gC[1] * wsum, gC[2] * wsum,
+                                     clamped ? 0.0f : ga * ell * oma[c] / (1.0f - al[c])};
+                accumulate(c, t[c], gq, I[c]);
+            }
         }
         return j;
     }
@@ -1310,8 +1392,10 @@ __global__ void __launch_bounds__(128, 5) render_backward_kernel(RenderArgs a) {
     using R = std::conditional_t<D, double, float>;
     extern __shared__ float4 s_tf[];
     __shared__ float s_scl[MAXC];
+    __shared__ float s_raw[MAXC];
     R* s_dtf = reinterpret_cast<R*>(s_tf + C * 512);
     for (int i = threadIdx.x; i < C * 1024; i += blockDim.x) s_dtf[i] = (R)0;
+    if (threadIdx.x < C) s_raw[threadIdx.x] = a.scl[MAXC + threadIdx.x];
     load_tables(a, C, s_tf, s_scl);
     const int lane = threadIdx.x & 31;
     R dsc[C];
@@ -1337,6 +1421,7 @@ __global__ void __launch_bounds__(128, 5) render_backward_kernel(RenderArgs a) {
         fw.s_tf = s_tf;
         fw.s_scl = s_scl;
         fw.ert = cp.ert;
+        if constexpr (D) fw.s_raw = s_raw;
         if constexpr (XF)
             march_xf<C, VS, POW2>(a.g, a.pool, a.rnodes, cp, d, t0, t1, a.xf, fw);
         else
@@ -1344,6 +1429,7 @@ __global__ void __launch_bounds__(128, 5) render_backward_kernel(RenderArgs a) {
         DVRAdjoint<C, D> bw;
         bw.s_tf = s_tf;
         bw.s_scl = s_scl;
+        bw.s_raw = s_raw;
         bw.s_dtf = s_dtf;
         bw.ert = cp.ert;
         bw.gC[0] = gl.x;

@@ -29,7 +29,11 @@ def _setup(tau=0, ert=2.0, size=40):
     return w, vol, r, cam
 
 
-ERT_MARGIN = 1e-5  # rays whose opacity passes this close to the threshold may stop a sample apart
+# Rays whose opacity passes this close to the threshold may stop a sample apart: the stop is decided
+# by the single-precision forward, whose opacity differs from the double one by up to ~1e-4 on the
+# near-opaque tables below (1 - alpha of a few 1e-4 loses most of its bits in single precision).
+# The same band as the early-termination band of the image check.
+ERT_MARGIN = 2e-4
 
 
 def _grad_close(got, ref, rel=1e-3, fp64=True):
@@ -92,7 +96,7 @@ def test_backward_matches_oracle_gradient():
 
 def test_backward_with_early_termination():
     """ERT on (most rays stop): per element against the oracle, the rays whose opacity passes within
-    1e-5 of the threshold (a stop one sample apart is correct there) excluded on both sides."""
+    ERT_MARGIN of the threshold (a stop one sample apart is correct there) excluded on both sides."""
     import torch
 
     w, vol, r, cam = _setup(ert=0.99)
