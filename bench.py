@@ -549,8 +549,9 @@ def main():
         samples_of[f] = st_.last_render_samples
         rays_of[f] = st_.last_render_rays
     # per-kernel launch count per step: level updates (N + 1) + the two tile-order kernels (every
-    # timed render follows a render of the same tile grid) + the render kernel
-    launches_per_step = r.levels + 3
+    # timed render follows a render of the same tile grid) + the render kernel + the continuation
+    # kernel that finishes the rays still marching when the tile queue runs dry
+    launches_per_step = r.levels + 4
 
     def step(i, host=False, image_free=None):
         z0, b = blocks[i % len(blocks)]
@@ -693,7 +694,8 @@ def main():
     ins_bytes = insert_algorithmic_bytes(w.dims, 3, SLICES_PER_STEP, levels)
     achieved = U / (render_ms / 1000.0) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "render_kernel<3,4,DVR>", "algorithmic_bytes_per_launch": U,
+            "traffic": None, "kernel": "render_kernel<3,4,DVR> + render_tail_kernel<3,4> (one vr_render)",
+            "algorithmic_bytes_per_launch": U,
             "peak_kind": peak_kind, "algorithmic_bytes_frames": len(fp),
             "distinct_voxels_per_level_first_frame": vox, "distinct_nodes_first_frame": nodes}
     # DRAM traffic, L2 traffic and executed instructions of the same kernel from one small ncu

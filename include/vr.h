@@ -102,6 +102,8 @@ typedef struct {
     int64_t pool_bytes, node_table_bytes;
     int64_t last_render_samples;      /* samples composited by the last vr_render (all cameras) */
     int64_t last_render_rays;         /* rays with a non-empty interval */
+    int64_t last_render_continued;    /* rays of the last vr_render finished by its second launch
+                                         (vr_set_ray_continuation) */
 } vr_stats_t;
 
 /* Create a context for a volume of final resolution dims (X, Y, Z), channels 1..4 and brick
@@ -311,6 +313,22 @@ vr_status vr_set_mip_segment_length(vr_ctx* ctx, int samples);
  * same in either order.  MIP stays in raster order (its rays all run to the end; the cost order
  * measured slower there).  Not part of the paper's method. */
 vr_status vr_set_tile_order(vr_ctx* ctx, int mode);
+
+/* Ray continuation of vr_render (DVR, FP32 or FP16, reading the store directly with no
+ * per-channel transforms).  Early ray termination makes ray lengths very uneven: once the ray-tile
+ * queue has run dry, the rest of a frame is a tail in which a few warps march the longest rays
+ * while the others idle.  With continuation on, a lane whose ray still has more than
+ * min_samples_left segment lengths to go at that point (checked every 16 steps) records the ray's
+ * state -- the next sample, transmittance and colour -- and a second launch resumes each recorded
+ * ray with lanes_per_ray lanes in lockstep: lane j shades samples k + j, and every lane of the group
+ * composites the step's shaded samples in order (the composite is split into a per-sample shading
+ * and an in-order ray update; runs of equal samples through brick-less nodes start at the same
+ * samples).  Images and sample counts are those of one lane per ray, bit for bit.  The buffers
+ * (32 bytes per thread of the render grid) are allocated through the context's allocator on first
+ * use.  lanes_per_ray: 0 (off) or 1, 2, 4, 8, 16, 32; min_samples_left >= 0; VR_ERR_INVALID_ARG
+ * otherwise.  Defaults 16 and 32.  Not part of the paper's method: a work decomposition of the ray
+ * loop of Algorithm 1. */
+vr_status vr_set_ray_continuation(vr_ctx* ctx, int lanes_per_ray, int min_samples_left);
 
 /* Ray-tile shape of the render queue: each warp renders tile_w x tile_h pixels (tile_w * tile_h
  * must be 32).  Default 8 x 4.  Chosen per workload by the autotuner of the Python package. */

@@ -71,6 +71,13 @@ struct vr_ctx {
     int threads = 256, ctas_per_sm = 8; // render launch shape (autotuned per workload)
     // tile queue order from the previous render of the same tile grid (costliest tiles first)
     int tile_order_mode = 1;
+    // ray continuation (plain DVR): once the queue runs dry, rays with more than cont_min samples
+    // left are finished by a second launch with 2^cont_lg lanes per ray (cont_lg < 0: off)
+    int cont_lg = 4;
+    int cont_min = 32;
+    RayCont* cont = nullptr;
+    unsigned int* cont_ctl = nullptr;
+    long long cont_cap = 0;
     int kseg_mip = 1024; // MIP: samples per ray segment (0: rays marched whole)
     SegBuf seg;
     unsigned int* lpt_cost = nullptr;
@@ -79,6 +86,7 @@ struct vr_ctx {
     long long lpt_cap = 0;
     unsigned long long lpt_sig = 0;
     bool lpt_have = false;
+    bool last_cont = false;       // the last vr_render continued rays (their number in cont_ctl[1])
     // out-of-core render cache (cache_cap slots; 0 = renders read the store directly)
     long long cache_cap = 0;
     uint16_t* cache = nullptr;
@@ -181,6 +189,26 @@ static vr_status order_prepare(vr_ctx* c, RenderArgs& a, const CamParam* cams, i
     return VR_OK;
 }
 
+// Ray continuation buffers for a render grid of `lanes` threads (each lane records at most one ray).
+static vr_status cont_prepare(vr_ctx* c, RenderArgs& a, long long lanes, cudaStream_t st) {
+    if (c->cont_lg < 0) return VR_OK;
+    if (lanes > c->cont_cap) {
+        CK(c, cudaDeviceSynchronize()); // the old buffers may still be in use (any stream)
+        dfree(c, c->cont);
+        c->cont_cap = 0;
+        c->cont = (RayCont*)dalloc(c, sizeof(RayCont) * (size_t)lanes);
+        if (!c->cont_ctl) c->cont_ctl = (unsigned int*)dalloc(c, sizeof(unsigned int) * 4);
+        if (!c->cont || !c->cont_ctl) return fail(c, VR_ERR_OUT_OF_MEMORY, "ray continuation buffers");
+        c->cont_cap = lanes;
+    }
+    CK(c, cudaMemsetAsync(c->cont_ctl, 0, sizeof(unsigned int) * 4, st));
+    a.cont = c->cont;
+    a.cont_ctl = c->cont_ctl;
+    a.cont_min = c->cont_min;
+    a.cont_lg = c->cont_lg;
+    return VR_OK;
+}
+
 static void seg_free(vr_ctx* c, SegBuf& b) {
     dfree(c, b.v);
     dfree(c, b.meta);
@@ -233,6 +261,8 @@ static void destroy_all(vr_ctx* c) {
     dfree(c, c->lpt_cost);
     dfree(c, c->lpt_order);
     dfree(c, c->lpt_aux);
+    dfree(c, c->cont);
+    dfree(c, c->cont_ctl);
     if (c->store_host) {
         if (c->pool) cudaFreeHost(c->pool);
     } else {
@@ -742,16 +772,23 @@ vr_status vr_render(vr_ctx* c, const vr_camera* cams, int n, float* const* image
     CK(c, cudaMemsetAsync(c->counter, 0, sizeof(unsigned long long), st));
     CK(c, cudaMemsetAsync(c->stats, 0, 2 * sizeof(unsigned long long), st));
     RenderArgs a = make_args(c, n, tiles);
+    const int blocks = grid_for(c, tiles, c->threads, c->ctas_per_sm);
+    const bool cont = mode == VR_MODE_DVR && !a.has_xf && !a.cache.cslot && c->cont_lg >= 0;
     if (mode == VR_MODE_DVR) { // whole-ray, per-channel-transform and render-cache passes alike
         s = order_prepare(c, a, c->h_cams, n, tiles, st);
+        if (s != VR_OK) return s;
+    }
+    if (cont) {
+        s = cont_prepare(c, a, (long long)blocks * c->threads, st);
         if (s != VR_OK) return s;
     }
     if (mode == VR_MODE_MIP) {
         s = seg_prepare(c, c->seg, a, c->h_cams, n, tiles, st);
         if (s != VR_OK) return s;
     }
-    CK(c, launch_render(a, mode, fp16 && mode == VR_MODE_DVR, grid_for(c, tiles, c->threads, c->ctas_per_sm),
-                        c->threads, st));
+    CK(c, launch_render(a, mode, fp16 && mode == VR_MODE_DVR, blocks, c->threads, st));
+    if (cont) CK(c, launch_render_tail(a, fp16, blocks, c->threads, st));
+    c->last_cont = cont;
     return VR_OK;
 }
 
@@ -1130,6 +1167,12 @@ vr_status vr_stats(vr_ctx* c, vr_stats_t* out) {
         return cuda_fail(c, cudaGetLastError(), "stats");
     out->last_render_samples = (int64_t)h[0];
     out->last_render_rays = (int64_t)h[1];
+    if (c->last_cont) {
+        unsigned n = 0;
+        if (cudaMemcpy(&n, c->cont_ctl + 1, sizeof n, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return cuda_fail(c, cudaGetLastError(), "stats");
+        out->last_render_continued = n;
+    }
     return VR_OK;
 }
 
@@ -1161,6 +1204,17 @@ vr_status vr_set_tile_order(vr_ctx* c, int mode) {
     if (!c || (mode != 0 && mode != 1)) return VR_ERR_INVALID_ARG;
     c->tile_order_mode = mode;
     c->lpt_have = false;
+    return VR_OK;
+}
+
+vr_status vr_set_ray_continuation(vr_ctx* c, int lanes_per_ray, int min_samples_left) {
+    if (!c) return VR_ERR_INVALID_ARG;
+    int lg = 0;
+    while (lg <= 5 && (1 << lg) != lanes_per_ray) ++lg;
+    if (lanes_per_ray != 0 && lg > 5) return fail(c, VR_ERR_INVALID_ARG, "ray continuation: 0 or 1..32 lanes (a power of two)");
+    if (min_samples_left < 0) return fail(c, VR_ERR_INVALID_ARG, "ray continuation: min_samples_left < 0");
+    c->cont_lg = lanes_per_ray == 0 ? -1 : lg;
+    c->cont_min = min_samples_left;
     return VR_OK;
 }
 

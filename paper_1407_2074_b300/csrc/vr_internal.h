@@ -90,6 +90,11 @@ struct RefineState { // one pixel of a refinement session
     int pad[2];
 };
 
+struct RayCont { // a DVR ray stopped at sample k with transmittance T and colour C, to be resumed
+    int ci, px, py, k;
+    float T, Cr, Cg, Cb;
+};
+
 struct RenderArgs {
     Geo g;
     const uint16_t* pool;
@@ -115,6 +120,12 @@ struct RenderArgs {
     unsigned int* seg_meta;             // [nseg][total_tiles][32] samples << 2 | 2 when the ray goes on
     unsigned int* seg_done;             // [nseg][total_tiles] 0 pending, 1 done, 3 done and rays go on
     const unsigned int* tile_order;     // queue position -> tile (nullptr: raster order)
+    // Ray continuation (plain DVR): once the tile queue runs dry, a lane whose ray has more than
+    // cont_min samples left stops, records its state in cont[] and a second launch finishes it
+    // with 2^cont_lg lanes per ray.  cont_ctl: [0] queue dry, [1] records, [2] records taken.
+    RayCont* cont;                      // nullptr: rays are marched to their end in one launch
+    unsigned int* cont_ctl;
+    int cont_min, cont_lg;
     unsigned int* tile_cost;            // per tile: SM clock cycles / 64 it took (nullptr: not kept)
     float* dtf;                         // backward: [C][256][4]
     float* dscale;                      // backward: [C]
@@ -136,6 +147,8 @@ cudaError_t launch_read_voxels(const Geo& g, int L, const uint16_t* pool, const 
 cudaError_t launch_prepare_tf(int C, const float* tf, const float* scale, float4* tf2, float* scl, cudaStream_t st);
 cudaError_t launch_render(const RenderArgs& a, int mode, int fp16, int blocks, int threads, cudaStream_t st);
 cudaError_t launch_render_backward(const RenderArgs& a, int blocks, int threads, cudaStream_t st);
+// the second launch of a continued DVR render: the recorded rays, 2^a.cont_lg lanes each
+cudaError_t launch_render_tail(const RenderArgs& a, int fp16, int blocks, int threads, cudaStream_t st);
 cudaError_t launch_tile_order(const unsigned int* cost, long long tiles, unsigned int* aux, unsigned int* order,
                               cudaStream_t st);
 cudaError_t launch_cache_gather(const uint16_t* store, uint16_t* cache, const int2* list, int n, long long slot_elems,

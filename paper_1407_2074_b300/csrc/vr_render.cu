@@ -125,64 +125,189 @@ struct TFLookup {
     }
 };
 
-// Marches one ray; calls f.sample(I[C], ell) for every sample until it returns true.
-// H = false: I in raw uint16 units, FP32 interpolation.  H = true: the eight corners are cached as
-// normalised FP16 channel pairs (value / 65535), interpolated in half2; I is that FP16 result.
-// With a render cache (ca != nullptr) a node's brick is read from the cache when resident;
-// otherwise it is requested and, in a full-frame pass, the brick of the parent or grandparent on
-// the descent path stands in when resident (nearest first; missing ones are requested too), else
-// the node's AVG (Sec. "Full-Frame Ray-Casting").  In a refinement pass (ca->refine) the ray
-// stops at its first missing brick instead and march returns -(k + 1), k the sample to resume
-// from (Sec. "Refinement Ray-Casting").  k0 is the first sample index.
-template <int C, int VS, bool POW2, bool H, class F>
-__device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restrict__ pool,
-                                           const RNode* __restrict__ rn, const CamParam& cp, const float d[3], float t0,
-                                           float t1, F& f, const CacheArgs* ca = nullptr, int k0 = 0,
-                                           int kend = MAX_SAMPLES) {
-    // samples k0 <= k < min(kend, MAX_SAMPLES) inside [t0, t1)
-    const float dt = cp.dt;
-    const int klim = kend < MAX_SAMPLES ? kend : MAX_SAMPLES;
-    const float eye[3] = {cp.eye[0], cp.eye[1], cp.eye[2]}; // in registers: cp lives in global memory
-    const int N = g.N, M = g.M, S = g.S;
-    const int mlog = __ffs(M) - 1; // log2(M) when POW2
+// Emission-absorption compositing runs in two steps (DVRComposite below): a sample is shaded on
+// its own over the channels into its local colour rgb_s and transmittance q_s, and then composited
+// into the ray, C += T rgb_s, T *= q_s.  Only the second step depends on the ray's state.
+struct Shaded {
+    float r, g, b, q;
+};
+
+__device__ __forceinline__ Shaded shfl_shaded(unsigned mask, const Shaded& s, int src) {
+    return Shaded{__shfl_sync(mask, s.r, src), __shfl_sync(mask, s.g, src), __shfl_sync(mask, s.b, src),
+                  __shfl_sync(mask, s.q, src)};
+}
+
+// Traversal state of one ray, shared by the one-lane march and the lane-group march: the level of
+// detail L* of the current sample and the cached node -- its level, grid index, the faces of its
+// box the ray heads for, and its brick slot or AVG.  Sample positions, L* and the node choice use
+// only correctly rounded single-precision operations in a fixed order.
+template <int C, int VS, bool POW2>
+struct RayCursor {
+    const Geo& g;
+    const uint16_t* __restrict__ pool;
+    const RNode* __restrict__ rn;
+    const float* tl; // the camera's LOD thresholds (global memory)
+    float eye[3], d[3];
+    int N, M, S, mlog;
     int Lstar = 0;
-    float tnext = cp.tl[1 <= N ? 1 : N + 1];
-    if (N < 1) tnext = CUDART_INF_F;
+    float tnext;
     // node cache
     int nlev = -1;
-    float tl_limit = 0.0f; // t at which L* would exceed the cached node's level
+    float tl_limit = 0.0f;   // t at which L* would exceed the cached node's level
     float bnd[3] = {0, 0, 0}; // the node-box face each axis is heading for (+-inf at the grid ends)
-    const bool neg[3] = {!(d[0] > 0.0f), !(d[1] > 0.0f), !(d[2] > 0.0f)};
+    bool neg[3];
     int cidx[3] = {0, 0, 0};
     bool brick = false;
     const uint16_t* sbase = nullptr;
     float avg[C];
     float off[3] = {0, 0, 0};
     float inv_vox = 1.0f;
-    constexpr int CP = (C + 1) / 2;
+
+    __device__ __forceinline__ RayCursor(const Geo& g_, const uint16_t* pool_, const RNode* rn_, const CamParam& cp,
+                                         const float dd[3])
+        : g(g_), pool(pool_), rn(rn_), tl(cp.tl) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            eye[a] = cp.eye[a]; // in registers: cp lives in global memory
+            d[a] = dd[a];
+            neg[a] = !(dd[a] > 0.0f);
+        }
+        N = g.N;
+        M = g.M;
+        S = g.S;
+        mlog = __ffs(M) - 1; // log2(M) when POW2
+        tnext = N >= 1 ? cp.tl[1] : CUDART_INF_F;
+    }
+    __device__ __forceinline__ void position(float tk, float (&p)[3]) const {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) p[a] = __fadd_rn(eye[a], __fmul_rn(tk, d[a]));
+    }
+    // L* = the largest L with tk >= t_L (t grows along the ray, so L* only rises)
+    __device__ __forceinline__ void advance_lod(float tk) {
+        while (tk >= tnext) {
+            ++Lstar;
+            tnext = (Lstar < N) ? tl[Lstar + 1] : CUDART_INF_F;
+        }
+    }
+    // p inside the cached node's box.  With power-of-two node sizes positions move monotonically
+    // along each axis, so only the face the ray is heading for can be crossed: (p < hi) for d > 0,
+    // (p >= lo) otherwise.
+    __device__ __forceinline__ bool in_box(const float (&p)[3]) const {
+        bool in = true;
+        if (POW2) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) in = in && ((p[a] < bnd[a]) != neg[a]);
+        } else {
+            const float size = (float)(M << nlev);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                int q = (int)floorf(__fdiv_rn(p[a], size));
+                const int qm = (int)g.nb[nlev][a] - 1;
+                q = q < 0 ? 0 : (q > qm ? qm : q);
+                in = in && (q == cidx[a]);
+            }
+        }
+        return in;
+    }
+    // the cached node is the one a descent would give for the sample at tk, p
+    __device__ __forceinline__ bool holds(float tk, const float (&p)[3]) const {
+        return nlev >= 0 && tk < tl_limit && in_box(p);
+    }
+    __device__ __forceinline__ long long node_id(int lev, const int (&idx)[3]) const {
+        return g.noff[lev] + ((long long)idx[2] * g.nb[lev][1] + idx[1]) * g.nb[lev][0] + idx[0];
+    }
+    // getNodeAtPosition: descend from the root towards L*, stopping at a node without children,
+    // and cache the node.  With power-of-two node sizes the descent restarts at the lowest
+    // ancestor of the cached node whose box holds p (at level L* or above): every ancestor has
+    // children, and from there the descent visits exactly the nodes the root descent would.
+    template <class F>
+    __device__ __forceinline__ void descend(const float (&p)[3], F& f) {
+        int lev = N;
+        int idx[3] = {0, 0, 0};
+        if (POW2 && nlev >= 0) {
+            for (int A = nlev + 1 > Lstar ? nlev + 1 : Lstar; A < N; ++A) {
+                const int sh = A - nlev;
+                const float inv = pow2_neg(mlog + A);
+                bool in = true;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) in = in && ((int)floorf(__fmul_rn(p[a], inv)) == (cidx[a] >> sh));
+                if (in) {
+                    lev = A;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) idx[a] = cidx[a] >> sh;
+                    break;
+                }
+            }
+        }
+        const long long nid0 = node_id(lev, idx);
+        RNode nd = rn[nid0];
+        f.on_node(nid0);
+        while (lev > Lstar && (nd.flags & F_CHILDREN)) {
+            --lev;
+            const float size = (float)(M << lev);
+            const float inv = POW2 ? pow2_neg(mlog + lev) : 0.0f;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const float qf = POW2 ? floorf(__fmul_rn(p[a], inv)) : floorf(__fdiv_rn(p[a], size));
+                const int c0 = 2 * idx[a];
+                int q = qf < (float)c0 ? c0 : (qf > (float)(c0 + 1) ? c0 + 1 : (int)qf);
+                const int qm = (int)g.nb[lev][a] - 1;
+                if (q > qm) q = qm;
+                idx[a] = q;
+            }
+            const long long nid = node_id(lev, idx);
+            nd = rn[nid];
+            f.on_node(nid);
+        }
+        nlev = lev;
+        tl_limit = (lev < N) ? tl[lev + 1] : CUDART_INF_F;
+        const float size = (float)(M << lev);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            cidx[a] = idx[a];
+            if (d[a] > 0.0f)
+                bnd[a] = (idx[a] == (int)g.nb[lev][a] - 1) ? CUDART_INF_F : (float)(idx[a] + 1) * size;
+            else
+                bnd[a] = (idx[a] == 0) ? -CUDART_INF_F : (float)idx[a] * size;
+            off[a] = (float)(idx[a] * M) - 0.5f;
+        }
+        inv_vox = pow2_neg(lev);
+        brick = (nd.flags & F_BRICK) && nd.slot >= 0 && nd.slot < g.n_slots_cap;
+        sbase = brick ? pool + (long long)nd.slot * g.slot_elems : nullptr;
+#pragma unroll
+        for (int c = 0; c < C; ++c) avg[c] = (float)nd.avg[c];
+    }
+    // cell of position pp in the cached brick: corner index i0 (clamped into the slot) and fractions
+    __device__ __forceinline__ const uint16_t* cell(const float (&pp)[3], float (&fr)[3], int (&i0)[3]) const {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float u = fmaf(pp[a], inv_vox, -off[a]); // == (p * 2^-L) - off: the product is exact
+            const float fl = floorf(u);
+            const int ii = (int)fl;
+            fr[a] = __fsub_rn(u, fl);
+            i0[a] = ii < 0 ? 0 : (ii > M ? M : ii);
+        }
+        return sbase + ((i0[2] * S + i0[1]) * S + i0[0]) * VS;
+    }
+    __device__ __forceinline__ const uint16_t* corner(const uint16_t* cp0, int q) const {
+        return cp0 + ((long long)(((q >> 2) & 1) * S + ((q >> 1) & 1)) * S + (q & 1)) * VS;
+    }
     // FP32 trilinear at position pp inside the cached node's brick.  The eight corners of the cell
     // are re-read at every sample (L1 hits): a per-lane cell cache made the reload a branch that
     // some lane of the warp takes at almost every sample (lanes enter new cells at different
     // samples), which cost more than the loads it saved.  Corners are 2^23 + value (biased()), so
     // the polynomial coefficients are exact differences and only the constant term drops 2^23:
     //   I = k0 + kx fx + ky fy + kz fz + kxy fx fy + kxz fx fz + kyz fy fz + kxyz fx fy fz
-    auto trilinear = [&](const float (&pp)[3], float (&out)[C]) {
+    template <class F>
+    __device__ __forceinline__ void trilinear(const float (&pp)[3], float (&out)[C], F& f) const {
         float fr[3];
         int i0[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const float u = fmaf(pp[a], inv_vox, -off[a]);
-            const float fl = floorf(u);
-            int ii = (int)fl;
-            fr[a] = __fsub_rn(u, fl);
-            i0[a] = ii < 0 ? 0 : (ii > M ? M : ii);
-        }
-        const uint16_t* cp0 = sbase + ((i0[2] * S + i0[1]) * S + i0[0]) * VS;
+        const uint16_t* cp0 = cell(pp, fr, i0);
         f.on_cell(g, nlev, cidx, i0);
         float w[8][C];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-            const uint16_t* v = cp0 + ((long long)(((q >> 2) & 1) * S + ((q >> 1) & 1)) * S + (q & 1)) * VS;
+            const uint16_t* v = corner(cp0, q);
             if (VS == 4) {
                 const uint2 x = __ldg(reinterpret_cast<const uint2*>(v));
                 const uint32_t ws[2] = {x.x, x.y};
@@ -219,25 +344,19 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
                 f.Id[c] = e + fx * fy * fz * (double)(((v7 - v6) - (v5 - v4)) - ((v3 - v2) - (v1 - v0)));
             }
         }
-    };
+    }
     // FP16 trilinear: corners as normalised half pairs, interpolated in half2
-    auto trilinear_h = [&](const float (&pp)[3], float (&out)[C]) {
+    template <class F>
+    __device__ __forceinline__ void trilinear_h(const float (&pp)[3], float (&out)[C], F& f) const {
+        constexpr int CP = (C + 1) / 2;
         float fr[3];
         int i0[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const float u = fmaf(pp[a], inv_vox, -off[a]); // == (p * 2^-L) - off: the product is exact
-            const float fl = floorf(u);
-            int ii = (int)fl;
-            fr[a] = __fsub_rn(u, fl);
-            i0[a] = ii < 0 ? 0 : (ii > M ? M : ii);
-        }
-        const uint16_t* cp0 = sbase + ((i0[2] * S + i0[1]) * S + i0[0]) * VS;
+        const uint16_t* cp0 = cell(pp, fr, i0);
         f.on_cell(g, nlev, cidx, i0);
         __half2 hv[8][CP];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-            const uint16_t* v = cp0 + ((long long)(((q >> 2) & 1) * S + ((q >> 1) & 1)) * S + (q & 1)) * VS;
+            const uint16_t* v = corner(cp0, q);
             float cv[C];
             if (VS == 4) {
                 const uint2 w = __ldg(reinterpret_cast<const uint2*>(v));
@@ -269,134 +388,147 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
             out[2 * j] = r.x;
             if (2 * j + 1 < C) out[2 * j + 1] = r.y;
         }
-    };
+    }
+    // sample intensity inside a brick node: FP32 or (H) FP16 interpolation
+    template <bool H, class F>
+    __device__ __forceinline__ void interpolate(const float (&pp)[3], float (&out)[C], F& f) const {
+        if constexpr (H)
+            trilinear_h(pp, out, f);
+        else
+            trilinear(pp, out, f);
+    }
+    // intensity of a brick-less node: its AVG (normalised and rounded to FP16 when H)
+    template <bool H, class F>
+    __device__ __forceinline__ void average(float (&out)[C], F& f) const {
+#pragma unroll
+        for (int c = 0; c < C; ++c) out[c] = H ? __half2float(__float2half_rn(avg[c] * (1.0f / 65535.0f))) : avg[c];
+        if constexpr (F::kExactI) {
+#pragma unroll
+            for (int c = 0; c < C; ++c) f.Id[c] = (double)avg[c];
+        }
+    }
+    // sample kk has a full segment and lies in the cached node at the same level
+    __device__ __forceinline__ bool in_run(int kk, float t0, float t1, float dt, int klim) const {
+        if (kk >= klim) return false;
+        const float t = __fadd_rn(t0, __fmul_rn((float)kk, dt));
+        if (!(t < t1) || !(t < tl_limit) || !(__fsub_rn(t1, t) >= dt)) return false;
+        float p[3];
+        position(t, p);
+        if (POW2) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                if ((p[a] < bnd[a]) == neg[a]) return false;
+            return true;
+        }
+        return in_box(p);
+    }
+    // A brick-less node gives every sample the same intensity: the number n >= 1 of samples
+    // k, k+1, ... (sample k, at tk, in the node with a full segment) that stay in the node with a
+    // full segment, found with the same per-sample single-precision tests (monotone in k).
+    __device__ __forceinline__ int run_length(int k, float tk, float t0, float t1, float dt, int klim) const {
+        // estimate of the last sample in the node (fast divisions: the exact per-sample tests decide)
+        float te = fminf(tl_limit, t1 - dt);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (d[a] != 0.0f) te = fminf(te, __fdividef(bnd[a] - eye[a], d[a]));
+        }
+        const float steps = floorf(__fdividef(te - tk, dt));
+        const int ke = k + (steps > 0.0f ? (int)fminf(steps, 16777216.0f) : 0);
+        int aa = k, bb;
+        if (ke > k && in_run(ke, t0, t1, dt, klim)) {
+            aa = ke;
+            int st = 1;
+            bb = ke + 1;
+            while (in_run(bb, t0, t1, dt, klim)) {
+                aa = bb;
+                st *= 2;
+                bb = aa + st;
+            }
+        } else {
+            bb = ke > k ? ke : k + 1;
+        }
+        while (bb - aa > 1) {
+            const int m = aa + (bb - aa) / 2;
+            if (in_run(m, t0, t1, dt, klim))
+                aa = m;
+            else
+                bb = m;
+        }
+        return aa - k + 1;
+    }
+};
+
+// Marches one ray; calls f.sample(I[C], ell) for every sample until it returns true.
+// H = false: I in raw uint16 units, FP32 interpolation.  H = true: the eight corners are cached as
+// normalised FP16 channel pairs (value / 65535), interpolated in half2; I is that FP16 result.
+// With a render cache (ca != nullptr) a node's brick is read from the cache when resident;
+// otherwise it is requested and, in a full-frame pass, the brick of the parent or grandparent on
+// the descent path stands in when resident (nearest first; missing ones are requested too), else
+// the node's AVG (Sec. "Full-Frame Ray-Casting").  In a refinement pass (ca->refine) the ray
+// stops at its first missing brick instead and march returns -(k + 1), k the sample to resume
+// from (Sec. "Refinement Ray-Casting").  k0 is the first sample index.  With dry != nullptr the
+// march also stops, returning -(k + 1), once *dry is set (checked every 16 steps) and more than
+// min_left segment lengths of the ray remain: f then holds the state before sample k.
+template <int C, int VS, bool POW2, bool H, class F>
+__device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restrict__ pool,
+                                           const RNode* __restrict__ rn, const CamParam& cp, const float d[3], float t0,
+                                           float t1, F& f, const CacheArgs* ca = nullptr, int k0 = 0,
+                                           int kend = MAX_SAMPLES, const unsigned* dry = nullptr, int min_left = 0) {
+    // samples k0 <= k < min(kend, MAX_SAMPLES) inside [t0, t1)
+    const float dt = cp.dt;
+    const int klim = kend < MAX_SAMPLES ? kend : MAX_SAMPLES;
+    RayCursor<C, VS, POW2> cur(g, pool, rn, cp, d);
+    const int N = cur.N, M = cur.M;
     int k = k0;
     float kf = (float)k0; // == (float)k, exact below 2^24
+    unsigned steps = 0;
     for (;; ++k, kf += 1.0f) {
         const float tk = __fadd_rn(t0, __fmul_rn(kf, dt));
         if (!(tk < t1) || k >= klim) break;
+        if (dry && (++steps & 15u) == 0u && *(volatile const unsigned*)dry != 0u &&
+            __fsub_rn(t1, tk) > (float)min_left * dt)
+            return -(long long)(k + 1);
         const float ell = fminf(dt, __fsub_rn(t1, tk));
         float p[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) p[a] = __fadd_rn(eye[a], __fmul_rn(tk, d[a]));
-        while (tk >= tnext) {
-            ++Lstar;
-            tnext = (Lstar < N) ? cp.tl[Lstar + 1] : CUDART_INF_F;
-        }
-        bool valid = nlev >= 0 && tk < tl_limit;
-        if (valid) {
-            if (POW2) {
-                // positions move monotonically along each axis, so only the face the ray is heading
-                // for can be crossed: (p < hi) for d > 0, (p >= lo) otherwise
-#pragma unroll
-                for (int a = 0; a < 3; ++a) valid = valid && ((p[a] < bnd[a]) != neg[a]);
-            } else {
-                const float size = (float)(M << nlev);
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    int q = (int)floorf(__fdiv_rn(p[a], size));
-                    const int qm = (int)g.nb[nlev][a] - 1;
-                    q = q < 0 ? 0 : (q > qm ? qm : q);
-                    valid = valid && (q == cidx[a]);
-                }
-            }
-        }
-        if (!valid) {
-            // getNodeAtPosition: descend from the root towards L*.  With power-of-two node sizes
-            // the descent restarts at the lowest ancestor of the cached node whose box holds p
-            // (at level L* or above): every ancestor has children, and from there the descent
-            // visits exactly the nodes the root descent would.
-            int lev = N;
-            int idx[3] = {0, 0, 0};
-            if (POW2 && nlev >= 0) {
-                for (int A = nlev + 1 > Lstar ? nlev + 1 : Lstar; A < N; ++A) {
-                    const int sh = A - nlev;
-                    const float inv = pow2_neg(mlog + A);
-                    bool in = true;
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) in = in && ((int)floorf(__fmul_rn(p[a], inv)) == (cidx[a] >> sh));
-                    if (in) {
-                        lev = A;
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) idx[a] = cidx[a] >> sh;
-                        break;
-                    }
-                }
-            }
-            const long long nid0 = g.noff[lev] + ((long long)idx[2] * g.nb[lev][1] + idx[1]) * g.nb[lev][0] + idx[0];
-            RNode nd = rn[nid0];
-            f.on_node(nid0);
-            while (lev > Lstar && (nd.flags & F_CHILDREN)) {
-                --lev;
-                const float size = (float)(M << lev);
-                const float inv = POW2 ? pow2_neg(mlog + lev) : 0.0f;
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    const float qf = POW2 ? floorf(__fmul_rn(p[a], inv)) : floorf(__fdiv_rn(p[a], size));
-                    const int c0 = 2 * idx[a];
-                    int q = qf < (float)c0 ? c0 : (qf > (float)(c0 + 1) ? c0 + 1 : (int)qf);
-                    const int qm = (int)g.nb[lev][a] - 1;
-                    if (q > qm) q = qm;
-                    idx[a] = q;
-                }
-                const long long nid = g.noff[lev] + ((long long)idx[2] * g.nb[lev][1] + idx[1]) * g.nb[lev][0] + idx[0];
-                nd = rn[nid];
-                f.on_node(nid);
-            }
-            nlev = lev;
-            tl_limit = (lev < N) ? cp.tl[lev + 1] : CUDART_INF_F;
-            const float size = (float)(M << lev);
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                cidx[a] = idx[a];
-                if (d[a] > 0.0f)
-                    bnd[a] = (idx[a] == (int)g.nb[lev][a] - 1) ? CUDART_INF_F : (float)(idx[a] + 1) * size;
-                else
-                    bnd[a] = (idx[a] == 0) ? -CUDART_INF_F : (float)idx[a] * size;
-                off[a] = (float)(idx[a] * M) - 0.5f;
-            }
-            inv_vox = pow2_neg(lev);
-            brick = (nd.flags & F_BRICK) && nd.slot >= 0 && nd.slot < g.n_slots_cap;
-            sbase = brick ? pool + (long long)nd.slot * g.slot_elems : nullptr;
-#pragma unroll
-            for (int c = 0; c < C; ++c) avg[c] = (float)nd.avg[c];
-            if (ca && brick) {
-                const long long nid = g.noff[lev] + ((long long)idx[2] * g.nb[lev][1] + idx[1]) * g.nb[lev][0] + idx[0];
+        cur.position(tk, p);
+        cur.advance_lod(tk);
+        if (!cur.holds(tk, p)) {
+            cur.descend(p, f);
+            if (ca && cur.brick) {
+                const int lev = cur.nlev;
+                const long long nid = cur.node_id(lev, cur.cidx);
                 const int cs = ca->cslot[nid];
                 if (cs >= 0) {
                     ca->used[nid] = 1;
-                    sbase = ca->cache + (long long)cs * g.slot_elems;
+                    cur.sbase = ca->cache + (long long)cs * g.slot_elems;
                 } else {
                     ca->req[nid] = 1;
                     if (ca->refine) return -(long long)(k + 1);
-                    brick = false;
-                    sbase = nullptr;
+                    cur.brick = false;
+                    cur.sbase = nullptr;
                     for (int up = 1; up <= 2 && lev + up <= N; ++up) {
                         const int L2 = lev + up;
-                        const int i2[3] = {idx[0] >> up, idx[1] >> up, idx[2] >> up};
-                        const long long n2 = g.noff[L2] + ((long long)i2[2] * g.nb[L2][1] + i2[1]) * g.nb[L2][0] + i2[0];
+                        const int i2[3] = {cur.cidx[0] >> up, cur.cidx[1] >> up, cur.cidx[2] >> up};
+                        const long long n2 = cur.node_id(L2, i2);
                         if (!(rn[n2].flags & F_BRICK)) continue;
                         const int c2 = ca->cslot[n2];
                         if (c2 < 0) {
                             ca->req[n2] = 1;
-                        } else if (!brick) {
-                            brick = true;
+                        } else if (!cur.brick) {
+                            cur.brick = true;
                             ca->used[n2] = 1;
-                            sbase = ca->cache + (long long)c2 * g.slot_elems;
+                            cur.sbase = ca->cache + (long long)c2 * g.slot_elems;
 #pragma unroll
-                            for (int a = 0; a < 3; ++a) off[a] = (float)(i2[a] * M) - 0.5f;
-                            inv_vox = pow2_neg(L2);
+                            for (int a = 0; a < 3; ++a) cur.off[a] = (float)(i2[a] * M) - 0.5f;
+                            cur.inv_vox = pow2_neg(L2);
                         }
                     }
                 }
             }
         }
         float I[C];
-        if (brick) {
-            if constexpr (H)
-                trilinear_h(p, I);
-            else
-                trilinear(p, I);
+        if (cur.brick) {
+            cur.template interpolate<H>(p, I, f);
             if constexpr (F::kPairs) {
                 // the next sample too when it lies in the same brick node at the same level with a
                 // full segment: both are shaded before the two are composited in order, so the
@@ -404,30 +536,12 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
                 if (ell == dt && k + 1 < klim) {
                     const float kf2 = kf + 1.0f;
                     const float tk2 = __fadd_rn(t0, __fmul_rn(kf2, dt));
-                    if (tk2 < t1 && __fsub_rn(t1, tk2) >= dt && tk2 < tnext && tk2 < tl_limit) {
+                    if (tk2 < t1 && __fsub_rn(t1, tk2) >= dt && tk2 < cur.tnext && tk2 < cur.tl_limit) {
                         float p2[3];
-                        bool in = true;
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) p2[a] = __fadd_rn(eye[a], __fmul_rn(tk2, d[a]));
-                        if (POW2) {
-#pragma unroll
-                            for (int a = 0; a < 3; ++a) in = in && ((p2[a] < bnd[a]) != neg[a]);
-                        } else {
-                            const float size = (float)(M << nlev);
-#pragma unroll
-                            for (int a = 0; a < 3; ++a) {
-                                int q = (int)floorf(__fdiv_rn(p2[a], size));
-                                const int qm = (int)g.nb[nlev][a] - 1;
-                                q = q < 0 ? 0 : (q > qm ? qm : q);
-                                in = in && (q == cidx[a]);
-                            }
-                        }
-                        if (in) {
+                        cur.position(tk2, p2);
+                        if (cur.in_box(p2)) {
                             float I2[C];
-                            if constexpr (H)
-                                trilinear_h(p2, I2);
-                            else
-                                trilinear(p2, I2);
+                            cur.template interpolate<H>(p2, I2, f);
                             const int st = f.sample2(I, I2, dt);
                             ++k;
                             if (st == 1) break;
@@ -442,62 +556,10 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
                 }
             }
         } else {
-#pragma unroll
-            for (int c = 0; c < C; ++c) I[c] = H ? __half2float(__float2half_rn(avg[c] * (1.0f / 65535.0f))) : avg[c];
-            if constexpr (F::kExactI) {
-#pragma unroll
-                for (int c = 0; c < C; ++c) f.Id[c] = (double)avg[c];
-            }
+            cur.template average<H>(I, f);
             if constexpr (F::kRuns) if (ell == dt) {
-                // A brick-less node gives every sample the same intensity: find the run of samples
-                // k..k+n-1 that stay in this node with a full segment, using the same per-sample
-                // single-precision tests as above (monotone in k), and composite it in one step.
-                auto in_run = [&](int kk) -> bool {
-                    if (kk >= klim) return false;
-                    const float t = __fadd_rn(t0, __fmul_rn((float)kk, dt));
-                    if (!(t < t1) || !(t < tl_limit) || !(__fsub_rn(t1, t) >= dt)) return false;
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        const float pa = __fadd_rn(eye[a], __fmul_rn(t, d[a]));
-                        if (POW2) {
-                            if ((pa < bnd[a]) == neg[a]) return false;
-                        } else {
-                            int q = (int)floorf(__fdiv_rn(pa, (float)(M << nlev)));
-                            const int qm = (int)g.nb[nlev][a] - 1;
-                            q = q < 0 ? 0 : (q > qm ? qm : q);
-                            if (q != cidx[a]) return false;
-                        }
-                    }
-                    return true;
-                };
-                // estimate of the last sample in the node (fast divisions: the exact per-sample
-                // tests below decide)
-                float te = fminf(tl_limit, t1 - dt);
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    if (d[a] != 0.0f) te = fminf(te, __fdividef(bnd[a] - eye[a], d[a]));
-                }
-                const float steps = floorf(__fdividef(te - tk, dt));
-                int ke = k + (steps > 0.0f ? (int)fminf(steps, 16777216.0f) : 0);
-                int aa = k, bb;
-                if (ke > k && in_run(ke)) {
-                    aa = ke;
-                    int st = 1;
-                    bb = ke + 1;
-                    while (in_run(bb)) {
-                        aa = bb;
-                        st *= 2;
-                        bb = aa + st;
-                    }
-                } else {
-                    bb = ke > k ? ke : k + 1;
-                }
-                while (bb - aa > 1) {
-                    const int m = aa + (bb - aa) / 2;
-                    if (in_run(m)) aa = m;
-                    else bb = m;
-                }
-                const int n = aa - k + 1;
+                // composite the run of equal samples through this brick-less node in one step
+                const int n = cur.run_length(k, tk, t0, t1, dt, klim);
                 if (n >= 2) {
                     bool stop = false;
                     const int used = (int)f.run(I, n, dt, stop);
@@ -517,6 +579,84 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
         }
     }
     return k;
+}
+
+// Lane-group march (DVR): the 2^lg lanes of one group march one ray together, lane j shading
+// samples k + j of each step in lockstep; every lane of the group then composites the shaded
+// samples in order from shuffles (the second step of the two-step composite), so the group ends
+// each step with the same ray state in every lane and stops at the same sample.  A step ends at the
+// group's first sample in a brick-less node with a full segment: as in the one-lane march, that
+// sample starts a run of equal samples, which its lane composites in closed form and shares.  The
+// samples composited, the runs and the stop are those of march(), so the image is bit for bit the
+// one-lane image.  gmask: the group's lanes; gbase: its first lane; j: this lane's place in it;
+// k0: the first sample (f holds the ray state before it).
+template <int C, int VS, bool POW2, bool H, class F>
+__device__ __forceinline__ long long march_group(const Geo& g, const uint16_t* __restrict__ pool,
+                                                 const RNode* __restrict__ rn, const CamParam& cp, const float d[3],
+                                                 float t0, float t1, F& f, int lg, unsigned gmask, int gbase, int j,
+                                                 int k0) {
+    const float dt = cp.dt;
+    const int G = 1 << lg;
+    const unsigned gbits = gmask >> gbase; // the group's lanes as bits 0 .. G-1
+    RayCursor<C, VS, POW2> cur(g, pool, rn, cp, d);
+    int k = k0;
+    for (;;) {
+        const int kk = k + j;
+        const float tk = __fadd_rn(t0, __fmul_rn((float)kk, dt));
+        const bool act = tk < t1 && kk < MAX_SAMPLES;
+        bool starts_run = false;
+        Shaded s{0.0f, 0.0f, 0.0f, 1.0f};
+        float I[C];
+        float ell = dt;
+        if (act) {
+            ell = fminf(dt, __fsub_rn(t1, tk));
+            float p[3];
+            cur.position(tk, p);
+            cur.advance_lod(tk);
+            if (!cur.holds(tk, p)) cur.descend(p, f);
+            if (cur.brick) {
+                cur.template interpolate<H>(p, I, f);
+                s = f.shade(I, ell);
+            } else {
+                cur.template average<H>(I, f);
+                if (F::kRuns && ell == dt)
+                    starts_run = true;
+                else
+                    s = f.shade(I, ell);
+            }
+        }
+        const unsigned run_bits = (__ballot_sync(gmask, starts_run) >> gbase) & gbits;
+        const unsigned end_bits = (__ballot_sync(gmask, !act) >> gbase) & gbits;
+        const int jr = run_bits ? __ffs(run_bits) - 1 : G; // first sample that starts a run
+        const int je = end_bits ? __ffs(end_bits) - 1 : G; // first sample past the ray's end
+        const int jl = jr < je ? jr : je;
+        for (int q = 0; q < jl; ++q) {
+            if (f.update(shfl_shaded(gmask, s, gbase + q))) return k + q + 1;
+        }
+        if (jl == G) {
+            k += G;
+            continue;
+        }
+        if (je < jr) return k + je;
+        // sample k + jr starts a run: its lane finds the run's length and composites it
+        k += jr;
+        int used = 0;
+        bool stop = false;
+        if (j == jr) {
+            const int n = cur.run_length(kk, tk, t0, t1, dt, MAX_SAMPLES);
+            if (n >= 2) {
+                used = (int)f.run(I, n, dt, stop);
+            } else {
+                stop = f.sample(I, ell);
+                used = 1;
+            }
+        }
+        f.bcast(gmask, gbase + jr);
+        used = __shfl_sync(gmask, used, gbase + jr);
+        stop = __shfl_sync(gmask, (int)stop, gbase + jr) != 0;
+        k += used;
+        if (stop) return k;
+    }
 }
 
 // March with a per-channel affine sample transform (Sec. "Correction of Chromatic Aberration"):
@@ -728,15 +868,6 @@ __device__ __forceinline__ long long composite_run(float lnq, const float K[3], 
 // stops once 1 - T >= ert.  Only the second step depends on the ray's state, so samples shaded by
 // different lanes and composited in order by each of them give the same bits as one lane marching
 // alone, in single steps, in pairs or in any grouping.
-struct Shaded {
-    float r, g, b, q;
-};
-
-__device__ __forceinline__ Shaded shfl_shaded(unsigned mask, const Shaded& s, int src) {
-    return Shaded{__shfl_sync(mask, s.r, src), __shfl_sync(mask, s.g, src), __shfl_sync(mask, s.b, src),
-                  __shfl_sync(mask, s.q, src)};
-}
-
 template <int C, bool RUNS = true, bool PAIRS = RUNS>
 struct DVRComposite : NoHooks {
     static constexpr bool kRuns = RUNS;
@@ -793,6 +924,13 @@ struct DVRComposite : NoHooks {
     }
     __device__ __forceinline__ bool sample(const float (&I)[C], float ell) { return update(shade(I, ell)); }
     __device__ __forceinline__ float alpha() const { return 1.0f - T; }
+    // the ray state of lane src to the lanes of mask (lane-group march)
+    __device__ __forceinline__ void bcast(unsigned mask, int src) {
+        T = __shfl_sync(mask, T, src);
+        Cr = __shfl_sync(mask, Cr, src);
+        Cg = __shfl_sync(mask, Cg, src);
+        Cb = __shfl_sync(mask, Cb, src);
+    }
 };
 
 // FP16 variant of the DVR functor: I is the FP16-interpolated normalised intensity; the
@@ -864,6 +1002,13 @@ struct DVRCompositeH : NoHooks {
     }
     __device__ __forceinline__ bool sample(const float (&I)[C], float ell) { return update(shade(I, ell)); }
     __device__ __forceinline__ float alpha() const { return 1.0f - T; }
+    // the ray state of lane src to the lanes of mask (lane-group march)
+    __device__ __forceinline__ void bcast(unsigned mask, int src) {
+        T = __shfl_sync(mask, T, src);
+        Cr = __shfl_sync(mask, Cr, src);
+        Cg = __shfl_sync(mask, Cg, src);
+        Cb = __shfl_sync(mask, Cb, src);
+    }
 };
 
 // DVR that also records the distinct (level, voxel) pairs read by trilinear corners and the
@@ -949,14 +1094,13 @@ __device__ __forceinline__ void load_tables(const RenderArgs& a, int C, float4* 
 #define VR_RENDER_MIN_CTAS 3 // resident 256-thread CTAs per SM the register budget is sized for
 #endif
 
-template <int C, int VS, int MODE, bool POW2, bool H, bool XF = false, bool CACHE = false>
-__global__ void __launch_bounds__(256, VR_RENDER_MIN_CTAS) render_kernel(RenderArgs a) {
-    extern __shared__ float4 s_tf[];
-    __shared__ float s_scl[MAXC];
-    __shared__ __half s_sh[MAXC];
-    HalfEntry* s_tfh = reinterpret_cast<HalfEntry*>(s_tf + C * 512);
+// The tables of the forward kernels: FP32 entries and differences, and with H their half
+// copies (entry, difference) after them and the half scales.
+template <int C, bool H>
+__device__ __forceinline__ void load_render_tables(const RenderArgs& a, float4* s_tf, float* s_scl, __half* s_sh) {
     load_tables(a, C, s_tf, s_scl);
     if (H) {
+        HalfEntry* s_tfh = reinterpret_cast<HalfEntry*>(s_tf + C * 512);
         for (int i = threadIdx.x; i < C * 256; i += blockDim.x) {
             const float4 T = s_tf[i], D = s_tf[C * 256 + i];
             HalfEntry e;
@@ -969,6 +1113,15 @@ __global__ void __launch_bounds__(256, VR_RENDER_MIN_CTAS) render_kernel(RenderA
         if (threadIdx.x < C) s_sh[threadIdx.x] = __float2half_rn(s_scl[threadIdx.x] * 65535.0f);
         __syncthreads();
     }
+}
+
+template <int C, int VS, int MODE, bool POW2, bool H, bool XF = false, bool CACHE = false>
+__global__ void __launch_bounds__(256, VR_RENDER_MIN_CTAS) render_kernel(RenderArgs a) {
+    extern __shared__ float4 s_tf[];
+    __shared__ float s_scl[MAXC];
+    __shared__ __half s_sh[MAXC];
+    HalfEntry* s_tfh = reinterpret_cast<HalfEntry*>(s_tf + C * 512);
+    load_render_tables<C, H>(a, s_tf, s_scl, s_sh);
     // Warp tiles: a warp takes one tile_w x tile_h pixel tile at a time and its lanes march their
     // rays in lockstep.  Neighbouring rays at the same depth read the same cache lines; refilling
     // lanes with new rays as soon as theirs end (tried) loses that coherence and is ~3.6x slower.
@@ -978,6 +1131,11 @@ __global__ void __launch_bounds__(256, VR_RENDER_MIN_CTAS) render_kernel(RenderA
     const int lane = threadIdx.x & 31;
     unsigned long long* counter = reinterpret_cast<unsigned long long*>(a.counter);
     unsigned long long my_samples = 0, my_rays = 0;
+    // Ray continuation (plain DVR, a.cont set): the first warp to find the queue empty raises the
+    // dry flag; from then on, lanes whose rays still have far to go stop and record their state
+    // for the second launch (render_tail_kernel), which marches each of them with a lane group.
+    constexpr bool CONT = MODE == 0 && !XF && !CACHE;
+    const unsigned* dry = (CONT && a.cont) ? a.cont_ctl : nullptr;
     // per-tile cost (optional): lane 0 notes the tile and the SM clock when it takes a tile and
     // stores the difference when it takes the next one (the warp has converged there)
     __shared__ unsigned s_ct_tile[8];
@@ -992,7 +1150,10 @@ __global__ void __launch_bounds__(256, VR_RENDER_MIN_CTAS) render_kernel(RenderA
             const long long cyc = (clock64() - s_ct_clk[wib]) >> 6;
             a.tile_cost[s_ct_tile[wib]] = cyc < 0xffffffffLL ? (unsigned)cyc : 0xffffffffu;
         }
-        if ((long long)tile >= a.total_tiles) break;
+        if ((long long)tile >= a.total_tiles) {
+            if (dry && lane == 0 && *(volatile const unsigned*)dry == 0u) *(volatile unsigned*)a.cont_ctl = 1u;
+            break;
+        }
         if (a.tile_order) tile = a.tile_order[tile];
         if (a.tile_cost && lane == 0) {
             s_ct_tile[wib] = (unsigned)tile;
@@ -1023,10 +1184,20 @@ __global__ void __launch_bounds__(256, VR_RENDER_MIN_CTAS) render_kernel(RenderA
                 f = DVRComposite<C>{{}, s_tf, s_scl, cp->ert};
             }
             long long n;
-            if constexpr (XF)
+            if constexpr (XF) {
                 n = march_xf<C, VS, POW2>(a.g, a.pool, a.rnodes, *cp, dd, r0, r1, a.xf, f);
-            else
+            } else if constexpr (CONT) {
+                n = march<C, VS, POW2, H>(a.g, a.pool, a.rnodes, *cp, dd, r0, r1, f, nullptr, 0, MAX_SAMPLES, dry,
+                                          a.cont_min);
+                if (n < 0) { // stopped at sample -n - 1: record the ray for the second launch
+                    const unsigned slot = atomicAdd(&a.cont_ctl[1], 1u);
+                    my_samples += (unsigned long long)(-n - 1);
+                    a.cont[slot] = RayCont{ci, px, py, (int)(-n - 1), f.T, f.Cr, f.Cg, f.Cb};
+                    continue; // the pixel is written by the second launch
+                }
+            } else {
                 n = march<C, VS, POW2, H>(a.g, a.pool, a.rnodes, *cp, dd, r0, r1, f, CACHE ? &a.cache : nullptr);
+            }
             my_samples += (unsigned long long)n;
             if constexpr (MODE == 1) {
                 if (n > 0) {
@@ -1058,6 +1229,57 @@ __global__ void __launch_bounds__(256, VR_RENDER_MIN_CTAS) render_kernel(RenderA
         atomicAdd(&a.stats[0], my_samples);
         atomicAdd(&a.stats[1], my_rays);
     }
+}
+
+// Second launch of a continued DVR render: every ray recorded by render_kernel once the tile queue
+// ran dry is resumed at its recorded sample and state and marched to its end by a group of
+// 2^a.cont_lg lanes (march_group), which then writes its pixel.  The first launch was latency-bound
+// by then -- few warps left, each with long rays -- and a lane group advances a ray by up to
+// 2^cont_lg samples per step; the samples composited, and so the pixel, are those of one lane.
+template <int C, int VS, bool POW2, bool H>
+__global__ void __launch_bounds__(256, VR_RENDER_MIN_CTAS) render_tail_kernel(RenderArgs a) {
+    extern __shared__ float4 s_tf[];
+    __shared__ float s_scl[MAXC];
+    __shared__ __half s_sh[MAXC];
+    const HalfEntry* s_tfh = reinterpret_cast<const HalfEntry*>(s_tf + C * 512);
+    load_render_tables<C, H>(a, s_tf, s_scl, s_sh);
+    using F = std::conditional_t<H, DVRCompositeH<C>, DVRComposite<C>>;
+    const int lane = threadIdx.x & 31;
+    const int lg = a.cont_lg, per = 32 >> lg;
+    const int j = lane & ((1 << lg) - 1), gbase = lane - j;
+    const unsigned gmask = lg == 5 ? 0xffffffffu : (((1u << (1 << lg)) - 1u) << gbase);
+    const unsigned n_cont = a.cont_ctl[1];
+    unsigned long long my_samples = 0;
+    for (;;) {
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(&a.cont_ctl[2], (unsigned)per);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= n_cont) break;
+        const unsigned gi = base + (unsigned)(lane >> lg);
+        if (gi >= n_cont) continue; // the whole group
+        const RayCont rc = a.cont[gi];
+        const CamParam* cp = &a.cams[rc.ci];
+        float dd[3], r0, r1;
+        ray_setup(*cp, a.g, rc.px, rc.py, dd, r0, r1); // the recorded ray: a non-empty interval
+        F f;
+        if constexpr (H)
+            f = DVRCompositeH<C>{{}, s_tfh, s_sh, cp->ert};
+        else
+            f = DVRComposite<C>{{}, s_tf, s_scl, cp->ert};
+        f.T = rc.T;
+        f.Cr = rc.Cr;
+        f.Cg = rc.Cg;
+        f.Cb = rc.Cb;
+        const long long n =
+            march_group<C, VS, POW2, H>(a.g, a.pool, a.rnodes, *cp, dd, r0, r1, f, lg, gmask, gbase, j, rc.k);
+        if (j == 0) {
+            my_samples += (unsigned long long)(n - rc.k);
+            reinterpret_cast<float4*>(cp->img)[(long long)rc.py * cp->W + rc.px] =
+                make_float4(f.Cr, f.Cg, f.Cb, f.alpha());
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) my_samples += __shfl_xor_sync(0xffffffffu, my_samples, o);
+    if (lane == 0 && a.stats) atomicAdd(&a.stats[0], my_samples);
 }
 
 // Opacity correction in double precision: a = 1 - (1 - alpha)^l and its complement.
@@ -1813,6 +2035,35 @@ static cudaError_t launch_fwd_c(const RenderArgs& a, int mode, int fp16, int blo
         else launch_one<C, VS, 1, false, false>(a, blocks, threads, st);
     }
     return cudaGetLastError();
+}
+
+template <int C, int VS, bool POW2, bool H>
+static void launch_tail_one(const RenderArgs& a, int blocks, int threads, cudaStream_t st) {
+    const size_t smem = (size_t)C * 512 * sizeof(float4) + (H ? (size_t)C * 256 * sizeof(HalfEntry) : 0);
+    cudaFuncSetAttribute(render_tail_kernel<C, VS, POW2, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    render_tail_kernel<C, VS, POW2, H><<<blocks, threads, smem, st>>>(a);
+}
+
+template <int C, int VS>
+static cudaError_t launch_tail_c(const RenderArgs& a, int fp16, int blocks, int threads, cudaStream_t st) {
+    if (a.g.pow2) {
+        if (fp16) launch_tail_one<C, VS, true, true>(a, blocks, threads, st);
+        else launch_tail_one<C, VS, true, false>(a, blocks, threads, st);
+    } else {
+        if (fp16) launch_tail_one<C, VS, false, true>(a, blocks, threads, st);
+        else launch_tail_one<C, VS, false, false>(a, blocks, threads, st);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_render_tail(const RenderArgs& a, int fp16, int blocks, int threads, cudaStream_t st) {
+    if (!a.cont || a.cont_lg < 0 || a.cont_lg > 5) return cudaErrorInvalidValue;
+    switch (a.g.C) {
+        case 1: return launch_tail_c<1, 1>(a, fp16, blocks, threads, st);
+        case 2: return launch_tail_c<2, 2>(a, fp16, blocks, threads, st);
+        case 3: return launch_tail_c<3, 4>(a, fp16, blocks, threads, st);
+        default: return launch_tail_c<4, 4>(a, fp16, blocks, threads, st);
+    }
 }
 
 cudaError_t launch_render(const RenderArgs& a, int mode, int fp16, int blocks, int threads, cudaStream_t st) {

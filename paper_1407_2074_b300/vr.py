@@ -49,7 +49,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("dims", ctypes.c_int64 * 3), ("channels", ctypes.c_int), ("brick_size", ctypes.c_int),
                 ("levels", ctypes.c_int), ("nodes", ctypes.c_int64), ("slots_capacity", ctypes.c_int64),
                 ("slots_used", ctypes.c_int64), ("pool_bytes", ctypes.c_int64), ("node_table_bytes", ctypes.c_int64),
-                ("last_render_samples", ctypes.c_int64), ("last_render_rays", ctypes.c_int64)]
+                ("last_render_samples", ctypes.c_int64), ("last_render_rays", ctypes.c_int64),
+                ("last_render_continued", ctypes.c_int64)]
 
 
 _lib = None
@@ -90,6 +91,7 @@ def lib():
         L.vr_refine_end.argtypes = [vp]
         L.vr_set_launch_shape.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.vr_set_tile_order.argtypes = [vp, ctypes.c_int]
+        L.vr_set_ray_continuation.argtypes = [vp, ctypes.c_int, ctypes.c_int]
         L.vr_set_gradient_precision.argtypes = [vp, ctypes.c_int]
         L.vr_set_mip_segment_length.argtypes = [vp, ctypes.c_int]
         L.vr_plan_create.argtypes = [vp, ctypes.POINTER(Camera), ctypes.c_int, ctypes.POINTER(vp), ctypes.c_int,
@@ -99,7 +101,7 @@ def lib():
         L.vr_plan_destroy.argtypes = [vp]
         for f in ("vr_create", "vr_destroy", "vr_insert_block", "vr_insert_slice", "vr_set_transfer_functions",
                   "vr_set_clip_planes", "vr_set_channel_transforms", "vr_render", "vr_render_backward", "vr_read_level", "vr_read_voxels", "vr_read_node", "vr_render_footprint",
-                  "vr_stats", "vr_set_tile_shape", "vr_set_launch_shape", "vr_set_tile_order", "vr_set_mip_segment_length",
+                  "vr_stats", "vr_set_tile_shape", "vr_set_launch_shape", "vr_set_tile_order", "vr_set_ray_continuation", "vr_set_mip_segment_length",
                   "vr_set_gradient_precision", "vr_plan_create",
                   "vr_plan_launch",
                   "vr_cache_update", "vr_cache_load", "vr_cache_read", "vr_refine_begin", "vr_refine_pass",
@@ -259,6 +261,11 @@ class Renderer:
     def set_tile_order(self, mode):
         """0: raster tile queue; 1 (default): costliest tiles of the previous render of the same grid first."""
         self._check(lib().vr_set_tile_order(self._ctx, mode))
+
+    def set_ray_continuation(self, lanes_per_ray=16, min_samples_left=32):
+        """Once the tile queue runs dry, finish rays with more than ``min_samples_left`` samples to go
+        in a second launch with ``lanes_per_ray`` lanes each (0 = off); see vr_set_ray_continuation."""
+        self._check(lib().vr_set_ray_continuation(self._ctx, int(lanes_per_ray), int(min_samples_left)))
 
     def plan(self, cams, images=None, mode=VR_MODE_DVR):
         """A graph-captured single launch over all ``cams``; returns a RenderPlan."""
