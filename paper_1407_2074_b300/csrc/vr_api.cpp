@@ -554,6 +554,10 @@ vr_status vr_insert_block(vr_ctx* c, const int64_t origin[3], const int64_t exte
         CK(c, launch_slot_init(g, c->pool, c->rn, c->ps, c->d_list, n, st));
     }
     const long long org[3] = {origin[0], origin[1], origin[2]}, ext[3] = {extent[0], extent[1], extent[2]};
+    // one launch per level, 0 .. N: each level reads the one below (step 2 of the construction).
+    // Levels 2 .. N in one launch, each parent updated by the CTA finishing its last child slot,
+    // measured slower (228 vs 84 us on the 24 GiB workload): a CTA that completes several parents
+    // updates them one after another, and one slot's update already takes ~13 us.
     for (int L = 0; L <= g.N; ++L) {
         CK(c, launch_level_update(g, L, lo[L], hi[L], src, org, ext, c->pool, c->rn, c->ns, c->ps, c->err, st));
         if (L == 0 && up >= 0) CK(c, cudaEventRecord(c->stage_free[up], st));
