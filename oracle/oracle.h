@@ -172,6 +172,14 @@ int or_render_grad_xf(or_volume* v, const or_camera* cam, const float* tf, const
                       int64_t n, const int32_t* px, const int32_t* py, const double* dl, double* dtf, double* dscale,
                       int threads);
 
+/* Algorithmic footprint of one DVR frame of cam (every pixel, single-precision decisions): the
+ * number of distinct voxels of each level 0..N read by a trilinear corner of some sample
+ * (voxels[L]) and of distinct node entries read on some sample's descent from the root (nodes),
+ * over the samples up to the natural early-termination stop.  What a frame must read at least;
+ * border duplicates and padding of a brick layout are not part of it. */
+int or_render_footprint(or_volume* v, const or_camera* cam, const float* tf, const float* scale, int64_t* voxels,
+                        int64_t* nodes, int threads);
+
 /* Full-frame rendering with a partial brick cache (Sec. "Full-Frame Ray-Casting"): resident[n]
  * != 0 when node n's brick is in the render cache (dense numbering of or_node_index).  A sample
  * whose node's brick is missing requests it and uses the nearest present brick of the parent or

@@ -369,6 +369,23 @@ def render_grad(vol, cam, tf, scale, pixels, dl, threads=0, xf=None, ert_margin=
     return dtf, dsc
 
 
+def render_footprint(vol: Volume, cam: dict, tf: np.ndarray, scale, threads=0):
+    """Distinct voxels per level read by trilinear corners and distinct node entries read on the
+    descents of a whole DVR frame (single-precision decisions, samples up to the natural stop)."""
+    L = lib()
+    L.or_render_footprint.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+    tf = np.ascontiguousarray(tf, dtype=np.float32)
+    sc = np.ascontiguousarray(scale, dtype=np.float32)
+    cs = camera_struct(cam)
+    vox = np.zeros(vol.N + 1, dtype=np.int64)
+    nodes = np.zeros(1, dtype=np.int64)
+    if L.or_render_footprint(vol.handle, ctypes.byref(cs), tf.ctypes.data, sc.ctypes.data, vox.ctypes.data,
+                             nodes.ctypes.data, threads) != 0:
+        raise ValueError("oracle render_footprint: invalid arguments")
+    return [int(x) for x in vox], int(nodes[0])
+
+
 def ray(vol_or_geom, cam, px, py):
     g = vol_or_geom.geom if isinstance(vol_or_geom, Volume) else vol_or_geom
     d = (ctypes.c_float * 3)()

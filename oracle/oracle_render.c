@@ -444,6 +444,31 @@ typedef struct {
     uint8_t* req;       /* per node: its brick was requested (output) */
 } cache_io;
 
+/* Algorithmic footprint of a render (or_render_footprint): one bit per (level, voxel) read by a
+ * trilinear corner and one per node entry read on a descent, for the samples up to the natural
+ * stop.  Set with atomic ORs (rays run on several threads). */
+typedef struct {
+    uint8_t* vox[OR_MAXL];
+    uint8_t* nodes;
+} fp_io;
+
+static void bit_set(uint8_t* bits, int64_t i) { __atomic_fetch_or(&bits[i >> 3], (uint8_t)(1u << (i & 7)), __ATOMIC_RELAXED); }
+
+/* The eight corners of the trilinear cell of p at level L (the same cell as trilinear()). */
+static void fp_corners(const or_geom* g, fp_io* fp, int L, const double p[3]) {
+    int64_t c[3][2];
+    for (int a = 0; a < 3; ++a) {
+        double u = ldexp(p[a], -L) - 0.5;
+        int64_t i = (int64_t)floor(u), hi = g->ldim[L][a] - 1;
+        c[a][0] = i < 0 ? 0 : (i > hi ? hi : i);
+        c[a][1] = i + 1 < 0 ? 0 : (i + 1 > hi ? hi : i + 1);
+    }
+    for (int dz = 0; dz < 2; ++dz)
+        for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx)
+                bit_set(fp->vox[L], (c[2][dz] * g->ldim[L][1] + c[1][dy]) * g->ldim[L][0] + c[0][dx]);
+}
+
 /* Admissible results of one march, for or_render_check: with target != NULL, *best receives the
  * smallest max-abs RGBA difference between target and a state the ray may correctly end in. */
 typedef struct {
@@ -467,7 +492,7 @@ static void adm_offer(adm_t* ad, const double st[4]) {
  * natural-decision forward for the adjoint; ad != NULL collects the admissible end states. */
 static void march(or_volume* v, const or_camera* cam, const cam_derived* cd, const float* tf, const float* scale,
                   const float* xf, int mode, int geometry, int px, int py, or_pixel* out, recbuf* rec,
-                  const cache_io* cio, edge_ctl* ctl, adm_t* ad) {
+                  const cache_io* cio, edge_ctl* ctl, adm_t* ad, fp_io* fp) {
     const or_geom* g = or_volume_geom(v);
     int C = g->C;
     const int fp64 = geometry == OR_GEOM_FP64;
@@ -586,6 +611,10 @@ static void march(or_volume* v, const or_camera* cam, const cam_derived* cd, con
                 }
             }
         if (!have_nat || mode == 1) ++nsamp;
+        if (fp && !fp64 && !xf && !have_nat) { /* the descent path and the cell of this sample */
+            for (int L = lev; L <= g->N; ++L) bit_set(fp->nodes, or_node_index(g, L, path[L][0], path[L][1], path[L][2]));
+            if (samp_lev >= 0) fp_corners(g, fp, samp_lev, p);
+        }
         for (int c = 0; c < C; ++c) {
             double I;
             if (xf)
@@ -695,6 +724,7 @@ typedef struct {
     const int32_t* px;
     const int32_t* py;
     or_pixel* out;
+    fp_io* fp;           /* or_render_footprint: bitmaps to mark, else NULL */
     const float* target; /* or_render_check: the pixels to compare [n][4] */
     or_check* chk;
     double stop_err; /* or_render_check: stop enumerating once a variant is this close */
@@ -704,7 +734,7 @@ static void render_range(void* p, int64_t b, int64_t e) {
     render_job* j = (render_job*)p;
     for (int64_t i = b; i < e; ++i)
         march(j->v, j->cam, &j->cd, j->tf, j->scale, j->xf, j->mode, j->geometry, j->px[i], j->py[i], &j->out[i],
-              NULL, &j->cio, NULL, NULL);
+              NULL, &j->cio, NULL, NULL, j->fp);
 }
 
 static int cam_valid(const or_camera* cam) {
@@ -751,6 +781,50 @@ int or_render(or_volume* v, const or_camera* cam, const float* tf, const float* 
     return or_render_xf(v, cam, tf, scale, NULL, mode, n, px, py, out, threads);
 }
 
+static int64_t popcount_bytes(const uint8_t* b, int64_t n) {
+    int64_t s = 0;
+    for (int64_t i = 0; i < n; ++i) s += __builtin_popcount(b[i]);
+    return s;
+}
+
+int or_render_footprint(or_volume* v, const or_camera* cam, const float* tf, const float* scale, int64_t* voxels,
+                        int64_t* nodes, int threads) {
+    if (!v || !cam_valid(cam) || !tf || !scale || !voxels || !nodes) return -1;
+    const or_geom* g = or_volume_geom(v);
+    const int64_t n = (int64_t)cam->width * cam->height;
+    int32_t* px = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t* py = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    or_pixel* out = (or_pixel*)malloc(sizeof(or_pixel) * (size_t)n);
+    fp_io fp;
+    memset(&fp, 0, sizeof fp);
+    int ok = px && py && out;
+    for (int L = 0; L <= g->N && ok; ++L) {
+        fp.vox[L] = (uint8_t*)calloc((size_t)((g->ldim[L][0] * g->ldim[L][1] * g->ldim[L][2] + 7) / 8), 1);
+        ok = fp.vox[L] != NULL;
+    }
+    if (ok) ok = (fp.nodes = (uint8_t*)calloc((size_t)((or_node_count(g) + 7) / 8), 1)) != NULL;
+    if (ok) {
+        for (int64_t i = 0; i < n; ++i) {
+            px[i] = (int32_t)(i % cam->width);
+            py[i] = (int32_t)(i / cam->width);
+        }
+        render_job j;
+        job_init(&j, v, cam, tf, scale, NULL, 0, OR_GEOM_FP32, px, py);
+        j.out = out;
+        j.fp = &fp;
+        or_parallel_for(n, 16, threads, render_range, &j);
+        for (int L = 0; L <= g->N; ++L)
+            voxels[L] = popcount_bytes(fp.vox[L], (g->ldim[L][0] * g->ldim[L][1] * g->ldim[L][2] + 7) / 8);
+        *nodes = popcount_bytes(fp.nodes, (or_node_count(g) + 7) / 8);
+    }
+    for (int L = 0; L <= g->N; ++L) free(fp.vox[L]);
+    free(fp.nodes);
+    free(px);
+    free(py);
+    free(out);
+    return ok ? 0 : -2;
+}
+
 /* Every variant of the ray's knife-edge decisions, depth first: the march with the branches in
  * script[0..len) forced and the natural branch beyond, then, for each later flagged decision j
  * (up to OR_MAXFLAG), the march that takes the other branch there and the natural one between. */
@@ -759,7 +833,7 @@ static void explore(render_job* j, int64_t i, const unsigned char* script, int l
     adm_t ad = {j->target + 4 * i, INFINITY};
     or_pixel pix;
     march(j->v, j->cam, &j->cd, j->tf, j->scale, j->xf, j->mode, j->geometry, j->px[i], j->py[i], &pix, NULL, NULL,
-          j->geometry == OR_GEOM_FP64 ? &e : NULL, &ad);
+          j->geometry == OR_GEOM_FP64 ? &e : NULL, &ad, NULL);
     out->variants++;
     if (ad.best < out->err) out->err = ad.best;
     if (len == 0) {
@@ -895,7 +969,7 @@ static void* grad_worker(void* p) {
         rb.n = 0;
         or_pixel px;
         march(j->rj.v, j->rj.cam, &j->rj.cd, j->rj.tf, j->rj.scale, j->rj.xf, 0, OR_GEOM_FP32, j->rj.px[i],
-              j->rj.py[i], &px, &rb, NULL, NULL, NULL);
+              j->rj.py[i], &px, &rb, NULL, NULL, NULL, NULL);
         ray_grad(g, j->rj.tf, &rb, j->dl + 4 * i, dtf, dsc);
         if (j->ert_edge) j->ert_edge[i] = (uint8_t)ert_knife_edge(&rb, (double)j->rj.cam->ert_alpha, j->ert_margin);
     }

@@ -1012,9 +1012,10 @@ struct DVRCompositeH : NoHooks {
 };
 
 // DVR that also records the distinct (level, voxel) pairs read by trilinear corners and the
-// node entries visited: the algorithmic footprint of a frame (measurement only).
+// node entries visited: the algorithmic footprint of a frame (measurement only).  Samples one by one
+// (no pairs), so that no sample past the stop is read.
 template <int C>
-struct DVRFootprint : DVRComposite<C> {
+struct DVRFootprint : DVRComposite<C, true, false> {
     unsigned int* const* vmark;
     unsigned int* nmark;
     __device__ __forceinline__ void on_node(long long nid) {
