@@ -153,7 +153,9 @@ REF_RAYS = 16384  # rays per step of the reference arm
 def oracle_volume(w, torch, slab=16):
     """The oracle state of the whole workload volume at the workload's tau: a streamed oracle volume
     fed once in z order (level 0 from the synthetic generator's device form, copied to the host;
-    levels >= 1 and node records built on the host). Untimed setup of the CPU baseline."""
+    levels >= 1 and node records built on the host). Untimed setup of the CPU baseline; the
+    oracle's own construction time (feeding the slices, then the upper levels and nodes, all host
+    cores) is kept in oracle_volume.last."""
     from oracle import oracle as O
 
     spec = w.spec()
@@ -162,14 +164,100 @@ def oracle_volume(w, torch, slab=16):
     buf = torch.empty((slab, Y, X, 3), dtype=torch.int16, device="cuda")
     host = torch.empty((slab, Y, X, 3), dtype=torch.int16, pin_memory=True)
     st = torch.cuda.current_stream().cuda_stream
+    t_feed = 0.0
     for z0 in range(0, Z, slab):
         z1 = min(Z, z0 + slab)
         spec.generate_device(buf.data_ptr(), z0, z1, st)
         host[: z1 - z0].copy_(buf[: z1 - z0])
         torch.cuda.synchronize()
+        t = time.time()
         vol.feed(z0, host[: z1 - z0].numpy())
+        t_feed += time.time() - t
+    t = time.time()
     vol.finish()
+    t_fin = time.time() - t
+    oracle_volume.last = {"slices": Z, "feed_s": t_feed, "finish_s": t_fin,
+                          "insert_ms_per_slice": 1e3 * (t_feed + t_fin) / Z, "cores": os.cpu_count()}
     return vol
+
+
+def oracle_frame_ms(vol, cam, tf, scale, n_all, n_one, seed=0):
+    """The oracle's time for one whole frame of cam, all host cores and one thread, estimated from
+    uniformly random pixels (n_all and n_one of them; the whole frame when it has fewer):
+    seconds for the sample x pixels of the frame / pixels sampled."""
+    from oracle import oracle as O
+
+    W, H = cam["width"], cam["height"]
+    out = {"pixels": W * H}
+    rng = np.random.default_rng(seed)
+    for key, n, threads in (("all_cores", n_all, 0), ("one_thread", n_one, 1)):
+        if n >= W * H:
+            pix, n = None, W * H
+        else:
+            pix = (rng.integers(0, W, n).astype(np.int32), rng.integers(0, H, n).astype(np.int32))
+        t = time.time()
+        O.render(vol, cam, tf, scale, pix, 0, threads)
+        dt = time.time() - t
+        out[key + "_ms"] = 1e3 * dt * (W * H) / n
+        out[key + "_pixels_timed"] = n
+    out["cores"] = os.cpu_count()
+    return out
+
+
+def oracle_leg(torch, vr, S):
+    """The oracle's own timings on the host cores for the tiny, streamed and differentiable
+    workloads: construction per slice and a whole frame (all cores and one thread; large frames
+    estimated from random pixels, see oracle_frame_ms)."""
+    from oracle import oracle as O
+
+    res = {}
+    w = S.tiny()
+    vol = w.spec().volume()
+    t = time.time()
+    ov = O.DenseVolume(w.dims, 3, w.brick, 0, w.tau)
+    for z in range(w.dims[2]):
+        ov.insert((0, 0, z), vol[z : z + 1])
+    ov.build()
+    res["tiny-64^3"] = {"construction_ms_per_slice": 1e3 * (time.time() - t) / w.dims[2],
+                        "frame": oracle_frame_ms(ov, w.cameras[0], w.tf(), [1.0, 1.0, 1.0], 1 << 30, 1 << 30)}
+    del ov
+    for name, w in (("streamed-1024x1024x512", S.streamed(tau=3277)),
+                    ("differentiable-512^3", S.differentiable())):
+        # a dense oracle volume (every level stored), fed slab by slab from the generator's device
+        # form; the oracle's construction (inserts + the build of levels >= 1 and nodes) is timed
+        spec = w.spec()
+        X, Y, Z = w.dims
+        ov = O.DenseVolume(w.dims, 3, w.brick, 0, w.tau)
+        buf = torch.empty((16, Y, X, 3), dtype=torch.int16, device="cuda")
+        host = torch.empty((16, Y, X, 3), dtype=torch.int16, pin_memory=True)
+        st = torch.cuda.current_stream().cuda_stream
+        t_ins = 0.0
+        for z0 in range(0, Z, 16):
+            z1 = min(Z, z0 + 16)
+            spec.generate_device(buf.data_ptr(), z0, z1, st)
+            host[: z1 - z0].copy_(buf[: z1 - z0])
+            torch.cuda.synchronize()
+            t = time.time()
+            ov.insert((0, 0, z0), host[: z1 - z0].numpy().view(np.uint16))
+            t_ins += time.time() - t
+        t = time.time()
+        ov.build()
+        t_build = time.time() - t
+        res[name] = {"construction_ms_per_slice": 1e3 * (t_ins + t_build) / Z, "insert_s": t_ins, "build_s": t_build,
+                     "frame": oracle_frame_ms(ov, w.cameras[0], w.tf(), [1.0, 1.0, 1.0], 65536, 8192)}
+        if name.startswith("differentiable"):
+            # the FP64 oracle gradient of the frame (all cores), from 16384 random pixels
+            cam = w.cameras[0]
+            rng = np.random.default_rng(5)
+            n = 16384
+            px = rng.integers(0, cam["width"], n).astype(np.int32)
+            py = rng.integers(0, cam["height"], n).astype(np.int32)
+            dl = rng.normal(size=(n, 4))
+            t = time.time()
+            O.render_grad(ov, cam, w.tf(), [1.0, 1.0, 1.0], (px, py), dl)
+            res[name]["gradient_ms_all_cores"] = 1e3 * (time.time() - t) * cam["width"] * cam["height"] / n
+        del ov, buf, host
+    return res
 
 
 def cpu_baseline(w, vol, n_rays, seed=0, threads=0):
@@ -472,7 +560,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--fp16", type=int, default=1, help="also time the FP16-interpolation render")
     ap.add_argument("--suite", type=int, default=1, help="also run the batched and differentiable legs")
-    ap.add_argument("--leg", choices=["batched", "adjoint", "out_of_core", "streamed"],
+    ap.add_argument("--leg", choices=["batched", "adjoint", "out_of_core", "streamed", "oracle"],
                     help="run only this secondary leg and print its JSON (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -489,7 +577,7 @@ def main():
         from synth import synth as S
 
         fn = {"batched": batched_leg, "adjoint": adjoint_leg, "out_of_core": table1_leg,
-              "streamed": streamed_leg}[args.leg]
+              "streamed": streamed_leg, "oracle": oracle_leg}[args.leg]
         print(json.dumps({args.leg: fn(torch, vr, S)}), flush=True)
         return
 
@@ -761,11 +849,19 @@ def main():
         table1 = table1_leg(torch, vr, S)
         streamed = streamed_leg(torch, vr, S)
 
-    cpu = parity = None
+    cpu = parity = oracle_times = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         ovol = oracle_volume(w, torch)
         s, t, cores = cpu_baseline(w, ovol, args.cpu_rays)
         from oracle import oracle as O
+
+        # the oracle's frame times (all cores, one thread) of orbit frames 0/15/30/45 and its
+        # construction time per slice
+        oracle_times = {"construction_ms_per_slice": oracle_volume.last["insert_ms_per_slice"],
+                        "construction": oracle_volume.last,
+                        "frames": {str(f): oracle_frame_ms(ovol, w.cameras[f], w.tf(), [1.0, 1.0, 1.0], 65536, 4096,
+                                                           seed=f)
+                                   for f in (0, 15, 30, 45) if f < len(w.cameras)}}
 
         per_frame = {}
         rng = np.random.default_rng(23)
@@ -826,7 +922,7 @@ def main():
                                     "frac": ins_bytes / (insert_ms / 1e3) / 1e9 / peak},
                 "samples_per_frame": samples / args.steps / ws, "build_s_full_volume": build_s,
                 "roofline": roof, "issue_roofline": issue, "cpu_baseline": cpu, "parity_vs_oracle": parity,
-                "e2e": e2e, "fp16": fp16,
+                "oracle_timings": oracle_times, "e2e": e2e, "fp16": fp16,
                 "next_rows": variants,
                 "batched": batched, "adjoint": adjoint, "out_of_core": table1, "streamed": streamed,
                 "gpu_launches": launches_per_step * args.steps, "clocks": clk.summary()}

@@ -53,6 +53,47 @@ class Stats(ctypes.Structure):
                 ("last_render_continued", ctypes.c_int64)]
 
 
+_AllocFn = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FreeFn = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class Allocator(ctypes.Structure):
+    _fields_ = [("alloc", _AllocFn), ("free", _FreeFn), ("user", ctypes.c_void_p)]
+
+
+def torch_allocator(device_index: int) -> Allocator:
+    """vr_allocator callbacks on PyTorch's caching allocator: the library's device memory (brick
+    pool, node tables, render buffers) is then torch's, counted by torch.cuda.memory_allocated and
+    released to torch when the context is destroyed.  alloc returns NULL when torch cannot
+    allocate (the library reports VR_ERR_OUT_OF_MEMORY)."""
+    import torch
+
+    def alloc(nbytes, user, stream):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device_index, stream if stream else None)
+        except Exception:
+            return None
+
+    def free(ptr, user, stream):
+        try:
+            torch.cuda.caching_allocator_delete(ptr)
+        except Exception:
+            pass
+
+    return Allocator(_AllocFn(alloc), _FreeFn(free), None)
+
+
+_live = None  # contexts to destroy before the interpreter (and torch) shuts down
+
+
+def _close_all():
+    for r in list(_live or ()):
+        try:
+            r.close()
+        except Exception:
+            pass
+
+
 _lib = None
 
 
@@ -140,7 +181,13 @@ class Renderer:
     """One volume context (vr_ctx) on the current CUDA device."""
 
     def __init__(self, dims, channels, brick, background=0, tau=0, pool_capacity_bytes=0, precision="fp32",
-                 device=None, cache_capacity_bytes=0, store_on_host=False):
+                 device=None, cache_capacity_bytes=0, store_on_host=False, allocator="torch"):
+        """allocator: "torch" (default) -- the library's device memory comes from PyTorch's caching
+        allocator through vr_allocator; None -- the library allocates with cudaMalloc itself."""
+        global _live
+        import atexit
+        import weakref
+
         import torch
 
         self._ctx = None
@@ -150,12 +197,20 @@ class Renderer:
         self.dims, self.C, self.M = tuple(int(d) for d in dims), int(channels), int(brick)
         opt = Options(background, tau, pool_capacity_bytes, VR_FP16_INTERP if precision == "fp16" else VR_FP32,
                       cache_capacity_bytes, 1 if store_on_host else 0)
+        # the callbacks live as long as the context
+        self._alloc = torch_allocator(self.device.index) if allocator == "torch" else None
+        if allocator not in ("torch", None):
+            raise ValueError('allocator must be "torch" or None')
         h = ctypes.c_void_p()
-        rc = lib().vr_create((ctypes.c_int64 * 3)(*self.dims), self.C, self.M, ctypes.byref(opt), None,
-                             ctypes.byref(h))
+        rc = lib().vr_create((ctypes.c_int64 * 3)(*self.dims), self.C, self.M, ctypes.byref(opt),
+                             ctypes.byref(self._alloc) if self._alloc is not None else None, ctypes.byref(h))
         if rc != VR_OK:
             raise VRError(rc, lib().vr_last_error(None).decode())
         self._ctx = h.value
+        if _live is None:
+            _live = weakref.WeakSet()
+            atexit.register(_close_all)
+        _live.add(self)
         st = self.stats()
         self.levels = st.levels
 
