@@ -83,8 +83,8 @@ class ClockSampler:
             self.t.start()
             self.source = "nvml, 2 ms"
             return self
-        except Exception:
-            pass
+        except Exception as e:
+            self.nvml_error = f"{type(e).__name__}: {e}"
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -121,8 +121,11 @@ class ClockSampler:
         if not self.rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
         reasons = sorted(set(n for r in self.rows for n in r[2]))
-        return {"sm_mhz": float(np.median([r[0] for r in self.rows])), "sm_max_mhz": max(r[1] for r in self.rows),
-                "reasons": reasons, "samples": len(self.rows), "sampler": self.source}
+        out = {"sm_mhz": float(np.median([r[0] for r in self.rows])), "sm_max_mhz": max(r[1] for r in self.rows),
+               "reasons": reasons, "samples": len(self.rows), "sampler": self.source}
+        if getattr(self, "nvml_error", None):
+            out["nvml_unavailable"] = self.nvml_error
+        return out
 
 
 def dist_env():
@@ -550,7 +553,7 @@ def table1_leg(torch, vr, S, frames=36, budget=64):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=120)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-rays", type=int, default=0, help="CPU baseline rays (0 = the whole frame 0)")

@@ -260,9 +260,10 @@ vr_status vr_read_voxels(vr_ctx* ctx, int level, int64_t n, const int64_t* xyz, 
 vr_status vr_read_node(vr_ctx* ctx, int level, int64_t i, int64_t j, int64_t k, uint32_t* flags, uint16_t* avg,
                        void* cuda_stream);
 
-/* Library utility (no counterpart in the paper): sizes of the tree and the pool, and the sample
- * and ray counts of the last vr_render (the work units of the measurement).  Host-side, does not
- * synchronise.  Errors: VR_ERR_INVALID_ARG (NULL). */
+/* Library utility (no counterpart in the paper): sizes of the tree and the pool, and the sample,
+ * ray and continued-ray counts of the last vr_render (the work units of the measurement), read
+ * from the device: waits for the work queued so far.  Errors: VR_ERR_INVALID_ARG (NULL),
+ * VR_ERR_CUDA. */
 vr_status vr_stats(vr_ctx* ctx, vr_stats_t* out);
 
 /* Test hook (no counterpart in the paper): writes code (!= 0) into the context's device error

@@ -132,11 +132,6 @@ struct Shaded {
     float r, g, b, q;
 };
 
-__device__ __forceinline__ Shaded shfl_shaded(unsigned mask, const Shaded& s, int src) {
-    return Shaded{__shfl_sync(mask, s.r, src), __shfl_sync(mask, s.g, src), __shfl_sync(mask, s.b, src),
-                  __shfl_sync(mask, s.q, src)};
-}
-
 // Traversal state of one ray, shared by the one-lane march and the lane-group march: the level of
 // detail L* of the current sample and the cached node -- its level, grid index, the faces of its
 // box the ray heads for, and its brick slot or AVG.  Sample positions, L* and the node choice use
@@ -583,20 +578,21 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
 
 // Lane-group march (DVR): the 2^lg lanes of one group march one ray together, lane j shading
 // samples k + j of each step in lockstep; every lane of the group then composites the shaded
-// samples in order from shuffles (the second step of the two-step composite), so the group ends
+// samples in order (the second step of the two-step composite), so the group ends
 // each step with the same ray state in every lane and stops at the same sample.  A step ends at the
 // group's first sample in a brick-less node with a full segment: as in the one-lane march, that
 // sample starts a run of equal samples, which its lane composites in closed form and shares.  The
 // samples composited, the runs and the stop are those of march(), so the image is bit for bit the
 // one-lane image.  gmask: the group's lanes; gbase: its first lane; j: this lane's place in it;
-// k0: the first sample (f holds the ray state before it).
+// k0: the first sample (f holds the ray state before it); s_grp: the warp's 32 shared-memory slots.
 template <int C, int VS, bool POW2, bool H, class F>
 __device__ __forceinline__ long long march_group(const Geo& g, const uint16_t* __restrict__ pool,
                                                  const RNode* __restrict__ rn, const CamParam& cp, const float d[3],
                                                  float t0, float t1, F& f, int lg, unsigned gmask, int gbase, int j,
-                                                 int k0) {
+                                                 int k0, float4* s_grp) {
     const float dt = cp.dt;
     const int G = 1 << lg;
+    const int lane = gbase + j;
     const unsigned gbits = gmask >> gbase; // the group's lanes as bits 0 .. G-1
     RayCursor<C, VS, POW2> cur(g, pool, rn, cp, d);
     int k = k0;
@@ -630,9 +626,26 @@ __device__ __forceinline__ long long march_group(const Geo& g, const uint16_t* _
         const int jr = run_bits ? __ffs(run_bits) - 1 : G; // first sample that starts a run
         const int je = end_bits ? __ffs(end_bits) - 1 : G; // first sample past the ray's end
         const int jl = jr < je ? jr : je;
+        // The in-order update of the ray by the step's shaded samples 0 .. jl-1, through the warp's
+        // shared-memory slots (one store per lane, broadcast reads): the reads do not depend on the
+        // chain, so they run ahead of it, and no branch leaves the loop early -- once the ray
+        // stops, the later samples are skipped, leaving the same state as update() one by one.
+        s_grp[lane] = make_float4(s.r, s.g, s.b, s.q);
+        __syncwarp(gmask);
+        int stop_at = -1;
+#pragma unroll 4
         for (int q = 0; q < jl; ++q) {
-            if (f.update(shfl_shaded(gmask, s, gbase + q))) return k + q + 1;
+            const float4 v = s_grp[gbase + q];
+            if (stop_at < 0) {
+                f.Cr = fmaf(f.T, v.x, f.Cr);
+                f.Cg = fmaf(f.T, v.y, f.Cg);
+                f.Cb = fmaf(f.T, v.z, f.Cb);
+                f.T *= v.w;
+                if (1.0f - f.T >= f.ert) stop_at = q;
+            }
         }
+        __syncwarp(gmask); // the slots are read before the next step writes them
+        if (stop_at >= 0) return k + stop_at + 1;
         if (jl == G) {
             k += G;
             continue;
@@ -1242,6 +1255,7 @@ __global__ void __launch_bounds__(256, VR_RENDER_MIN_CTAS) render_tail_kernel(Re
     extern __shared__ float4 s_tf[];
     __shared__ float s_scl[MAXC];
     __shared__ __half s_sh[MAXC];
+    __shared__ float4 s_grp[8][32]; // per warp: the shaded samples of a step (256-thread CTAs)
     const HalfEntry* s_tfh = reinterpret_cast<const HalfEntry*>(s_tf + C * 512);
     load_render_tables<C, H>(a, s_tf, s_scl, s_sh);
     using F = std::conditional_t<H, DVRCompositeH<C>, DVRComposite<C>>;
@@ -1272,7 +1286,8 @@ __global__ void __launch_bounds__(256, VR_RENDER_MIN_CTAS) render_tail_kernel(Re
         f.Cg = rc.Cg;
         f.Cb = rc.Cb;
         const long long n =
-            march_group<C, VS, POW2, H>(a.g, a.pool, a.rnodes, *cp, dd, r0, r1, f, lg, gmask, gbase, j, rc.k);
+            march_group<C, VS, POW2, H>(a.g, a.pool, a.rnodes, *cp, dd, r0, r1, f, lg, gmask, gbase, j, rc.k,
+                                        s_grp[threadIdx.x >> 5]);
         if (j == 0) {
             my_samples += (unsigned long long)(n - rc.k);
             reinterpret_cast<float4*>(cp->img)[(long long)rc.py * cp->W + rc.px] =
