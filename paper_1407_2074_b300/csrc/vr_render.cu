@@ -118,10 +118,14 @@ struct TFLookup {
         i = min((int)w, 254);
         lam = w - (float)i;
         const float4 T = s_tf[c * 256 + i], D = s_tf[(C + c) * 256 + i];
-        r = fmaf(lam, D.x, T.x);
-        g = fmaf(lam, D.y, T.y);
-        b = fmaf(lam, D.z, T.z);
-        al = fmaf(lam, D.w, T.w);
+        // two packed FP32 FMAs (each element rounded as fmaf)
+        const float2 l2 = make_float2(lam, lam);
+        const float2 rg = __ffma2_rn(l2, make_float2(D.x, D.y), make_float2(T.x, T.y));
+        const float2 ba = __ffma2_rn(l2, make_float2(D.z, D.w), make_float2(T.z, T.w));
+        r = rg.x;
+        g = rg.y;
+        b = ba.x;
+        al = ba.y;
     }
 };
 
@@ -317,17 +321,39 @@ struct RayCursor {
             }
         }
         const float fxy = fr[0] * fr[1], fxz = fr[0] * fr[2], fyz = fr[1] * fr[2], fxyz = fxy * fr[2];
+        // channel pairs in packed FP32 (each element rounded as its scalar operation)
+        auto sub2 = [](float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); };
+        auto bcast2 = [](float x) { return make_float2(x, x); };
+#pragma unroll
+        for (int c = 0; c + 1 < C; c += 2) {
+            float2 W[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) W[q] = make_float2(w[q][c], w[q][c + 1]);
+            const float2 d10 = sub2(W[1], W[0]), d20 = sub2(W[2], W[0]), d40 = sub2(W[4], W[0]);
+            const float2 d32 = sub2(W[3], W[2]), d54 = sub2(W[5], W[4]), d64 = sub2(W[6], W[4]);
+            float2 v = __ffma2_rn(bcast2(fr[0]), d10, sub2(W[0], bcast2(VBIAS)));
+            v = __ffma2_rn(bcast2(fr[1]), d20, v);
+            v = __ffma2_rn(bcast2(fr[2]), d40, v);
+            v = __ffma2_rn(bcast2(fxy), sub2(d32, d10), v);
+            v = __ffma2_rn(bcast2(fxz), sub2(d54, d10), v);
+            v = __ffma2_rn(bcast2(fyz), sub2(d64, d20), v);
+            v = __ffma2_rn(bcast2(fxyz), sub2(sub2(sub2(W[7], W[6]), d54), sub2(d32, d10)), v);
+            out[c] = v.x;
+            out[c + 1] = v.y;
+        }
 #pragma unroll
         for (int c = 0; c < C; ++c) {
             const float v0 = w[0][c], v1 = w[1][c], v2 = w[2][c], v3 = w[3][c];
             const float v4 = w[4][c], v5 = w[5][c], v6 = w[6][c], v7 = w[7][c];
-            float v = fmaf(fr[0], v1 - v0, v0 - VBIAS);
-            v = fmaf(fr[1], v2 - v0, v);
-            v = fmaf(fr[2], v4 - v0, v);
-            v = fmaf(fxy, (v3 - v2) - (v1 - v0), v);
-            v = fmaf(fxz, (v5 - v4) - (v1 - v0), v);
-            v = fmaf(fyz, (v6 - v4) - (v2 - v0), v);
-            out[c] = fmaf(fxyz, ((v7 - v6) - (v5 - v4)) - ((v3 - v2) - (v1 - v0)), v);
+            if (c == C - 1 && (C & 1)) { // the odd channel out
+                float v = fmaf(fr[0], v1 - v0, v0 - VBIAS);
+                v = fmaf(fr[1], v2 - v0, v);
+                v = fmaf(fr[2], v4 - v0, v);
+                v = fmaf(fxy, (v3 - v2) - (v1 - v0), v);
+                v = fmaf(fxz, (v5 - v4) - (v1 - v0), v);
+                v = fmaf(fyz, (v6 - v4) - (v2 - v0), v);
+                out[c] = fmaf(fxyz, ((v7 - v6) - (v5 - v4)) - ((v3 - v2) - (v1 - v0)), v);
+            }
             if constexpr (F::kExactI) {
                 // the same polynomial in double: its coefficients are exact integers and the
                 // fractions exact floats, so this is the trilinear value to double rounding
@@ -899,16 +925,18 @@ struct DVRComposite : NoHooks {
             float a, oma;
             opacity(al, ell, a, oma);
             const float w = s.q * a;
-            s.r = fmaf(w, t.r, s.r);
-            s.g = fmaf(w, t.g, s.g);
+            const float2 rg = __ffma2_rn(make_float2(w, w), make_float2(t.r, t.g), make_float2(s.r, s.g));
+            s.r = rg.x;
+            s.g = rg.y;
             s.b = fmaf(w, t.b, s.b);
             s.q *= oma;
         }
         return s;
     }
     __device__ __forceinline__ bool update(const Shaded& s) {
-        Cr = fmaf(T, s.r, Cr);
-        Cg = fmaf(T, s.g, Cg);
+        const float2 rg = __ffma2_rn(make_float2(T, T), make_float2(s.r, s.g), make_float2(Cr, Cg));
+        Cr = rg.x;
+        Cg = rg.y;
         Cb = fmaf(T, s.b, Cb);
         T *= s.q;
         return 1.0f - T >= ert;
