@@ -789,12 +789,11 @@ def main():
             "algorithmic_bytes_per_launch": U,
             "peak_kind": peak_kind, "algorithmic_bytes_frames": len(fp),
             "distinct_voxels_per_level_first_frame": vox, "distinct_nodes_first_frame": nodes}
-    # DRAM traffic, L2 traffic and executed instructions of the same kernel from one small ncu
-    # capture (the medium stand-in volume, 1.2 GB pool, three launches), valid while the render
-    # sources are unchanged.  Scaling to this workload: DRAM and L2 bytes in proportion to the
-    # algorithmic bytes of the frame (traffic / U of the captured frames x this frame's U);
-    # instructions in proportion to the composited samples (instructions per sample of the
-    # captured frames x the live sample rate)
+    # DRAM and L2 traffic of the render's two kernels from one small ncu capture (the medium
+    # stand-in volume, 2.9 GB pool, three frames), valid while the render sources are unchanged,
+    # scaled to this workload in proportion to the algorithmic bytes of the frame (traffic / U of
+    # the captured frames x this frame's U); the captured instructions give an issue fraction only
+    # for the captured workload itself
     issue = None
     tr = os.path.join(ROOT, "profiles", "render_medium_counters.json")
     if os.path.exists(tr):
@@ -810,14 +809,18 @@ def main():
             roof["traffic_from"] = (f"ncu capture of {d['workload']} ({len(cf)} launches, {d['pool_gb']:.1f} GB "
                                     f"pool): DRAM bytes / algorithmic bytes = {dram_per_u:.2f}, scaled by this "
                                     f"frame's algorithmic bytes")
-            mhz = clk.summary().get("sm_mhz") or 2032.0
-            sms = torch.cuda.get_device_properties(local).multi_processor_count
-            ipeak = sms * 4 * 32 * mhz * 1e6 / 1e12
-            ach = ips * (samples / args.steps / ws) / (render_ms / 1e3) / 1e12
-            issue = {"bound": "issue", "achieved": ach, "peak": ipeak, "unit": "T thread-instructions/s",
-                     "frac": ach / ipeak, "thread_instructions_per_sample": ips,
-                     "instructions_from": f"ncu capture of {d['workload']}, per composited sample",
-                     "peak_from": f"{sms} SMs x 4 schedulers x 32 lanes x median SM clock"}
+            if args.workload == "medium":
+                # the captured frames themselves: their instructions per sample times the live rate
+                mhz = clk.summary().get("sm_mhz") or 2032.0
+                sms = torch.cuda.get_device_properties(local).multi_processor_count
+                ipeak = sms * 4 * 32 * mhz * 1e6 / 1e12
+                ach = ips * (samples / args.steps / ws) / (render_ms / 1e3) / 1e12
+                issue = {"bound": "issue", "achieved": ach, "peak": ipeak, "unit": "T thread-instructions/s",
+                         "frac": ach / ipeak, "thread_instructions_per_sample": ips,
+                         "instructions_from": f"ncu capture of {d['workload']}, per composited sample",
+                         "peak_from": f"{sms} SMs x 4 schedulers x 32 lanes x median SM clock"}
+            # (instructions per sample do not carry over to another workload: they depend on the share
+            # of samples composited in closed-form runs, so no issue figure is scaled to this one)
     capture_frames = None
     if args.workload == "medium":
         # what a counter capture of the first three render launches (frames 0-2) is divided by
