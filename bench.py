@@ -410,7 +410,8 @@ def streamed_leg(torch, vr, S):
 def adjoint_leg(torch, vr, S, steps=200, check_grad=True):
     """512^3 x 3 SPIM-like volume, 512x512 view: fit TF tables [3,256,4] + scales [3] to a target
     rendered with other tables (seeds 201-203) and scales (0.8, 1, 1.25); mean-L2 loss, Adam lr 1e-2,
-    hand-written adjoint with per-ray recompute."""
+    hand-written adjoint (each ray's final state read from the forward image, its samples re-marched
+    by the sweep, never stored)."""
     w = S.differentiable()
     spec = w.spec()
     X, Y, Z = w.dims
@@ -475,7 +476,8 @@ def adjoint_leg(torch, vr, S, steps=200, check_grad=True):
         dl[py, px] = g
         tf_np, sc_np = tf.detach().cpu().numpy(), sc.detach().cpu().numpy()
         r.set_transfer_functions(tf.detach(), sc.detach())
-        dtf, dsc = r.render_backward([cam], [torch.from_numpy(dl).cuda()])
+        fwd = r.render([cam])  # the training path: the backward reads each ray's end state from it
+        dtf, dsc = r.render_backward([cam], [torch.from_numpy(dl).cuda()], images=fwd)
         torch.cuda.synchronize()
         g_used = dl[py, px].astype(np.float64)  # duplicates keep the last write on both sides
         u, first_idx = np.unique(py.astype(np.int64) * cam["width"] + px, return_index=True)

@@ -194,6 +194,18 @@ vr_status vr_render_noalloc(vr_ctx* ctx, const vr_camera* cams, int n_cams, floa
 vr_status vr_render_backward(vr_ctx* ctx, const vr_camera* cams, int n_cams, const float* const* dl_dimages,
                              float* dl_dtf, float* dl_dscale, void* cuda_stream);
 
+/* vr_render_backward given also the DVR images (FP32 interpolation) that vr_render wrote for the
+ * same cameras, volume state, transfer functions and scales (device [H_i][W_i][4], unchanged
+ * since): each ray's final colour and transmittance (1 - alpha) are read from its pixel instead of
+ * being recomputed by a forward march, so each ray is marched once, by the sweep, which still
+ * takes the forward's decisions (samples, runs, early termination) itself.  The transmittance
+ * recovered as 1 - alpha carries alpha's rounding (absolute ~6e-8).  In the FP64 gradient-check
+ * mode the images are not used (the double forward is recomputed).  Errors as
+ * vr_render_backward, and VR_ERR_INVALID_ARG for NULL images.  The paper has no counterpart. */
+vr_status vr_render_backward_with_images(vr_ctx* ctx, const vr_camera* cams, int n_cams, const float* const* images,
+                                         const float* const* dl_dimages, float* dl_dtf, float* dl_dscale,
+                                         void* cuda_stream);
+
 /* Accumulation precision of vr_render_backward.  0 (default): single precision throughout.
  * 1 (FP64 gradient-check mode): the per-ray transmittance and colour of the sweep, the gradient
  * terms and their sums are double precision, for checks of the gradient element by element

@@ -796,15 +796,15 @@ vr_status vr_render(vr_ctx* c, const vr_camera* cams, int n, float* const* image
     return VR_OK;
 }
 
-vr_status vr_render_backward(vr_ctx* c, const vr_camera* cams, int n, const float* const* dl, float* dtf,
-                             float* dscale, void* stream) {
+static vr_status render_backward(vr_ctx* c, const vr_camera* cams, int n, const float* const* images,
+                                 const float* const* dl, float* dtf, float* dscale, void* stream) {
     vr_status s = check_ctx(c);
     if (s != VR_OK) return s;
     if (!cams || n <= 0 || !dl || !dtf || !dscale) return fail(c, VR_ERR_INVALID_ARG, "NULL argument");
     if (!c->tf_set) return fail(c, VR_ERR_INVALID_ARG, "transfer functions not set");
     cudaStream_t st = (cudaStream_t)stream;
     long long tiles = 0;
-    s = prepare_cams(c, cams, n, nullptr, dl, st, &tiles);
+    s = prepare_cams(c, cams, n, const_cast<float* const*>(images), dl, st, &tiles);
     if (s != VR_OK) return s;
     CK(c, cudaMemsetAsync(dtf, 0, sizeof(float) * 1024 * c->g.C, st));
     CK(c, cudaMemsetAsync(dscale, 0, sizeof(float) * c->g.C, st));
@@ -813,6 +813,7 @@ vr_status vr_render_backward(vr_ctx* c, const vr_camera* cams, int n, const floa
     a.stats = nullptr;
     a.dtf = dtf;
     a.dscale = dscale;
+    a.fwd_img = images != nullptr && !c->grad_fp64;
     if (c->grad_fp64) {
         const size_t nb = sizeof(double) * (size_t)(c->g.C * 1024 + c->g.C);
         if (!c->d_gacc) {
@@ -824,6 +825,17 @@ vr_status vr_render_backward(vr_ctx* c, const vr_camera* cams, int n, const floa
     }
     CK(c, launch_render_backward(a, grid_for(c, tiles, 128, 5), 128, st));
     return VR_OK;
+}
+
+vr_status vr_render_backward(vr_ctx* c, const vr_camera* cams, int n, const float* const* dl, float* dtf,
+                             float* dscale, void* stream) {
+    return render_backward(c, cams, n, nullptr, dl, dtf, dscale, stream);
+}
+
+vr_status vr_render_backward_with_images(vr_ctx* c, const vr_camera* cams, int n, const float* const* images,
+                                         const float* const* dl, float* dtf, float* dscale, void* stream) {
+    if (c && !images) return fail(c, VR_ERR_INVALID_ARG, "NULL images");
+    return render_backward(c, cams, n, images, dl, dtf, dscale, stream);
 }
 
 vr_status vr_render_footprint(vr_ctx* c, const vr_camera* cams, int n, float* const* images,

@@ -127,6 +127,7 @@ struct RenderArgs {
     unsigned int* cont_ctl;
     int cont_min, cont_lg;
     unsigned int* tile_cost;            // per tile: SM clock cycles / 64 it took (nullptr: not kept)
+    int fwd_img;                        // backward: cams[].img hold the forward's DVR images
     float* dtf;                         // backward: [C][256][4]
     float* dscale;                      // backward: [C]
     double* dacc;                       // backward, FP64 check mode: [C * 1024 + C] sums (zeroed)

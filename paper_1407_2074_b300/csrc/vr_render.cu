@@ -1682,16 +1682,25 @@ __global__ void __launch_bounds__(128, 5) render_backward_kernel(RenderArgs a) {
         if (!ray_setup(cp, a.g, px, py, d, t0, t1)) continue;
         const float4 gl = reinterpret_cast<const float4*>(cp.dimg)[(long long)py * cp.W + px];
         if (gl.x == 0.0f && gl.y == 0.0f && gl.z == 0.0f && gl.w == 0.0f) continue;
-        // the forward pass: the sweep's arithmetic (runs, no pairs)
+        // the forward pass: the sweep's arithmetic (runs, no pairs) -- or, given the forward's
+        // images (a.fwd_img; single precision only), the final colour and transmittance of the ray
+        // read from its pixel: the forward render composited the same samples in the same order
         std::conditional_t<D, DVRForwardD<C>, DVRComposite<C, true, false>> fw;
         fw.s_tf = s_tf;
         fw.s_scl = s_scl;
         fw.ert = cp.ert;
         if constexpr (D) fw.s_raw = s_raw;
-        if constexpr (XF)
+        if (!D && a.fwd_img) {
+            const float4 im = reinterpret_cast<const float4*>(cp.img)[(long long)py * cp.W + px];
+            fw.Cr = im.x;
+            fw.Cg = im.y;
+            fw.Cb = im.z;
+            fw.T = 1.0f - im.w;
+        } else if constexpr (XF) {
             march_xf<C, VS, POW2>(a.g, a.pool, a.rnodes, cp, d, t0, t1, a.xf, fw);
-        else
+        } else {
             march<C, VS, POW2, false>(a.g, a.pool, a.rnodes, cp, d, t0, t1, fw);
+        }
         DVRAdjoint<C, D> bw;
         bw.s_tf = s_tf;
         bw.s_scl = s_scl;

@@ -113,6 +113,8 @@ def lib():
         L.vr_set_channel_transforms.argtypes = [vp, vp]
         L.vr_render.argtypes = [vp, ctypes.POINTER(Camera), ctypes.c_int, ctypes.POINTER(vp), ctypes.c_int, vp]
         L.vr_render_backward.argtypes = [vp, ctypes.POINTER(Camera), ctypes.c_int, ctypes.POINTER(vp), vp, vp, vp]
+        L.vr_render_backward_with_images.argtypes = [vp, ctypes.POINTER(Camera), ctypes.c_int, ctypes.POINTER(vp),
+                                                     ctypes.POINTER(vp), vp, vp, vp]
         L.vr_read_level.argtypes = [vp, ctypes.c_int, vp, vp]
         L.vr_render_footprint.argtypes = [vp, ctypes.POINTER(Camera), ctypes.c_int, ctypes.POINTER(vp),
                                           ctypes.POINTER(vp), vp, vp]
@@ -141,7 +143,7 @@ def lib():
         L.vr_plan_samples.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
         L.vr_plan_destroy.argtypes = [vp]
         for f in ("vr_create", "vr_destroy", "vr_insert_block", "vr_insert_slice", "vr_set_transfer_functions",
-                  "vr_set_clip_planes", "vr_set_channel_transforms", "vr_render", "vr_render_backward", "vr_read_level", "vr_read_voxels", "vr_read_node", "vr_render_footprint",
+                  "vr_set_clip_planes", "vr_set_channel_transforms", "vr_render", "vr_render_backward", "vr_render_backward_with_images", "vr_read_level", "vr_read_voxels", "vr_read_node", "vr_render_footprint",
                   "vr_stats", "vr_set_tile_shape", "vr_set_launch_shape", "vr_set_tile_order", "vr_set_ray_continuation", "vr_set_mip_segment_length",
                   "vr_set_gradient_precision", "vr_plan_create",
                   "vr_plan_launch",
@@ -195,6 +197,7 @@ class Renderer:
             torch.cuda.set_device(torch.device(device))
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.dims, self.C, self.M = tuple(int(d) for d in dims), int(channels), int(brick)
+        self.precision = precision
         opt = Options(background, tau, pool_capacity_bytes, VR_FP16_INTERP if precision == "fp16" else VR_FP32,
                       cache_capacity_bytes, 1 if store_on_host else 0)
         # the callbacks live as long as the context
@@ -370,7 +373,10 @@ class Renderer:
 
         return [popcount(m) for m in marks], popcount(nodes)
 
-    def render_backward(self, cams, grads, dtf=None, dscale=None, stream=None):
+    def render_backward(self, cams, grads, dtf=None, dscale=None, stream=None, images=None):
+        """dL/d(tf, scale) for dL/dimage ``grads``.  ``images``: the FP32 DVR images render() gave
+        for the same cameras and state -- each ray is then marched once instead of twice
+        (vr_render_backward_with_images)."""
         import torch
 
         n = len(cams)
@@ -381,9 +387,17 @@ class Renderer:
             dtf = torch.empty((self.C, 256, 4), dtype=torch.float32, device=self.device)
         if dscale is None:
             dscale = torch.empty((self.C,), dtype=torch.float32, device=self.device)
-        self._check(lib().vr_render_backward(self._ctx, cs, n, ptrs, ctypes.c_void_p(dtf.data_ptr()),
-                                             ctypes.c_void_p(dscale.data_ptr()),
-                                             ctypes.c_void_p(_stream_ptr(stream))))
+        if images is None:
+            self._check(lib().vr_render_backward(self._ctx, cs, n, ptrs, ctypes.c_void_p(dtf.data_ptr()),
+                                                 ctypes.c_void_p(dscale.data_ptr()),
+                                                 ctypes.c_void_p(_stream_ptr(stream))))
+        else:
+            ims = [im.contiguous() for im in images]
+            iptrs = (ctypes.c_void_p * n)(*[im.data_ptr() for im in ims])
+            self._check(lib().vr_render_backward_with_images(self._ctx, cs, n, iptrs, ptrs,
+                                                             ctypes.c_void_p(dtf.data_ptr()),
+                                                             ctypes.c_void_p(dscale.data_ptr()),
+                                                             ctypes.c_void_p(_stream_ptr(stream))))
         return dtf, dscale
 
     # ---- inspection ----
@@ -525,19 +539,21 @@ def _torch_fn():
         @staticmethod
         def forward(ctx, tf, scale, renderer, cams):
             renderer.set_transfer_functions(tf.detach(), scale.detach())
-            imgs = renderer.render(cams)
+            imgs = renderer.render(cams, mode=VR_MODE_DVR)
             ctx.renderer, ctx.cams = renderer, cams
-            ctx.save_for_backward(tf, scale)
+            # FP32 images: the backward reads each ray's final colour and transmittance from them
+            ctx.fp32 = renderer.precision != "fp16"
+            ctx.save_for_backward(tf, scale, *imgs)
             return tuple(imgs)
 
         @staticmethod
         def backward(ctx, *grads):
-            tf, scale = ctx.saved_tensors
+            tf, scale, *imgs = ctx.saved_tensors
             r = ctx.renderer
             gs = [g if g is not None else torch.zeros((c["height"], c["width"], 4), device=r.device)
                   for g, c in zip(grads, ctx.cams)]
             r.set_transfer_functions(tf.detach(), scale.detach())
-            dtf, dsc = r.render_backward(ctx.cams, gs)
+            dtf, dsc = r.render_backward(ctx.cams, gs, images=imgs if ctx.fp32 else None)
             return dtf, dsc, None, None
 
     return RenderFn

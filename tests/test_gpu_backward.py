@@ -208,3 +208,46 @@ def test_differentiable_full_size_sampled_gradient():
     g = dtf.cpu().numpy()
     assert np.linalg.norm(g - rtf) <= 1e-3 * np.linalg.norm(rtf)
     assert np.linalg.norm(dsc.cpu().numpy() - rsc) <= 1e-3 * np.linalg.norm(rsc)
+
+
+def test_backward_from_forward_images():
+    """vr_render_backward_with_images: each ray's final colour and transmittance read from the
+    forward's image instead of a second march.  Equal to the re-marching adjoint up to the rounding
+    of 1 - alpha, and within the gradient tolerance of the oracle; also through the autograd
+    function (which passes its forward images)."""
+    import torch
+    import paper_1407_2074_b300 as vr
+
+    w, vol, r, cam = _setup(ert=0.99)
+    ov = oracle_dense(vol, 16)
+    tf = w.tf()
+    tf[..., 3] = np.minimum(1.0, tf[..., 3] * 4.0)
+    sc = np.array([1.0, 0.9, 1.1], np.float32)
+    dl = np.random.default_rng(4).normal(size=(cam["height"], cam["width"], 4)).astype(np.float32)
+    dl, rtf, rsc, _ = _oracle_grad_ert(ov, cam, tf, sc, dl)
+    r.set_transfer_functions(torch.from_numpy(tf), torch.from_numpy(sc))
+    fwd = r.render([cam])
+    g = [torch.from_numpy(dl).cuda()]
+    a_tf, a_sc = r.render_backward([cam], g)
+    b_tf, b_sc = r.render_backward([cam], g, images=fwd)
+    torch.cuda.synchronize()
+    a_tf, b_tf = a_tf.cpu().numpy().astype(np.float64), b_tf.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(a_tf - b_tf) <= 1e-5 * np.linalg.norm(a_tf)
+    assert np.abs(a_sc.cpu().numpy() - b_sc.cpu().numpy()).max() <= 1e-5 * np.abs(a_sc.cpu().numpy()).max()
+    _grad_close(b_tf, rtf, fp64=False)
+    _grad_close(b_sc.cpu().numpy(), rsc, fp64=False)
+    # the autograd path: d(sum dl * image) through RenderFn
+    tf_t = torch.from_numpy(tf).cuda().requires_grad_(True)
+    sc_t = torch.from_numpy(sc).cuda().requires_grad_(True)
+    img = vr.render(r, [cam], tf_t, sc_t)[0]
+    (img * g[0]).sum().backward()
+    torch.cuda.synchronize()
+    # (the sums use atomics: equal up to their order)
+    assert np.linalg.norm(tf_t.grad.cpu().numpy() - b_tf) <= 1e-6 * np.linalg.norm(b_tf)
+    # the FP64 check mode ignores the images (recomputes the double forward)
+    r.set_gradient_precision(True)
+    c_tf, _ = r.render_backward([cam], g, images=fwd)
+    torch.cuda.synchronize()
+    _grad_close(c_tf.cpu().numpy(), rtf, fp64=True)
+    r.set_gradient_precision(False)
+    r.close()
