@@ -298,6 +298,7 @@ vr_status vr_plan_create(vr_ctx* ctx, const vr_camera* cams, int n_cams, float* 
 vr_status vr_plan_launch(vr_render_plan* plan, void* cuda_stream);
 /* Samples composited and rays of the last replay (synchronises). */
 vr_status vr_plan_samples(vr_render_plan* plan, int64_t* samples, int64_t* rays);
+/* Destroys a plan; plans must be destroyed before their context (vr_destroy). */
 vr_status vr_plan_destroy(vr_render_plan* plan);
 
 /* Launch shape of the ray caster: warp tile tile_w x tile_h (product 32), threads per CTA (64, 128

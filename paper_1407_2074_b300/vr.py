@@ -210,6 +210,7 @@ class Renderer:
         if rc != VR_OK:
             raise VRError(rc, lib().vr_last_error(None).decode())
         self._ctx = h.value
+        self._plans = weakref.WeakSet()  # destroyed before the context (a plan refers to it)
         if _live is None:
             _live = weakref.WeakSet()
             atexit.register(_close_all)
@@ -223,6 +224,8 @@ class Renderer:
 
     def close(self):
         if self._ctx:
+            for p in list(getattr(self, "_plans", ())):
+                p.close()
             lib().vr_destroy(self._ctx)
             self._ctx = None
 
@@ -505,8 +508,10 @@ class RenderPlan:
         cs = (Camera * n)(*[camera_struct(c) for c in cams])
         ptrs = (ctypes.c_void_p * n)(*[im.data_ptr() for im in self.images])
         h = ctypes.c_void_p()
+        self._p = None
         renderer._check(lib().vr_plan_create(renderer.handle, cs, n, ptrs, mode, ctypes.byref(h)))
         self._p = h.value
+        renderer._plans.add(self)
 
     def launch(self, stream=None):
         self.r._check(lib().vr_plan_launch(self._p, ctypes.c_void_p(_stream_ptr(stream))))

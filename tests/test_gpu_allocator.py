@@ -51,3 +51,32 @@ def test_library_allocator_leaves_torch_alone():
     r.close()
     with pytest.raises(ValueError):
         vr.Renderer((64, 64, 64), 3, 16, allocator="cuda")
+
+
+def test_process_exit_with_live_renderer_and_plan(tmp_path):
+    """A script that leaves a Renderer and a render plan alive until the interpreter exits ends
+    cleanly: the contexts still open are destroyed at exit (their memory goes back to torch while
+    torch is still up), each after its plans."""
+    import subprocess
+    import sys
+
+    root = __import__("os").path.dirname(__import__("os").path.dirname(__file__))
+    script = tmp_path / "live.py"
+    script.write_text(
+        "import sys\n"
+        f"sys.path.insert(0, {root!r})\n"
+        "import numpy as np, torch\n"
+        "import paper_1407_2074_b300 as vr\n"
+        "from synth import synth as S\n"
+        "w = S.tiny()\n"
+        "r = vr.Renderer(w.dims, 3, 16)\n"
+        "r.insert_block((0, 0, 0), w.spec().volume())\n"
+        "r.set_transfer_functions(torch.from_numpy(w.tf()), torch.ones(3))\n"
+        "cam = dict(w.cameras[0], width=32, height=32)\n"
+        "p = r.plan([cam])\n"
+        "p.launch()\n"
+        "torch.cuda.synchronize()\n"
+        "print('ok')\n")
+    res = subprocess.run([sys.executable, str(script)], capture_output=True, text=True, timeout=300)
+    assert res.returncode == 0, res.stderr[-2000:]
+    assert res.stdout.strip().endswith("ok")
