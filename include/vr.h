@@ -301,8 +301,9 @@ vr_status vr_plan_samples(vr_render_plan* plan, int64_t* samples, int64_t* rays)
 /* Destroys a plan; plans must be destroyed before their context (vr_destroy). */
 vr_status vr_plan_destroy(vr_render_plan* plan);
 
-/* Launch shape of the ray caster: warp tile tile_w x tile_h (product 32), threads per CTA (64, 128
- * or 256) and CTAs per SM of the persistent grid.  Defaults 8 x 4, 256, 8. */
+/* Launch shape of the ray caster: warp tile tile_w x tile_h (product 32), threads per CTA (64, 128,
+ * 256, 512 or 768) and CTAs per SM of the persistent grid (up to 768 threads are resident per SM).
+ * Defaults 8 x 4, 768, 1: one CTA per SM keeps one copy of the transfer-function tables there. */
 vr_status vr_set_launch_shape(vr_ctx* ctx, int tile_w, int tile_h, int threads_per_cta, int ctas_per_sm);
 
 /* MIP ray segments (vr_render and render plans in VR_MODE_MIP that read the store directly, no

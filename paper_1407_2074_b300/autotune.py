@@ -10,6 +10,7 @@ import json
 import os
 
 CANDIDATES = [
+    (8, 4, 768, 1), (4, 8, 768, 1),
     (8, 4, 256, 8), (16, 2, 256, 8), (4, 8, 256, 8), (32, 1, 256, 8),
     (8, 4, 128, 16), (16, 2, 128, 16), (4, 8, 128, 16),
     (8, 4, 256, 2), (8, 4, 64, 32),

@@ -68,7 +68,7 @@ struct vr_ctx {
     int n_clip_default = 0;
     float clip_default[VR_MAX_CLIP][4] = {};
     int tile_w = 8, tile_h = 4;
-    int threads = 256, ctas_per_sm = 8; // render launch shape (autotuned per workload)
+    int threads = 768, ctas_per_sm = 1; // render launch shape (autotuned per workload)
     // tile queue order from the previous render of the same tile grid (costliest tiles first)
     int tile_order_mode = 1;
     // ray continuation (plain DVR): once the queue runs dry, rays with more than cont_min samples
@@ -1235,7 +1235,8 @@ vr_status vr_set_ray_continuation(vr_ctx* c, int lanes_per_ray, int min_samples_
 }
 
 vr_status vr_set_launch_shape(vr_ctx* c, int tw, int th, int threads, int ctas_per_sm) {
-    if (!c || tw <= 0 || th <= 0 || tw * th != 32 || (threads != 64 && threads != 128 && threads != 256) ||
+    if (!c || tw <= 0 || th <= 0 || tw * th != 32 ||
+        (threads != 64 && threads != 128 && threads != 256 && threads != 512 && threads != 768) ||
         ctas_per_sm < 1 || ctas_per_sm > 32)
         return VR_ERR_INVALID_ARG;
     c->tile_w = tw;

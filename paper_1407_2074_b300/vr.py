@@ -308,7 +308,7 @@ class Renderer:
     def set_tile_shape(self, tw, th):
         self._check(lib().vr_set_tile_shape(self._ctx, tw, th))
 
-    def set_launch_shape(self, tw, th, threads=256, ctas_per_sm=8):
+    def set_launch_shape(self, tw, th, threads=768, ctas_per_sm=1):
         self._check(lib().vr_set_launch_shape(self._ctx, tw, th, threads, ctas_per_sm))
 
     def set_mip_segment_length(self, samples):
