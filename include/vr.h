@@ -329,6 +329,18 @@ vr_status vr_set_mip_segment_length(vr_ctx* ctx, int samples);
  * measured slower there).  Not part of the paper's method. */
 vr_status vr_set_tile_order(vr_ctx* ctx, int mode);
 
+/* How level 0 of an insert reads the block (Sec. "Incremental Construction", step 2: the
+ * inserted voxels are copied into the level-0 bricks).  1 (default): the rows of each brick slot's
+ * changed planes are staged in shared memory by bulk tensor copies (TMA), one copy per plane,
+ * when the block allows it: its base address and its row pitch (extent[0] x channels x 2 bytes)
+ * multiples of 16 bytes, and the brick edge small enough for one copy box ((M + 2) x channels + 7
+ * elements and M + 2 rows, each at most 256); other blocks take the per-thread loads.  0: always
+ * the per-thread loads.  The tree is the same bit for bit either way.  A staged copy that has not
+ * landed after about two seconds sets device error bit 4 (read back as VR_ERR_DEVICE_ASSERT by
+ * the next call that polls it) instead of waiting forever.  Errors: VR_ERR_INVALID_ARG (NULL
+ * context, mode not 0 or 1). */
+vr_status vr_set_insert_staging(vr_ctx* ctx, int mode);
+
 /* Ray continuation of vr_render (DVR, FP32 or FP16, reading the store directly with no
  * per-channel transforms).  Early ray termination makes ray lengths very uneven: once the ray-tile
  * queue has run dry, the rest of a frame is a tail in which a few warps march the longest rays

@@ -71,6 +71,7 @@ struct vr_ctx {
     int threads = 768, ctas_per_sm = 1; // render launch shape (autotuned per workload)
     // tile queue order from the previous render of the same tile grid (costliest tiles first)
     int tile_order_mode = 1;
+    int insert_staging = 1; // level 0 of an insert reads the block through TMA-staged rows when it can
     // ray continuation (plain DVR): once the queue runs dry, rays with more than cont_min samples
     // left are finished by a second launch with 2^cont_lg lanes per ray (cont_lg < 0: off)
     int cont_lg = 4;
@@ -559,7 +560,8 @@ vr_status vr_insert_block(vr_ctx* c, const int64_t origin[3], const int64_t exte
     // measured slower (228 vs 84 us on the 24 GiB workload): a CTA that completes several parents
     // updates them one after another, and one slot's update already takes ~13 us.
     for (int L = 0; L <= g.N; ++L) {
-        CK(c, launch_level_update(g, L, lo[L], hi[L], src, org, ext, c->pool, c->rn, c->ns, c->ps, c->err, st));
+        CK(c, launch_level_update(g, L, lo[L], hi[L], src, org, ext, c->pool, c->rn, c->ns, c->ps, c->err, st,
+                                  c->insert_staging != 0));
         if (L == 0 && up >= 0) CK(c, cudaEventRecord(c->stage_free[up], st));
     }
     if (c->cache_cap > 0) {
@@ -1220,6 +1222,12 @@ vr_status vr_set_tile_order(vr_ctx* c, int mode) {
     if (!c || (mode != 0 && mode != 1)) return VR_ERR_INVALID_ARG;
     c->tile_order_mode = mode;
     c->lpt_have = false;
+    return VR_OK;
+}
+
+vr_status vr_set_insert_staging(vr_ctx* c, int mode) {
+    if (!c || (mode != 0 && mode != 1)) return VR_ERR_INVALID_ARG;
+    c->insert_staging = mode;
     return VR_OK;
 }
 

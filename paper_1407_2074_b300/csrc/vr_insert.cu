@@ -15,6 +15,7 @@
 //           launch), homogeneity (max - min < tau in every channel) and the render record.
 // The launches are ordered on the caller's stream; level L reads only level L-1 and its own
 // slot, so the result is independent of scheduling.
+#include <cuda.h> // CUtensorMap and its enums; the encoder is fetched from the driver at run time
 #include <cuda_runtime.h>
 
 #include "vr_internal.h"
@@ -207,6 +208,142 @@ __device__ __forceinline__ void half_sample(const LevelArgs& a, int L, int x, in
     for (int c = 0; c < C; ++c) v[c] = (uint16_t)rhu_pow2(sum[c], ksh);
 }
 
+// After a slot's positions are written: the plane statistics of its changed interior planes
+// (gathered while writing, or re-read), then the node's finalize in warp 0.
+template <int C, int VS>
+__device__ __forceinline__ void finish_slot(const LevelArgs& a, const long long (&b)[3], long long nid, int slot,
+                                            const uint16_t* dst, const int (&l0)[3], const int (&l1)[3],
+                                            const int (&nin)[3], bool interior, bool full_xy, bool gather,
+                                            uint32_t (*s_pmn)[C], uint32_t (*s_pmx)[C], uint32_t (*s_psm)[C]) {
+    const Geo& g = a.g;
+    const int L = a.L, M = g.M, S = g.S;
+    if (gather) {
+        __syncthreads();
+        const int pz0 = l0[2] > 1 ? l0[2] : 1, pz1 = l1[2] < nin[2] ? l1[2] : nin[2];
+        for (int i = threadIdx.x; i < (pz1 - pz0 + 1) * C; i += blockDim.x) {
+            const int lz = pz0 + i / C, c = i % C;
+            PStat p;
+            p.mn = (uint16_t)s_pmn[lz][c];
+            p.mx = (uint16_t)s_pmx[lz][c];
+            p.sum = s_psm[lz][c];
+            a.ps[((long long)slot * M + (lz - 1)) * C + c] = p;
+        }
+    }
+    if (!interior) return; // only border copies changed: the node's own statistics did not
+    if (!full_xy) {
+        __syncthreads();
+        // per-plane statistics of the changed interior planes, re-read (in-volume voxels only)
+        const int pz0 = l0[2] > 1 ? l0[2] : 1, pz1 = l1[2] < M ? l1[2] : M;
+        for (int lz = pz0; lz <= pz1; ++lz) {
+            if (lz > nin[2]) break; // plane beyond the real extent: unused
+            uint32_t mn[C], mx[C];
+            unsigned long long sm[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                mn[c] = 0xffffu;
+                mx[c] = 0;
+                sm[c] = 0;
+            }
+            const int npl = nin[0] * nin[1];
+            for (int t = threadIdx.x; t < npl; t += blockDim.x) {
+                const int ty = t / nin[0];
+                const int lx = 1 + (t - ty * nin[0]), ly = 1 + ty;
+                const uint16_t* q = dst + ((lz * S + ly) * S + lx) * VS;
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    const uint32_t val = q[c];
+                    mn[c] = min(mn[c], val);
+                    mx[c] = max(mx[c], val);
+                    sm[c] += val;
+                }
+            }
+            block_reduce_stats<C>(mn, mx, sm);
+            if (threadIdx.x == 0) {
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    PStat p;
+                    p.mn = (uint16_t)mn[c];
+                    p.mx = (uint16_t)mx[c];
+                    p.sum = (uint32_t)sm[c];
+                    a.ps[((long long)slot * M + (lz - 1)) * C + c] = p;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x >= 32) return;
+    // finalize the node in warp 0 (Sec. "CPU Data Structure": homogeneity, AVG; all channels must
+    // be homogeneous, Sec. "Handling Multi-Channel Data").  Lane l reads the plane statistics of
+    // planes l, l+32, ... and lane l < 8 the subtree statistics of child l; warp reductions.
+    const int lane = threadIdx.x;
+    uint32_t bmn[C], bmx[C], cmn[C], cmx[C];
+    unsigned long long bsm[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        bmn[c] = cmn[c] = 0xffffu;
+        bmx[c] = cmx[c] = 0u;
+        bsm[c] = 0ull;
+    }
+    for (int lz = 1 + lane; lz <= nin[2]; lz += 32) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const PStat p = a.ps[((long long)slot * M + (lz - 1)) * C + c];
+            bmn[c] = min(bmn[c], (uint32_t)p.mn);
+            bmx[c] = max(bmx[c], (uint32_t)p.mx);
+            bsm[c] += p.sum;
+        }
+    }
+    if (L > 0 && lane < 8) {
+        const long long ci = 2 * b[0] + (lane & 1), cj = 2 * b[1] + ((lane >> 1) & 1), ck = 2 * b[2] + (lane >> 2);
+        if (ci < g.nb[L - 1][0] && cj < g.nb[L - 1][1] && ck < g.nb[L - 1][2]) {
+            const long long cn = g.noff[L - 1] + (ck * g.nb[L - 1][1] + cj) * g.nb[L - 1][0] + ci;
+            const bool t = (a.rn[cn].flags & F_TOUCHED) != 0;
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                cmn[c] = t ? (uint32_t)a.ns[cn].smin[c] : (uint32_t)g.bg;
+                cmx[c] = t ? (uint32_t)a.ns[cn].smax[c] : (uint32_t)g.bg;
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        for (int o = 16; o > 0; o >>= 1) {
+            bmn[c] = min(bmn[c], __shfl_xor_sync(0xffffffffu, bmn[c], o));
+            bmx[c] = max(bmx[c], __shfl_xor_sync(0xffffffffu, bmx[c], o));
+            bsm[c] += __shfl_xor_sync(0xffffffffu, bsm[c], o);
+            cmn[c] = min(cmn[c], __shfl_xor_sync(0xffffffffu, cmn[c], o));
+            cmx[c] = max(cmx[c], __shfl_xor_sync(0xffffffffu, cmx[c], o));
+        }
+    }
+    if (lane != 0) return;
+    NStat s;
+    bool bh = true, sh = true;
+    s.count = nin[0] * nin[1] * nin[2];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        s.bmin[c] = (uint16_t)bmn[c];
+        s.bmax[c] = (uint16_t)bmx[c];
+        s.bsum[c] = bsm[c];
+        const uint32_t smn = (L > 0) ? cmn[c] : bmn[c];
+        const uint32_t smx = (L > 0) ? cmx[c] : bmx[c];
+        s.smin[c] = (uint16_t)smn;
+        s.smax[c] = (uint16_t)smx;
+        if (!((int)bmx[c] - (int)bmn[c] < (int)g.tau)) bh = false;
+        if (!((int)smx - (int)smn < (int)g.tau)) sh = false;
+    }
+    for (int c = C; c < MAXC; ++c) {
+        s.bmin[c] = s.bmax[c] = s.smin[c] = s.smax[c] = 0;
+        s.bsum[c] = 0;
+    }
+    a.ns[nid] = s;
+    RNode r;
+    r.slot = slot;
+    r.flags = F_TOUCHED | ((L > 0 && !sh) ? F_CHILDREN : 0u) | (!bh ? F_BRICK : 0u);
+    for (int c = 0; c < 4; ++c)
+        r.avg[c] = (c < C) ? rhu(s.bsum[c], (unsigned long long)s.count) : (uint16_t)0;
+    a.rn[nid] = r;
+}
+
 template <int C, int VS, bool LEVEL0, bool WIDE = false>
 __global__ void __launch_bounds__(WIDE ? 1024 : 256) level_update_kernel(LevelArgs a) {
     const Geo& g = a.g;
@@ -340,131 +477,195 @@ __global__ void __launch_bounds__(WIDE ? 1024 : 256) level_update_kernel(LevelAr
             }
         }
     }
-    if (gather) {
-        __syncthreads();
-        const int pz0 = l0[2] > 1 ? l0[2] : 1, pz1 = l1[2] < nin[2] ? l1[2] : nin[2];
-        for (int i = threadIdx.x; i < (pz1 - pz0 + 1) * C; i += blockDim.x) {
-            const int lz = pz0 + i / C, c = i % C;
-            PStat p;
-            p.mn = (uint16_t)s_pmn[lz][c];
-            p.mx = (uint16_t)s_pmx[lz][c];
-            p.sum = s_psm[lz][c];
-            a.ps[((long long)slot * M + (lz - 1)) * C + c] = p;
-        }
+    finish_slot<C, VS>(a, b, nid, slot, dst, l0, l1, nin, interior, full_xy, gather, s_pmn, s_pmx, s_psm);
+}
+
+// ---- level 0 with the block's rows staged in shared memory by the tensor memory accelerator ----
+//
+// One CTA per level-0 slot as above.  For each chunk of up to `pb_max` changed planes, thread 0
+// issues one bulk tensor copy per plane: the box of bw x bh elements of the block that holds the
+// plane's (M+2)^2 clamped positions, its x origin rounded down to a 16-byte boundary (the copy's
+// alignment rule); positions past the block's end read zeros that no position uses.  The CTA
+// waits on one mbarrier (bounded), then each warp converts one plane (or its share of one) from
+// shared memory into 8-byte slot voxels, gathering that plane's statistics in registers.
+
+constexpr long long COPY_WAIT_CYCLES = 4000000000ll; // ~2 s at 2 GHz: a copy that never lands
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// true once the barrier's phase `parity` has completed; false after COPY_WAIT_CYCLES
+__device__ __forceinline__ bool wait_phase(uint32_t bar, uint32_t parity) {
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > COPY_WAIT_CYCLES) return false;
     }
-    if (!interior) return; // only border copies changed: the node's own statistics did not
-    if (!full_xy) {
-        __syncthreads();
-        // per-plane statistics of the changed interior planes, re-read (in-volume voxels only)
-        const int pz0 = l0[2] > 1 ? l0[2] : 1, pz1 = l1[2] < M ? l1[2] : M;
-        for (int lz = pz0; lz <= pz1; ++lz) {
-            if (lz > nin[2]) break; // plane beyond the real extent: unused
-            uint32_t mn[C], mx[C];
-            unsigned long long sm[C];
+}
+
+template <int C, int VS>
+__global__ void __launch_bounds__(256) level0_staged_kernel(LevelArgs a, const __grid_constant__ CUtensorMap tm,
+                                                            int bw, int bh, int plane_bytes, int pb_max) {
+    extern __shared__ __align__(128) unsigned char s_dyn[];
+    __shared__ __align__(8) unsigned long long s_bar;
+    // the copies' destinations on a 128-byte boundary (the launch adds 128 bytes of slack)
+    unsigned char* const s_box = s_dyn + ((128u - (smem_u32(s_dyn) & 127u)) & 127u);
+    __shared__ uint32_t s_pmn[MAX_S][C], s_pmx[MAX_S][C], s_psm[MAX_S][C];
+    const Geo& g = a.g;
+    const int M = g.M, S = g.S;
+    long long bb = blockIdx.x;
+    long long b[3];
+    b[0] = a.blo[0] + bb % a.bn[0];
+    bb /= a.bn[0];
+    b[1] = a.blo[1] + bb % a.bn[1];
+    b[2] = a.blo[2] + bb / a.bn[1];
+    const long long nid = g.noff[0] + (b[2] * g.nb[0][1] + b[1]) * g.nb[0][0] + b[0];
+    const int slot = a.rn[nid].slot;
+    if (slot < 0) return;
+    if (slot >= g.n_slots_cap) {
+        if (threadIdx.x == 0) atomicOr(a.err, ERR_SLOT_RANGE);
+        return;
+    }
+    int l0[3], l1[3];
+    bool interior = true;
+    for (int d = 0; d < 3; ++d) {
+        long long base = b[d] * M - 1, ext = g.ldim[0][d];
+        long long s0 = (a.lo[d] == 0) ? 0 : a.lo[d] - base;
+        long long s1 = (a.hi[d] == ext - 1) ? S - 1 : a.hi[d] - base;
+        if (s0 < 0) s0 = 0;
+        if (s1 > S - 1) s1 = S - 1;
+        l0[d] = (int)s0;
+        l1[d] = (int)s1;
+        if (s0 > s1) return;
+        interior = interior && (b[d] * M <= a.hi[d]) && (b[d] * M + M - 1 >= a.lo[d]);
+    }
+    uint16_t* dst = a.pool + (long long)slot * g.slot_elems;
+    const int nx = l1[0] - l0[0] + 1, ny = l1[1] - l0[1] + 1;
+    const int np = nx * ny;
+    int nin[3];
+    for (int d = 0; d < 3; ++d) {
+        const long long r = g.ldim[0][d] - b[d] * M;
+        nin[d] = (int)(r < M ? r : M);
+    }
+    const bool full_xy = l0[0] <= 1 && l1[0] >= nin[0] && l0[1] <= 1 && l1[1] >= nin[1];
+    const bool gather = interior && full_xy;
+    const uint32_t bar = smem_u32(&s_bar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (gather)
+        for (int i = threadIdx.x; i < S * C; i += blockDim.x) {
+            s_pmn[i / C][i % C] = 0xffffu;
+            s_pmx[i / C][i % C] = 0u;
+            s_psm[i / C][i % C] = 0u;
+        }
+    __syncthreads();
+    const int bx0 = (int)(b[0] * M) - 1, by0 = (int)(b[1] * M) - 1, bz0 = (int)(b[2] * M) - 1;
+    const int X = (int)g.ldim[0][0], Y = (int)g.ldim[0][1], Z = (int)g.ldim[0][2];
+    const int ox = (int)a.org[0], oy = (int)a.org[1], oz = (int)a.org[2];
+    // the box: rows from the first position's clamped y, elements from its clamped x (times C)
+    // rounded down to a multiple of 8 (16 bytes)
+    const int ya = clampi(by0 + l0[1], 0, Y - 1);
+    const int ex = ((clampi(bx0 + l0[0], 0, X - 1) - ox) * C) & ~7;
+    const uint32_t mnx = nx > 1 ? (uint32_t)((0x100000000ull + (unsigned)nx - 1) / (unsigned)nx) : 0u;
+    const int nw = (int)(blockDim.x >> 5), w = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
+    constexpr int U = 4;
+    uint32_t parity = 0;
+    for (int pz0 = l0[2]; pz0 <= l1[2]; pz0 += pb_max) {
+        const int pb = min(pb_max, l1[2] - pz0 + 1);
+        if (threadIdx.x == 0) {
+            // the previous chunk's reads of these buffers (ordered by the barrier below) come first
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(pb * bw * bh * 2)
+                         : "memory");
+            for (int p = 0; p < pb; ++p) {
+                const int z = clampi(bz0 + pz0 + p, 0, Z - 1) - oz;
+                asm volatile(
+                    "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                    ::"r"(smem_u32(s_box + p * plane_bytes)), "l"(reinterpret_cast<unsigned long long>(&tm)), "r"(ex),
+                      "r"(ya - oy), "r"(z), "r"(bar)
+                    : "memory");
+            }
+        }
+        const bool late = !wait_phase(bar, parity);
+        parity ^= 1u;
+        if (__syncthreads_or(late)) {
+            if (threadIdx.x == 0) atomicOr(a.err, ERR_COPY_TIMEOUT);
+            return;
+        }
+        // warps to planes: gw warps share one plane when the chunk has fewer planes than warps
+        const int gw = pb >= nw ? 1 : nw / pb;
+        for (int p = w / gw; p < pb; p += nw / gw) {
+            const int lz = pz0 + p;
+            const bool stats_here = gather && lz >= 1 && lz <= nin[2];
+            const uint16_t* sp = reinterpret_cast<const uint16_t*>(s_box + p * plane_bytes);
+            uint32_t mn[C], mx[C], sm32[C];
 #pragma unroll
             for (int c = 0; c < C; ++c) {
                 mn[c] = 0xffffu;
                 mx[c] = 0;
-                sm[c] = 0;
+                sm32[c] = 0;
             }
-            const int npl = nin[0] * nin[1];
-            for (int t = threadIdx.x; t < npl; t += blockDim.x) {
-                const int ty = t / nin[0];
-                const int lx = 1 + (t - ty * nin[0]), ly = 1 + ty;
-                const uint16_t* q = dst + ((lz * S + ly) * S + lx) * VS;
+            const int stride = gw * 32;
+            for (int t0 = (w % gw) * 32 + lane; t0 < np; t0 += U * stride) {
 #pragma unroll
-                for (int c = 0; c < C; ++c) {
-                    const uint32_t val = q[c];
-                    mn[c] = min(mn[c], val);
-                    mx[c] = max(mx[c], val);
-                    sm[c] += val;
+                for (int u = 0; u < U; ++u) {
+                    const int t = t0 + u * stride;
+                    if (t >= np) break;
+                    const int ty = nx > 1 ? (int)__umulhi((uint32_t)t, mnx) : t;
+                    const int lx = l0[0] + (t - ty * nx), ly = l0[1] + ty;
+                    const int x = clampi(bx0 + lx, 0, X - 1), y = clampi(by0 + ly, 0, Y - 1);
+                    const uint16_t* q = sp + (y - ya) * bw + ((x - ox) * C - ex);
+                    uint16_t v[VS];
+#pragma unroll
+                    for (int c = 0; c < VS; ++c) v[c] = c < C ? q[c] : (uint16_t)0;
+                    uint16_t* d = dst + ((lz * S + ly) * S + lx) * VS;
+                    if (VS == 4) {
+                        uint2 wv;
+                        wv.x = (uint32_t)v[0] | ((uint32_t)v[VS > 1 ? 1 : 0] << 16);
+                        wv.y = (uint32_t)v[VS > 2 ? 2 : 0] | ((uint32_t)v[VS > 3 ? 3 : 0] << 16);
+                        *reinterpret_cast<uint2*>(d) = wv;
+                    } else if (VS == 2) {
+                        *reinterpret_cast<uint32_t*>(d) = (uint32_t)v[0] | ((uint32_t)v[VS > 1 ? 1 : 0] << 16);
+                    } else {
+                        d[0] = v[0];
+                    }
+                    if (stats_here && lx >= 1 && lx <= nin[0] && ly >= 1 && ly <= nin[1]) {
+#pragma unroll
+                        for (int c = 0; c < C; ++c) {
+                            mn[c] = min(mn[c], (uint32_t)v[c]);
+                            mx[c] = max(mx[c], (uint32_t)v[c]);
+                            sm32[c] += v[c];
+                        }
+                    }
                 }
             }
-            block_reduce_stats<C>(mn, mx, sm);
-            if (threadIdx.x == 0) {
+            if (stats_here) {
 #pragma unroll
                 for (int c = 0; c < C; ++c) {
-                    PStat p;
-                    p.mn = (uint16_t)mn[c];
-                    p.mx = (uint16_t)mx[c];
-                    p.sum = (uint32_t)sm[c];
-                    a.ps[((long long)slot * M + (lz - 1)) * C + c] = p;
+                    const uint32_t wmn = __reduce_min_sync(0xffffffffu, mn[c]);
+                    const uint32_t wmx = __reduce_max_sync(0xffffffffu, mx[c]);
+                    const uint32_t wsm = __reduce_add_sync(0xffffffffu, sm32[c]);
+                    if (lane == 0) {
+                        atomicMin(&s_pmn[lz][c], wmn);
+                        atomicMax(&s_pmx[lz][c], wmx);
+                        atomicAdd(&s_psm[lz][c], wsm);
+                    }
                 }
             }
         }
+        // every warp is done with this chunk's planes before the next chunk's copies land
+        __syncthreads();
     }
-    __syncthreads();
-    if (threadIdx.x >= 32) return;
-    // finalize the node in warp 0 (Sec. "CPU Data Structure": homogeneity, AVG; all channels must
-    // be homogeneous, Sec. "Handling Multi-Channel Data").  Lane l reads the plane statistics of
-    // planes l, l+32, ... and lane l < 8 the subtree statistics of child l; warp reductions.
-    const int lane = threadIdx.x;
-    uint32_t bmn[C], bmx[C], cmn[C], cmx[C];
-    unsigned long long bsm[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-        bmn[c] = cmn[c] = 0xffffu;
-        bmx[c] = cmx[c] = 0u;
-        bsm[c] = 0ull;
-    }
-    for (int lz = 1 + lane; lz <= nin[2]; lz += 32) {
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-            const PStat p = a.ps[((long long)slot * M + (lz - 1)) * C + c];
-            bmn[c] = min(bmn[c], (uint32_t)p.mn);
-            bmx[c] = max(bmx[c], (uint32_t)p.mx);
-            bsm[c] += p.sum;
-        }
-    }
-    if (L > 0 && lane < 8) {
-        const long long ci = 2 * b[0] + (lane & 1), cj = 2 * b[1] + ((lane >> 1) & 1), ck = 2 * b[2] + (lane >> 2);
-        if (ci < g.nb[L - 1][0] && cj < g.nb[L - 1][1] && ck < g.nb[L - 1][2]) {
-            const long long cn = g.noff[L - 1] + (ck * g.nb[L - 1][1] + cj) * g.nb[L - 1][0] + ci;
-            const bool t = (a.rn[cn].flags & F_TOUCHED) != 0;
-#pragma unroll
-            for (int c = 0; c < C; ++c) {
-                cmn[c] = t ? (uint32_t)a.ns[cn].smin[c] : (uint32_t)g.bg;
-                cmx[c] = t ? (uint32_t)a.ns[cn].smax[c] : (uint32_t)g.bg;
-            }
-        }
-    }
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-        for (int o = 16; o > 0; o >>= 1) {
-            bmn[c] = min(bmn[c], __shfl_xor_sync(0xffffffffu, bmn[c], o));
-            bmx[c] = max(bmx[c], __shfl_xor_sync(0xffffffffu, bmx[c], o));
-            bsm[c] += __shfl_xor_sync(0xffffffffu, bsm[c], o);
-            cmn[c] = min(cmn[c], __shfl_xor_sync(0xffffffffu, cmn[c], o));
-            cmx[c] = max(cmx[c], __shfl_xor_sync(0xffffffffu, cmx[c], o));
-        }
-    }
-    if (lane != 0) return;
-    NStat s;
-    bool bh = true, sh = true;
-    s.count = nin[0] * nin[1] * nin[2];
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-        s.bmin[c] = (uint16_t)bmn[c];
-        s.bmax[c] = (uint16_t)bmx[c];
-        s.bsum[c] = bsm[c];
-        const uint32_t smn = (L > 0) ? cmn[c] : bmn[c];
-        const uint32_t smx = (L > 0) ? cmx[c] : bmx[c];
-        s.smin[c] = (uint16_t)smn;
-        s.smax[c] = (uint16_t)smx;
-        if (!((int)bmx[c] - (int)bmn[c] < (int)g.tau)) bh = false;
-        if (!((int)smx - (int)smn < (int)g.tau)) sh = false;
-    }
-    for (int c = C; c < MAXC; ++c) {
-        s.bmin[c] = s.bmax[c] = s.smin[c] = s.smax[c] = 0;
-        s.bsum[c] = 0;
-    }
-    a.ns[nid] = s;
-    RNode r;
-    r.slot = slot;
-    r.flags = F_TOUCHED | ((L > 0 && !sh) ? F_CHILDREN : 0u) | (!bh ? F_BRICK : 0u);
-    for (int c = 0; c < 4; ++c)
-        r.avg[c] = (c < C) ? rhu(s.bsum[c], (unsigned long long)s.count) : (uint16_t)0;
-    a.rn[nid] = r;
+    finish_slot<C, VS>(a, b, nid, slot, dst, l0, l1, nin, interior, full_xy, gather, s_pmn, s_pmx, s_psm);
 }
 
 template <int C, int VS>
@@ -481,9 +682,66 @@ static void launch_level(const LevelArgs& a, bool level0, long long nblocks, cud
     }
 }
 
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+constexpr int STAGE_SMEM_MAX = 64 * 1024; // staged planes of one level-0 CTA (+ 128 bytes of alignment slack)
+constexpr int STAGE_PLANES_MAX = 8;
+
+// Level 0 through level0_staged_kernel when the block allows it: base and rows 16-byte aligned,
+// and the box of one slot plane within the copy engine's 256-element box limit.  Returns false
+// (nothing launched) otherwise.
+template <int C, int VS>
+static bool launch_level0_staged(const LevelArgs& a, long long nblocks, cudaStream_t st, cudaError_t* e) {
+    const Geo& g = a.g;
+    const int S = g.S;
+    const int bw = ((S * C + 7) + 7) & ~7, bh = S;
+    const unsigned long long row = (unsigned long long)a.ext[0] * C * sizeof(uint16_t);
+    if (bw > 256 || bh > 256 || ((uintptr_t)a.block & 15u) != 0 || (row & 15u) != 0) return false;
+    const int plane_bytes = (bw * bh * 2 + 127) & ~127;
+    int pb_max = STAGE_SMEM_MAX / plane_bytes;
+    if (pb_max > STAGE_PLANES_MAX) pb_max = STAGE_PLANES_MAX;
+    if (pb_max < 1) return false;
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return false;
+    CUtensorMap tm;
+    const cuuint64_t dims[3] = {(cuuint64_t)a.ext[0] * C, (cuuint64_t)a.ext[1], (cuuint64_t)a.ext[2]};
+    const cuuint64_t strides[2] = {row, row * (cuuint64_t)a.ext[1]};
+    const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, 1u};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, const_cast<uint16_t*>(a.block), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    const int smem = pb_max * plane_bytes + 128;
+    *e = cudaFuncSetAttribute(level0_staged_kernel<C, VS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (*e != cudaSuccess) return true;
+    level0_staged_kernel<C, VS><<<(unsigned)nblocks, 256, smem, st>>>(a, tm, bw, bh, plane_bytes, pb_max);
+    *e = cudaGetLastError();
+    return true;
+}
+
 cudaError_t launch_level_update(const Geo& g, int L, const long long lo[3], const long long hi[3],
                                 const uint16_t* block, const long long org[3], const long long ext[3], uint16_t* pool,
-                                RNode* rn, NStat* ns, PStat* ps, int* err, cudaStream_t st) {
+                                RNode* rn, NStat* ns, PStat* ps, int* err, cudaStream_t st, bool stage_rows) {
     LevelArgs a;
     a.g = g;
     a.L = L;
@@ -514,6 +772,17 @@ cudaError_t launch_level_update(const Geo& g, int L, const long long lo[3], cons
     a.err = err;
     if (nblocks <= 0) return cudaSuccess;
     if (nblocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    if (L == 0 && stage_rows) {
+        cudaError_t e = cudaSuccess;
+        bool done = false;
+        switch (g.C) {
+            case 1: done = launch_level0_staged<1, 1>(a, nblocks, st, &e); break;
+            case 2: done = launch_level0_staged<2, 2>(a, nblocks, st, &e); break;
+            case 3: done = launch_level0_staged<3, 4>(a, nblocks, st, &e); break;
+            default: done = launch_level0_staged<4, 4>(a, nblocks, st, &e); break;
+        }
+        if (done) return e;
+    }
     switch (g.C) {
         case 1: launch_level<1, 1>(a, L == 0, nblocks, st); break;
         case 2: launch_level<2, 2>(a, L == 0, nblocks, st); break;

@@ -55,7 +55,7 @@ struct Geo {
 };
 
 // Error word bits set by kernels (never trap).
-enum : int { ERR_SLOT_RANGE = 1, ERR_NODE_RANGE = 2 };
+enum : int { ERR_SLOT_RANGE = 1, ERR_NODE_RANGE = 2, ERR_COPY_TIMEOUT = 4 };
 
 struct SlotInit {
     long long node; // global node index
@@ -140,7 +140,7 @@ cudaError_t launch_slot_init(const Geo& g, uint16_t* pool, RNode* rn, PStat* ps,
                              cudaStream_t st);
 cudaError_t launch_level_update(const Geo& g, int L, const long long lo[3], const long long hi[3],
                                 const uint16_t* block, const long long org[3], const long long ext[3], uint16_t* pool,
-                                RNode* rn, NStat* ns, PStat* ps, int* err, cudaStream_t st);
+                                RNode* rn, NStat* ns, PStat* ps, int* err, cudaStream_t st, bool stage_rows = true);
 cudaError_t launch_read_level(const Geo& g, int L, const uint16_t* pool, const RNode* rn, uint16_t* out,
                               cudaStream_t st);
 cudaError_t launch_read_voxels(const Geo& g, int L, const uint16_t* pool, const RNode* rn, const long long* xyz,

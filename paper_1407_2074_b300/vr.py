@@ -134,6 +134,7 @@ def lib():
         L.vr_refine_end.argtypes = [vp]
         L.vr_set_launch_shape.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.vr_set_tile_order.argtypes = [vp, ctypes.c_int]
+        L.vr_set_insert_staging.argtypes = [vp, ctypes.c_int]
         L.vr_set_ray_continuation.argtypes = [vp, ctypes.c_int, ctypes.c_int]
         L.vr_set_gradient_precision.argtypes = [vp, ctypes.c_int]
         L.vr_set_mip_segment_length.argtypes = [vp, ctypes.c_int]
@@ -144,7 +145,7 @@ def lib():
         L.vr_plan_destroy.argtypes = [vp]
         for f in ("vr_create", "vr_destroy", "vr_insert_block", "vr_insert_slice", "vr_set_transfer_functions",
                   "vr_set_clip_planes", "vr_set_channel_transforms", "vr_render", "vr_render_backward", "vr_render_backward_with_images", "vr_read_level", "vr_read_voxels", "vr_read_node", "vr_render_footprint",
-                  "vr_stats", "vr_set_tile_shape", "vr_set_launch_shape", "vr_set_tile_order", "vr_set_ray_continuation", "vr_set_mip_segment_length",
+                  "vr_stats", "vr_set_tile_shape", "vr_set_launch_shape", "vr_set_tile_order", "vr_set_insert_staging", "vr_set_ray_continuation", "vr_set_mip_segment_length",
                   "vr_set_gradient_precision", "vr_plan_create",
                   "vr_plan_launch",
                   "vr_cache_update", "vr_cache_load", "vr_cache_read", "vr_refine_begin", "vr_refine_pass",
@@ -322,6 +323,11 @@ class Renderer:
     def set_tile_order(self, mode):
         """0: raster tile queue; 1 (default): costliest tiles of the previous render of the same grid first."""
         self._check(lib().vr_set_tile_order(self._ctx, mode))
+
+    def set_insert_staging(self, mode):
+        """1 (default): level 0 of an insert stages the block's rows in shared memory by TMA copies
+        when the block is 16-byte aligned; 0: per-thread loads.  Same tree either way."""
+        self._check(lib().vr_set_insert_staging(self._ctx, mode))
 
     def set_ray_continuation(self, lanes_per_ray=16, min_samples_left=32):
         """Once the tile queue runs dry, finish rays with more than ``min_samples_left`` samples to go

@@ -84,6 +84,53 @@ def test_random_order_blocks_and_overwrites(C, M, dims):
     _compare_state(r, oracle_dense(vol, M, bg=123, tau=600))
 
 
+@pytest.mark.parametrize("C,M,dims", [(3, 32, (96, 72, 80)), (3, 64, (136, 72, 70)), (4, 16, (40, 24, 17)),
+                                      (1, 8, (48, 20, 9)), (2, 8, (36, 20, 12))])
+def test_staged_level0_matches_per_thread_loads(C, M, dims):
+    """Level 0 through rows staged in shared memory by bulk tensor copies and through per-thread
+    loads build the same tree, equal to the oracle's: a whole-volume block (up to M + 2 planes per
+    slot: several staged chunks; M = 64 holds two planes per chunk), sub-boxes whose rows are or are
+    not 16-byte aligned (the latter take the per-thread loads), a device block at a base address
+    off the 16-byte grid, then 8-slice slabs over the whole volume."""
+    import torch
+
+    spec = S.VolumeSpec(S.KIND_SPIM, dims, C, 40, seed=9)
+    vol = spec.volume()
+    X, Y, Z = dims
+    rng = np.random.default_rng(C * 1000 + M)
+    junk = rng.integers(0, 65535, size=vol.shape, dtype=np.uint16)
+    boxes = []
+    for q in range(8):
+        o = [int(rng.integers(0, d)) for d in dims]
+        e = [int(rng.integers(1, d - oo + 1)) for d, oo in zip(dims, o)]
+        if q % 2 == 0:  # a row pitch that is a multiple of 16 bytes where the box allows one
+            step = 8 // np.gcd(8, C)
+            if e[0] >= step:
+                e[0] -= e[0] % step
+        boxes.append((o, e))
+    rs = []
+    for staged in (1, 0):
+        r = _renderer(dims, C, M, bg=321, tau=900)
+        r.set_insert_staging(staged)
+        r.insert_block((0, 0, 0), torch.from_numpy(junk.view(np.int16)).cuda())
+        for o, e in boxes:
+            r.insert_block(o, vol[o[2]:o[2] + e[2], o[1]:o[1] + e[1], o[0]:o[0] + e[0]])
+        # a device block whose base is 2 bytes past a 16-byte boundary
+        ez = min(5, Z)
+        flat = torch.empty(ez * Y * X * C + 1, dtype=torch.int16, device="cuda")
+        blk = flat[1:].view(ez, Y, X, C)
+        blk.copy_(torch.from_numpy(junk[:ez].view(np.int16)))
+        r.insert_block((0, 0, 0), blk)
+        for z0 in range(0, Z, 8):
+            r.insert_block((0, 0, z0), torch.from_numpy(vol[z0:z0 + 8].view(np.int16)).cuda())
+        torch.cuda.synchronize()
+        rs.append(r)
+    for L in range(rs[0].levels):
+        a, b = rs[0].read_level(L), rs[1].read_level(L)
+        assert np.array_equal(a, b), f"level {L}: staged and per-thread loads differ"
+    _compare_state(rs[0], oracle_dense(vol, M, bg=321, tau=900))
+
+
 def test_overlapped_host_uploads_interleaved_with_renders():
     """VR_HOST_ASYNC: pinned host blocks of changing sizes uploaded on the library's upload
     stream while renders are queued between the inserts; the state equals the oracle's."""
