@@ -703,7 +703,7 @@ static EncodeTiledFn encode_tiled() {
     return fn;
 }
 
-constexpr int STAGE_SMEM_MAX = 64 * 1024; // staged planes of one level-0 CTA (+ 128 bytes of alignment slack)
+constexpr int STAGE_SMEM_MAX = 32 * 1024; // staged planes of one level-0 CTA (+ 128 bytes of alignment slack)
 constexpr int STAGE_PLANES_MAX = 8;
 
 // Level 0 through level0_staged_kernel when the block allows it: base and rows 16-byte aligned,
