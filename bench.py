@@ -792,10 +792,10 @@ def main():
             "peak_kind": peak_kind, "algorithmic_bytes_frames": len(fp),
             "distinct_voxels_per_level_first_frame": vox, "distinct_nodes_first_frame": nodes}
     # DRAM and L2 traffic of the render's two kernels from one small ncu capture (the medium
-    # stand-in volume, 2.9 GB pool, three frames), valid while the render sources are unchanged,
-    # scaled to this workload in proportion to the algorithmic bytes of the frame (traffic / U of
-    # the captured frames x this frame's U); the captured instructions give an issue fraction only
-    # for the captured workload itself
+    # stand-in volume, 2.9 GB pool, the two launches of one frame), valid while the render sources
+    # are unchanged, scaled to this workload in proportion to the algorithmic bytes of the frame
+    # (traffic / U of the captured frame x this frame's U); the captured instructions give an issue
+    # fraction only for the captured workload itself
     issue = None
     tr = os.path.join(ROOT, "profiles", "render_medium_counters.json")
     if os.path.exists(tr):
@@ -821,11 +821,22 @@ def main():
                          "frac": ach / ipeak, "thread_instructions_per_sample": ips,
                          "instructions_from": f"ncu capture of {d['workload']}, per composited sample",
                          "peak_from": f"{sms} SMs x 4 schedulers x 32 lanes x median SM clock"}
-            # (instructions per sample do not carry over to another workload: they depend on the share
-            # of samples composited in closed-form runs, so no issue figure is scaled to this one)
+            else:
+                # instructions per sample do not carry over to another workload (they depend on the
+                # share of samples composited in closed-form runs): the captured workload's own issue
+                # fraction is reported, labelled as such, and nothing is scaled to this one
+                ci = d.get("issue")
+                if ci:
+                    issue = {"bound": "issue", "workload": d["workload"], "frac": ci["thread_issue_frac"],
+                             "achieved": ci["thread_issue_achieved_T_per_s"], "peak": ci["thread_issue_peak_T_per_s"],
+                             "unit": "T thread-instructions/s",
+                             "warp_issue_frac": ci["warp_issue_frac"],
+                             "thread_instructions_per_sample": ci["thread_instructions_per_sample"],
+                             "measured": "on the captured workload (its live rate and its ncu instruction "
+                                         "counts), not on this one", "peak_from": ci["peak_from"]}
     capture_frames = None
     if args.workload == "medium":
-        # what a counter capture of the first three render launches (frames 0-2) is divided by
+        # what a counter capture of the first render launches (frame 0: its two kernels) is divided by
         capture_frames = []
         for f in (0, 1, 2):
             vox_f, nodes_f = r.footprint([w.cameras[f]])
