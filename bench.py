@@ -40,7 +40,7 @@ def peaks():
 class ClockSampler:
     """SM clocks and throttle reasons sampled DURING the timed region: NVML polled every 2 ms from a
     thread (the main thread waits in CUDA synchronisation, which releases the GIL), so that even a
-    timed region of a few tens of milliseconds gets many samples; nvidia-smi at 100 ms if NVML is
+    timed region of a few tens of milliseconds gets many samples; nvidia-smi every 25 ms if NVML is
     unavailable."""
 
     NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
@@ -90,11 +90,11 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "25"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
-            self.source = "nvidia-smi, 100 ms"
+            self.source = "nvidia-smi, 25 ms"
         except Exception:
             self.proc = None
         return self
@@ -808,9 +808,9 @@ def main():
             ips = sum(f["thread_instructions"] for f in cf) / sum(f["samples"] for f in cf)
             roof["traffic"] = dram_per_u * U
             roof["l2_traffic"] = l2_per_u * U
-            roof["traffic_from"] = (f"ncu capture of {d['workload']} ({len(cf)} launches, {d['pool_gb']:.1f} GB "
-                                    f"pool): DRAM bytes / algorithmic bytes = {dram_per_u:.2f}, scaled by this "
-                                    f"frame's algorithmic bytes")
+            roof["traffic_from"] = (f"ncu capture of {d['workload']} ({len(cf)} frame(s), render_kernel + "
+                                    f"render_tail_kernel each, {d['pool_gb']:.1f} GB pool): DRAM bytes / "
+                                    f"algorithmic bytes = {dram_per_u:.2f}, scaled by this frame's algorithmic bytes")
             if args.workload == "medium":
                 # the captured frames themselves: their instructions per sample times the live rate
                 mhz = clk.summary().get("sm_mhz") or 2032.0
