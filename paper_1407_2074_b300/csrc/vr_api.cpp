@@ -780,20 +780,22 @@ vr_status vr_render(vr_ctx* c, const vr_camera* cams, int n, float* const* image
     RenderArgs a = make_args(c, n, tiles);
     const int blocks = grid_for(c, tiles, c->threads, c->ctas_per_sm);
     const bool cont = mode == VR_MODE_DVR && !a.has_xf && !a.cache.cslot && c->cont_lg >= 0;
-    if (mode == VR_MODE_DVR) { // whole-ray, per-channel-transform and render-cache passes alike
-        s = order_prepare(c, a, c->h_cams, n, tiles, st);
+    if (cont) { // before the tile order: its reset is no kernel, and the kernels below form one chain
+        s = cont_prepare(c, a, (long long)blocks * c->threads, st);
         if (s != VR_OK) return s;
     }
-    if (cont) {
-        s = cont_prepare(c, a, (long long)blocks * c->threads, st);
+    if (mode == VR_MODE_DVR) { // whole-ray, per-channel-transform and render-cache passes alike
+        s = order_prepare(c, a, c->h_cams, n, tiles, st);
         if (s != VR_OK) return s;
     }
     if (mode == VR_MODE_MIP) {
         s = seg_prepare(c, c->seg, a, c->h_cams, n, tiles, st);
         if (s != VR_OK) return s;
     }
-    CK(c, launch_render(a, mode, fp16 && mode == VR_MODE_DVR, blocks, c->threads, st));
-    if (cont) CK(c, launch_render_tail(a, fp16, blocks, c->threads, st));
+    // the tile-order scatter, the ray caster and the continuation as programmatic dependents, each
+    // of the kernel before it
+    CK(c, launch_render(a, mode, fp16 && mode == VR_MODE_DVR, blocks, c->threads, st, true));
+    if (cont) CK(c, launch_render_tail(a, fp16, blocks, c->threads, st, true));
     c->last_cont = cont;
     return VR_OK;
 }

@@ -146,10 +146,13 @@ cudaError_t launch_read_level(const Geo& g, int L, const uint16_t* pool, const R
 cudaError_t launch_read_voxels(const Geo& g, int L, const uint16_t* pool, const RNode* rn, const long long* xyz,
                                long long n, uint16_t* out, cudaStream_t st);
 cudaError_t launch_prepare_tf(int C, const float* tf, const float* scale, float4* tf2, float* scl, cudaStream_t st);
-cudaError_t launch_render(const RenderArgs& a, int mode, int fp16, int blocks, int threads, cudaStream_t st);
+// pdl: launched as a programmatic dependent of the kernel before it on st (vr_render's own chain)
+cudaError_t launch_render(const RenderArgs& a, int mode, int fp16, int blocks, int threads, cudaStream_t st,
+                          bool pdl = false);
 cudaError_t launch_render_backward(const RenderArgs& a, int blocks, int threads, cudaStream_t st);
 // the second launch of a continued DVR render: the recorded rays, 2^a.cont_lg lanes each
-cudaError_t launch_render_tail(const RenderArgs& a, int fp16, int blocks, int threads, cudaStream_t st);
+cudaError_t launch_render_tail(const RenderArgs& a, int fp16, int blocks, int threads, cudaStream_t st,
+                               bool pdl = false);
 cudaError_t launch_tile_order(const unsigned int* cost, long long tiles, unsigned int* aux, unsigned int* order,
                               cudaStream_t st);
 cudaError_t launch_cache_gather(const uint16_t* store, uint16_t* cache, const int2* list, int n, long long slot_elems,

@@ -32,6 +32,14 @@
 
 namespace vrk {
 
+// Programmatic dependent launch within one vr_render: the tile-order scatter, the ray caster and
+// the continuation are launched with programmatic stream serialization, so each launch is
+// processed while the kernel before it drains; a kernel does its independent set-up (tables into
+// shared memory, its own counting) and then waits here for the kernel before it to complete and
+// its writes to be visible.  No kernel triggers its dependents early.  The wait does nothing in a
+// kernel launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ bool ray_setup(const CamParam& cp, const Geo& g, int px, int py, float d[3], float& t0,
                                           float& t1) {
     const float a = (float)(2 * px + 1);
@@ -1190,6 +1198,7 @@ __global__ void __launch_bounds__(RENDER_MAX_THREADS, 1) render_kernel(RenderArg
     __shared__ long long s_ct_clk[RENDER_MAX_WARPS];
     const int wib = threadIdx.x >> 5;
     if (lane == 0) s_ct_tile[wib] = 0xffffffffu;
+    pdl_wait(); // the tile order of this call (tile_scatter_kernel) is complete
     for (;;) {
         unsigned long long tile = 0;
         if (lane == 0) tile = atomicAdd(counter, 1ull);
@@ -1297,6 +1306,7 @@ __global__ void __launch_bounds__(RENDER_MAX_THREADS, 1) render_tail_kernel(Rend
     const int lg = a.cont_lg, per = 32 >> lg;
     const int j = lane & ((1 << lg) - 1), gbase = lane - j;
     const unsigned gmask = lg == 5 ? 0xffffffffu : (((1u << (1 << lg)) - 1u) << gbase);
+    pdl_wait(); // the rays recorded by render_kernel are complete
     const unsigned n_cont = a.cont_ctl[1];
     unsigned long long my_samples = 0;
     for (;;) {
@@ -1789,6 +1799,12 @@ __global__ void tile_hist_kernel(const unsigned* __restrict__ cost, long long n,
 __global__ void tile_scatter_kernel(const unsigned* __restrict__ cost, long long n, unsigned* aux,
                                     unsigned* __restrict__ order) {
     __shared__ unsigned base[NCLS], cnt[NCLS];
+    if (threadIdx.x < NCLS) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        atomicAdd(&cnt[cost_class(cost[i])], 1u);
+    pdl_wait(); // the class sizes (tile_hist_kernel) are complete
     if (threadIdx.x == 0) {
         unsigned acc = 0;
         for (int c = NCLS - 1; c >= 0; --c) {
@@ -1796,11 +1812,6 @@ __global__ void tile_scatter_kernel(const unsigned* __restrict__ cost, long long
             acc += aux[c];
         }
     }
-    if (threadIdx.x < NCLS) cnt[threadIdx.x] = 0;
-    __syncthreads();
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-        atomicAdd(&cnt[cost_class(cost[i])], 1u);
     __syncthreads();
     if (threadIdx.x < NCLS) {
         base[threadIdx.x] += cnt[threadIdx.x] ? atomicAdd(&aux[NCLS + threadIdx.x], cnt[threadIdx.x]) : 0u;
@@ -2045,17 +2056,34 @@ static void prefer_l1(const void* kernel, int threads, size_t dyn_smem) {
         cudaGetLastError();
 }
 
+// One launch of kernel k, as a programmatic dependent of the kernel before it on st when pdl.
+template <class K>
+static cudaError_t launch_k(K k, int blocks, int threads, size_t smem, cudaStream_t st, bool pdl, const RenderArgs& a) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, a);
+}
+
 template <int C, int VS, int MODE, bool POW2, bool H, bool XF = false, bool CACHE = false>
-static void launch_one(const RenderArgs& a, int blocks, int threads, cudaStream_t st) {
+static void launch_one(const RenderArgs& a, int blocks, int threads, cudaStream_t st, bool pdl = false) {
     const size_t smem = (size_t)C * 512 * sizeof(float4) + (H ? (size_t)C * 256 * sizeof(HalfEntry) : 0);
     cudaFuncSetAttribute(render_kernel<C, VS, MODE, POW2, H, XF, CACHE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     prefer_l1(reinterpret_cast<const void*>(render_kernel<C, VS, MODE, POW2, H, XF, CACHE>), threads, smem);
-    render_kernel<C, VS, MODE, POW2, H, XF, CACHE><<<blocks, threads, smem, st>>>(a);
+    launch_k(render_kernel<C, VS, MODE, POW2, H, XF, CACHE>, blocks, threads, smem, st, pdl, a);
 }
 
 template <int C, int VS>
-static cudaError_t launch_fwd_c(const RenderArgs& a, int mode, int fp16, int blocks, int threads, cudaStream_t st) {
+static cudaError_t launch_fwd_c(const RenderArgs& a, int mode, int fp16, int blocks, int threads, cudaStream_t st,
+                                bool pdl) {
     const bool p2 = a.g.pow2 != 0;
     if (mode == 3) {
         const size_t smem = (size_t)C * 512 * sizeof(float4);
@@ -2103,11 +2131,11 @@ static cudaError_t launch_fwd_c(const RenderArgs& a, int mode, int fp16, int blo
         return cudaGetLastError();
     }
     if (mode == 0 && fp16) {
-        if (p2) launch_one<C, VS, 0, true, true>(a, blocks, threads, st);
-        else launch_one<C, VS, 0, false, true>(a, blocks, threads, st);
+        if (p2) launch_one<C, VS, 0, true, true>(a, blocks, threads, st, pdl);
+        else launch_one<C, VS, 0, false, true>(a, blocks, threads, st, pdl);
     } else if (mode == 0) {
-        if (p2) launch_one<C, VS, 0, true, false>(a, blocks, threads, st);
-        else launch_one<C, VS, 0, false, false>(a, blocks, threads, st);
+        if (p2) launch_one<C, VS, 0, true, false>(a, blocks, threads, st, pdl);
+        else launch_one<C, VS, 0, false, false>(a, blocks, threads, st, pdl);
     } else if (mode == 2) {
         if (p2) launch_one<C, VS, 2, true, false>(a, blocks, threads, st);
         else launch_one<C, VS, 2, false, false>(a, blocks, threads, st);
@@ -2119,41 +2147,41 @@ static cudaError_t launch_fwd_c(const RenderArgs& a, int mode, int fp16, int blo
 }
 
 template <int C, int VS, bool POW2, bool H>
-static void launch_tail_one(const RenderArgs& a, int blocks, int threads, cudaStream_t st) {
+static void launch_tail_one(const RenderArgs& a, int blocks, int threads, cudaStream_t st, bool pdl) {
     const size_t smem = (size_t)C * 512 * sizeof(float4) + (H ? (size_t)C * 256 * sizeof(HalfEntry) : 0);
     cudaFuncSetAttribute(render_tail_kernel<C, VS, POW2, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     prefer_l1(reinterpret_cast<const void*>(render_tail_kernel<C, VS, POW2, H>), threads, smem);
-    render_tail_kernel<C, VS, POW2, H><<<blocks, threads, smem, st>>>(a);
+    launch_k(render_tail_kernel<C, VS, POW2, H>, blocks, threads, smem, st, pdl, a);
 }
 
 template <int C, int VS>
-static cudaError_t launch_tail_c(const RenderArgs& a, int fp16, int blocks, int threads, cudaStream_t st) {
+static cudaError_t launch_tail_c(const RenderArgs& a, int fp16, int blocks, int threads, cudaStream_t st, bool pdl) {
     if (a.g.pow2) {
-        if (fp16) launch_tail_one<C, VS, true, true>(a, blocks, threads, st);
-        else launch_tail_one<C, VS, true, false>(a, blocks, threads, st);
+        if (fp16) launch_tail_one<C, VS, true, true>(a, blocks, threads, st, pdl);
+        else launch_tail_one<C, VS, true, false>(a, blocks, threads, st, pdl);
     } else {
-        if (fp16) launch_tail_one<C, VS, false, true>(a, blocks, threads, st);
-        else launch_tail_one<C, VS, false, false>(a, blocks, threads, st);
+        if (fp16) launch_tail_one<C, VS, false, true>(a, blocks, threads, st, pdl);
+        else launch_tail_one<C, VS, false, false>(a, blocks, threads, st, pdl);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_render_tail(const RenderArgs& a, int fp16, int blocks, int threads, cudaStream_t st) {
+cudaError_t launch_render_tail(const RenderArgs& a, int fp16, int blocks, int threads, cudaStream_t st, bool pdl) {
     if (!a.cont || a.cont_lg < 0 || a.cont_lg > 5) return cudaErrorInvalidValue;
     switch (a.g.C) {
-        case 1: return launch_tail_c<1, 1>(a, fp16, blocks, threads, st);
-        case 2: return launch_tail_c<2, 2>(a, fp16, blocks, threads, st);
-        case 3: return launch_tail_c<3, 4>(a, fp16, blocks, threads, st);
-        default: return launch_tail_c<4, 4>(a, fp16, blocks, threads, st);
+        case 1: return launch_tail_c<1, 1>(a, fp16, blocks, threads, st, pdl);
+        case 2: return launch_tail_c<2, 2>(a, fp16, blocks, threads, st, pdl);
+        case 3: return launch_tail_c<3, 4>(a, fp16, blocks, threads, st, pdl);
+        default: return launch_tail_c<4, 4>(a, fp16, blocks, threads, st, pdl);
     }
 }
 
-cudaError_t launch_render(const RenderArgs& a, int mode, int fp16, int blocks, int threads, cudaStream_t st) {
+cudaError_t launch_render(const RenderArgs& a, int mode, int fp16, int blocks, int threads, cudaStream_t st, bool pdl) {
     switch (a.g.C) {
-        case 1: return launch_fwd_c<1, 1>(a, mode, fp16, blocks, threads, st);
-        case 2: return launch_fwd_c<2, 2>(a, mode, fp16, blocks, threads, st);
-        case 3: return launch_fwd_c<3, 4>(a, mode, fp16, blocks, threads, st);
-        default: return launch_fwd_c<4, 4>(a, mode, fp16, blocks, threads, st);
+        case 1: return launch_fwd_c<1, 1>(a, mode, fp16, blocks, threads, st, pdl);
+        case 2: return launch_fwd_c<2, 2>(a, mode, fp16, blocks, threads, st, pdl);
+        case 3: return launch_fwd_c<3, 4>(a, mode, fp16, blocks, threads, st, pdl);
+        default: return launch_fwd_c<4, 4>(a, mode, fp16, blocks, threads, st, pdl);
     }
 }
 
@@ -2190,7 +2218,17 @@ cudaError_t launch_tile_order(const unsigned* cost, long long tiles, unsigned* a
     const long long b = (tiles + 1023) / 1024;
     const int blocks = (int)(b < 1 ? 1 : (b > 148 ? 148 : b));
     tile_hist_kernel<<<blocks, 1024, 0, st>>>(cost, tiles, aux);
-    tile_scatter_kernel<<<blocks, 1024, 0, st>>>(cost, tiles, aux, order);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3(1024u);
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, tile_scatter_kernel, cost, tiles, aux, order);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
