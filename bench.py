@@ -283,6 +283,29 @@ def cpu_baseline(w, vol, n_rays, seed=0, threads=0):
     return float(samples.sum()), dt, cores
 
 
+def workload_config(w, pool_gb, ws):
+    """The bench line's config: the workload of one step and its parameters (both arms)."""
+    return {"workload": w.name + ": insert 8 slices + render one 1920x1080 orbit frame per step",
+            "dims": list(w.dims), "channels": 3, "brick": w.brick, "tau": w.tau, "step_voxels": 0.5,
+            "lod_error_px": 1.0, "ert_alpha": 0.99, "l2": f"inputs larger than L2 (brick pool {pool_gb:.1f} GB)",
+            "parallelism": f"replicas x{ws}"}
+
+
+def full_tree_pool_gb(dims, M, C):
+    """Bytes of a brick pool with a slot for every node of the full tree ((M + 2)^3 voxels of C
+    channels, 3 padded to 4, 2 bytes each), as the library sizes it by default."""
+    vs = 4 if C == 3 else C
+    dims = list(dims)
+    n = 0
+    while True:
+        nb = [-(-d // M) for d in dims]
+        n += nb[0] * nb[1] * nb[2]
+        if max(nb) == 1:
+            break
+        dims = [-(-d // 2) for d in dims]
+    return n * (M + 2) ** 3 * vs * 2 / 1e9
+
+
 def run_reference(args):
     """--impl reference: the FP64 oracle on the host cores, each step a bounded sample (rays) of
     the same workload, same metric and unit."""
@@ -305,8 +328,9 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "samples/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tot_t / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name + " orbit frame 0 at 1920x1080", "tau": w.tau,
-                       "sample": f"{REF_RAYS} random rays per step (render only; the oracle state is built untimed)"},
+            "config": workload_config(w, full_tree_pool_gb(w.dims, w.brick, 3), args.gpus),
+            "sample": f"each step: {REF_RAYS} random rays of orbit frame 0 (the render only; the oracle state of "
+                      "the full volume is built untimed)",
             "cpu_baseline": {"value": v, "unit": "samples/s", "cores": cores, "kind": "oracle",
                              "sample": f"{REF_RAYS} random rays of orbit frame 0 per step, streamed oracle volume, "
                                        "tau = 3277"},
@@ -927,10 +951,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": w.name + ": insert 8 slices + render one 1920x1080 orbit frame per step",
-                           "dims": list(w.dims), "channels": 3, "brick": w.brick, "tau": w.tau, "step_voxels": 0.5,
-                           "lod_error_px": 1.0, "ert_alpha": 0.99, "l2": "inputs larger than L2 (brick pool "
-                           f"{pool_gb:.1f} GB)", "parallelism": f"replicas x{ws}"},
+                "config": workload_config(w, pool_gb, ws),
                 "ms_per_frame": render_ms, "ms_per_frame_median": render_ms_median,
                 "pixel_rays_per_s": H * W / (render_ms / 1e3),
                 "volume_rays_per_s": rays_per_frame / (render_ms / 1e3),
