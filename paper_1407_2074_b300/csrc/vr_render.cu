@@ -85,13 +85,25 @@ __device__ __forceinline__ bool ray_setup(const CamParam& cp, const Geo& g, int 
     return t0 < t1;
 }
 
+// Hardware square root and reciprocal approximations (one SFU operation each, relative error
+// about 2^-22; flush-to-zero is harmless: the operands lie in [1e-6, 2]).
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Opacity correction a = 1 - (1 - alpha)^l and its complement (1 - alpha)^l, accurate for small
-// alpha (no 1 - (1 - x) cancellation).
+// alpha (no 1 - (1 - x) cancellation): for l = 1/2, a = alpha / (1 + sqrt(1 - alpha)).
 __device__ __forceinline__ void opacity(float al, float ell, float& a, float& oma) {
     if (ell == 0.5f) {
-        const float om = 1.0f - al; // >= 1e-6
-        const float s = om * rsqrtf(om);
-        a = __fdividef(al, 1.0f + s);
+        const float s = sqrt_approx(1.0f - al); // 1 - al >= 1e-6
+        a = al * rcp_approx(1.0f + s);
         oma = s;
     } else if (ell == 1.0f) {
         a = al;
