@@ -159,8 +159,9 @@ struct Shaded {
 // Traversal state of one ray, shared by the one-lane march and the lane-group march: the level of
 // detail L* of the current sample and the cached node -- its level, grid index, the faces of its
 // box the ray heads for, and its brick slot or AVG.  Sample positions, L* and the node choice use
-// only correctly rounded single-precision operations in a fixed order.
-template <int C, int VS, bool POW2>
+// only correctly rounded single-precision operations in a fixed order.  SK > 0: the slot edge
+// M + 2 known at compile time (corner offsets become immediates); 0: read from the geometry.
+template <int C, int VS, bool POW2, int SK = 0>
 struct RayCursor {
     const Geo& g;
     const uint16_t* __restrict__ pool;
@@ -192,8 +193,8 @@ struct RayCursor {
             neg[a] = !(dd[a] > 0.0f);
         }
         N = g.N;
-        M = g.M;
-        S = g.S;
+        M = SK > 0 ? SK - 2 : g.M; // the launch picks SK == g.S
+        S = SK > 0 ? SK : g.S;
         mlog = __ffs(M) - 1; // log2(M) when POW2
         tnext = N >= 1 ? cp.tl[1] : CUDART_INF_F;
     }
@@ -304,7 +305,9 @@ struct RayCursor {
             const float fl = floorf(u);
             const int ii = (int)fl;
             fr[a] = __fsub_rn(u, fl);
-            i0[a] = ii < 0 ? 0 : (ii > M ? M : ii);
+            // in [0, M] with one unsigned minimum: the node's box keeps ii in [0, M]; any other
+            // value (a negative one reads as a large unsigned) still lands inside the slot
+            i0[a] = (int)min((unsigned)ii, (unsigned)M);
         }
         return sbase + ((i0[2] * S + i0[1]) * S + i0[0]) * VS;
     }
@@ -510,7 +513,7 @@ struct RayCursor {
 // from (Sec. "Refinement Ray-Casting").  k0 is the first sample index.  With dry != nullptr the
 // march also stops, returning -(k + 1), once *dry is set (checked every 16 steps) and more than
 // min_left segment lengths of the ray remain: f then holds the state before sample k.
-template <int C, int VS, bool POW2, bool H, class F>
+template <int C, int VS, bool POW2, bool H, class F, int SK = 0>
 __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restrict__ pool,
                                            const RNode* __restrict__ rn, const CamParam& cp, const float d[3], float t0,
                                            float t1, F& f, const CacheArgs* ca = nullptr, int k0 = 0,
@@ -518,7 +521,7 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
     // samples k0 <= k < min(kend, MAX_SAMPLES) inside [t0, t1)
     const float dt = cp.dt;
     const int klim = kend < MAX_SAMPLES ? kend : MAX_SAMPLES;
-    RayCursor<C, VS, POW2> cur(g, pool, rn, cp, d);
+    RayCursor<C, VS, POW2, SK> cur(g, pool, rn, cp, d);
     const int N = cur.N, M = cur.M;
     int k = k0;
     float kf = (float)k0; // == (float)k, exact below 2^24
@@ -631,7 +634,7 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
 // samples composited, the runs and the stop are those of march(), so the image is bit for bit the
 // one-lane image.  gmask: the group's lanes; gbase: its first lane; j: this lane's place in it;
 // k0: the first sample (f holds the ray state before it); s_grp: the warp's 32 shared-memory slots.
-template <int C, int VS, bool POW2, bool H, class F>
+template <int C, int VS, bool POW2, bool H, class F, int SK = 0>
 __device__ __forceinline__ long long march_group(const Geo& g, const uint16_t* __restrict__ pool,
                                                  const RNode* __restrict__ rn, const CamParam& cp, const float d[3],
                                                  float t0, float t1, F& f, int lg, unsigned gmask, int gbase, int j,
@@ -640,7 +643,7 @@ __device__ __forceinline__ long long march_group(const Geo& g, const uint16_t* _
     const int G = 1 << lg;
     const int lane = gbase + j;
     const unsigned gbits = gmask >> gbase; // the group's lanes as bits 0 .. G-1
-    RayCursor<C, VS, POW2> cur(g, pool, rn, cp, d);
+    RayCursor<C, VS, POW2, SK> cur(g, pool, rn, cp, d);
     int k = k0;
     for (;;) {
         const int kk = k + j;
@@ -842,7 +845,7 @@ __device__ __forceinline__ long long march_xf(const Geo& g, const uint16_t* __re
                     const float fl = floorf(u);
                     const int ii = (int)fl;
                     fr[a] = __fsub_rn(u, fl);
-                    i0[a] = ii < 0 ? 0 : (ii > M ? M : ii);
+                    i0[a] = ii < 0 ? 0 : (ii > M ? M : ii); // a transformed point may leave the volume
                 }
                 const int coff = ((i0[2] * S + i0[1]) * S + i0[0]) * VS;
                 {
@@ -1183,7 +1186,7 @@ __device__ __forceinline__ void load_render_tables(const RenderArgs& a, float4* 
     }
 }
 
-template <int C, int VS, int MODE, bool POW2, bool H, bool XF = false, bool CACHE = false>
+template <int C, int VS, int MODE, bool POW2, bool H, bool XF = false, bool CACHE = false, int SK = 0>
 __global__ void __launch_bounds__(RENDER_MAX_THREADS, 1) render_kernel(RenderArgs a) {
     extern __shared__ float4 s_tf[];
     __shared__ float s_scl[MAXC];
@@ -1256,7 +1259,7 @@ __global__ void __launch_bounds__(RENDER_MAX_THREADS, 1) render_kernel(RenderArg
             if constexpr (XF) {
                 n = march_xf<C, VS, POW2>(a.g, a.pool, a.rnodes, *cp, dd, r0, r1, a.xf, f);
             } else if constexpr (CONT) {
-                n = march<C, VS, POW2, H>(a.g, a.pool, a.rnodes, *cp, dd, r0, r1, f, nullptr, 0, MAX_SAMPLES, dry,
+                n = march<C, VS, POW2, H, F, SK>(a.g, a.pool, a.rnodes, *cp, dd, r0, r1, f, nullptr, 0, MAX_SAMPLES, dry,
                                           a.cont_min);
                 if (n < 0) { // stopped at sample -n - 1: record the ray for the second launch
                     const unsigned slot = atomicAdd(&a.cont_ctl[1], 1u);
@@ -1265,7 +1268,7 @@ __global__ void __launch_bounds__(RENDER_MAX_THREADS, 1) render_kernel(RenderArg
                     continue; // the pixel is written by the second launch
                 }
             } else {
-                n = march<C, VS, POW2, H>(a.g, a.pool, a.rnodes, *cp, dd, r0, r1, f, CACHE ? &a.cache : nullptr);
+                n = march<C, VS, POW2, H, F, SK>(a.g, a.pool, a.rnodes, *cp, dd, r0, r1, f, CACHE ? &a.cache : nullptr);
             }
             my_samples += (unsigned long long)n;
             if constexpr (MODE == 1) {
@@ -1305,7 +1308,7 @@ __global__ void __launch_bounds__(RENDER_MAX_THREADS, 1) render_kernel(RenderArg
 // 2^a.cont_lg lanes (march_group), which then writes its pixel.  The first launch was latency-bound
 // by then -- few warps left, each with long rays -- and a lane group advances a ray by up to
 // 2^cont_lg samples per step; the samples composited, and so the pixel, are those of one lane.
-template <int C, int VS, bool POW2, bool H>
+template <int C, int VS, bool POW2, bool H, int SK = 0>
 __global__ void __launch_bounds__(RENDER_MAX_THREADS, 1) render_tail_kernel(RenderArgs a) {
     extern __shared__ float4 s_tf[];
     __shared__ float s_scl[MAXC];
@@ -1342,7 +1345,7 @@ __global__ void __launch_bounds__(RENDER_MAX_THREADS, 1) render_tail_kernel(Rend
         f.Cg = rc.Cg;
         f.Cb = rc.Cb;
         const long long n =
-            march_group<C, VS, POW2, H>(a.g, a.pool, a.rnodes, *cp, dd, r0, r1, f, lg, gmask, gbase, j, rc.k,
+            march_group<C, VS, POW2, H, F, SK>(a.g, a.pool, a.rnodes, *cp, dd, r0, r1, f, lg, gmask, gbase, j, rc.k,
                                         s_grp[threadIdx.x >> 5]);
         if (j == 0) {
             my_samples += (unsigned long long)(n - rc.k);
@@ -2084,14 +2087,18 @@ static cudaError_t launch_k(K k, int blocks, int threads, size_t smem, cudaStrea
     return cudaLaunchKernelEx(&cfg, k, a);
 }
 
-template <int C, int VS, int MODE, bool POW2, bool H, bool XF = false, bool CACHE = false>
+template <int C, int VS, int MODE, bool POW2, bool H, bool XF = false, bool CACHE = false, int SK = 0>
 static void launch_one(const RenderArgs& a, int blocks, int threads, cudaStream_t st, bool pdl = false) {
     const size_t smem = (size_t)C * 512 * sizeof(float4) + (H ? (size_t)C * 256 * sizeof(HalfEntry) : 0);
-    cudaFuncSetAttribute(render_kernel<C, VS, MODE, POW2, H, XF, CACHE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    prefer_l1(reinterpret_cast<const void*>(render_kernel<C, VS, MODE, POW2, H, XF, CACHE>), threads, smem);
-    launch_k(render_kernel<C, VS, MODE, POW2, H, XF, CACHE>, blocks, threads, smem, st, pdl, a);
+    cudaFuncSetAttribute(render_kernel<C, VS, MODE, POW2, H, XF, CACHE, SK>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    prefer_l1(reinterpret_cast<const void*>(render_kernel<C, VS, MODE, POW2, H, XF, CACHE, SK>), threads, smem);
+    launch_k(render_kernel<C, VS, MODE, POW2, H, XF, CACHE, SK>, blocks, threads, smem, st, pdl, a);
 }
+
+// The slot edge the plain DVR kernels are also built for as a compile-time constant (M = 32, the
+// brick size of the large workloads): its corner offsets become immediates.
+constexpr int SK_DVR = 34;
 
 template <int C, int VS>
 static cudaError_t launch_fwd_c(const RenderArgs& a, int mode, int fp16, int blocks, int threads, cudaStream_t st,
@@ -2142,11 +2149,14 @@ static cudaError_t launch_fwd_c(const RenderArgs& a, int mode, int fp16, int blo
         mip_merge_kernel<C><<<mblocks, 256, smem, st>>>(a);
         return cudaGetLastError();
     }
+    const bool sk = p2 && a.g.S == SK_DVR;
     if (mode == 0 && fp16) {
-        if (p2) launch_one<C, VS, 0, true, true>(a, blocks, threads, st, pdl);
+        if (sk) launch_one<C, VS, 0, true, true, false, false, SK_DVR>(a, blocks, threads, st, pdl);
+        else if (p2) launch_one<C, VS, 0, true, true>(a, blocks, threads, st, pdl);
         else launch_one<C, VS, 0, false, true>(a, blocks, threads, st, pdl);
     } else if (mode == 0) {
-        if (p2) launch_one<C, VS, 0, true, false>(a, blocks, threads, st, pdl);
+        if (sk) launch_one<C, VS, 0, true, false, false, false, SK_DVR>(a, blocks, threads, st, pdl);
+        else if (p2) launch_one<C, VS, 0, true, false>(a, blocks, threads, st, pdl);
         else launch_one<C, VS, 0, false, false>(a, blocks, threads, st, pdl);
     } else if (mode == 2) {
         if (p2) launch_one<C, VS, 2, true, false>(a, blocks, threads, st);
@@ -2158,17 +2168,21 @@ static cudaError_t launch_fwd_c(const RenderArgs& a, int mode, int fp16, int blo
     return cudaGetLastError();
 }
 
-template <int C, int VS, bool POW2, bool H>
+template <int C, int VS, bool POW2, bool H, int SK = 0>
 static void launch_tail_one(const RenderArgs& a, int blocks, int threads, cudaStream_t st, bool pdl) {
     const size_t smem = (size_t)C * 512 * sizeof(float4) + (H ? (size_t)C * 256 * sizeof(HalfEntry) : 0);
-    cudaFuncSetAttribute(render_tail_kernel<C, VS, POW2, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    prefer_l1(reinterpret_cast<const void*>(render_tail_kernel<C, VS, POW2, H>), threads, smem);
-    launch_k(render_tail_kernel<C, VS, POW2, H>, blocks, threads, smem, st, pdl, a);
+    cudaFuncSetAttribute(render_tail_kernel<C, VS, POW2, H, SK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    prefer_l1(reinterpret_cast<const void*>(render_tail_kernel<C, VS, POW2, H, SK>), threads, smem);
+    launch_k(render_tail_kernel<C, VS, POW2, H, SK>, blocks, threads, smem, st, pdl, a);
 }
 
 template <int C, int VS>
 static cudaError_t launch_tail_c(const RenderArgs& a, int fp16, int blocks, int threads, cudaStream_t st, bool pdl) {
-    if (a.g.pow2) {
+    if (a.g.pow2 && a.g.S == SK_DVR) {
+        if (fp16) launch_tail_one<C, VS, true, true, SK_DVR>(a, blocks, threads, st, pdl);
+        else launch_tail_one<C, VS, true, false, SK_DVR>(a, blocks, threads, st, pdl);
+    } else if (a.g.pow2) {
         if (fp16) launch_tail_one<C, VS, true, true>(a, blocks, threads, st, pdl);
         else launch_tail_one<C, VS, true, false>(a, blocks, threads, st, pdl);
     } else {
