@@ -1857,7 +1857,7 @@ __device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
 }
 
 // seg_done[segment][tile]: 0 pending, 1 done and no ray of the tile goes on, 3 done and some do
-template <int C, int VS, bool POW2>
+template <int C, int VS, bool POW2, int SK = 0>
 __global__ void __launch_bounds__(RENDER_MAX_THREADS, 1) mip_seg_kernel(RenderArgs a) {
     const int lane = threadIdx.x & 31;
     unsigned long long* counter = reinterpret_cast<unsigned long long*>(a.counter);
@@ -1896,7 +1896,8 @@ __global__ void __launch_bounds__(RENDER_MAX_THREADS, 1) mip_seg_kernel(RenderAr
             if (seg == 0) ++my_rays;
             MIPMax<C> f;
             const int k0 = seg * a.kseg, k1 = k0 + a.kseg;
-            const long long k = march<C, VS, POW2, false>(a.g, a.pool, a.rnodes, *cp, dd, r0, r1, f, nullptr, k0, k1);
+            const long long k =
+                march<C, VS, POW2, false, decltype(f), SK>(a.g, a.pool, a.rnodes, *cp, dd, r0, r1, f, nullptr, k0, k1);
             const bool cont = k == k1 && __fadd_rn(r0, __fmul_rn((float)k1, cp->dt)) < r1;
             meta = ((unsigned)(k - k0) << 2) | (cont ? SEG_GOES_ON : SEG_END_RAY);
 #pragma unroll
@@ -2096,9 +2097,9 @@ static void launch_one(const RenderArgs& a, int blocks, int threads, cudaStream_
     launch_k(render_kernel<C, VS, MODE, POW2, H, XF, CACHE, SK>, blocks, threads, smem, st, pdl, a);
 }
 
-// The slot edge the plain DVR kernels are also built for as a compile-time constant (M = 32, the
-// brick size of the large workloads): its corner offsets become immediates.
-constexpr int SK_DVR = 34;
+// The slot edges the plain DVR kernels are also built for as compile-time constants (M = 32, the
+// brick size of the large workloads, and M = 16): their corner offsets become immediates.
+constexpr int SK_DVR = 34, SK_DVR16 = 18;
 
 template <int C, int VS>
 static cudaError_t launch_fwd_c(const RenderArgs& a, int mode, int fp16, int blocks, int threads, cudaStream_t st,
@@ -2140,7 +2141,8 @@ static cudaError_t launch_fwd_c(const RenderArgs& a, int mode, int fp16, int blo
     }
     if (mode == 1 && a.nseg > 0) { // MIP in ray segments: segments, then the merge
         cudaMemsetAsync(a.seg_done, 0, sizeof(unsigned) * (size_t)a.nseg * (size_t)a.total_tiles, st);
-        if (p2) mip_seg_kernel<C, VS, true><<<blocks, threads, 0, st>>>(a);
+        if (p2 && a.g.S == SK_DVR) mip_seg_kernel<C, VS, true, SK_DVR><<<blocks, threads, 0, st>>>(a);
+        else if (p2) mip_seg_kernel<C, VS, true><<<blocks, threads, 0, st>>>(a);
         else mip_seg_kernel<C, VS, false><<<blocks, threads, 0, st>>>(a);
         const long long mb = (a.total_tiles + 7) / 8;
         const int mblocks = (int)(mb < 1 ? 1 : (mb > 4096 ? 4096 : mb));
@@ -2149,13 +2151,15 @@ static cudaError_t launch_fwd_c(const RenderArgs& a, int mode, int fp16, int blo
         mip_merge_kernel<C><<<mblocks, 256, smem, st>>>(a);
         return cudaGetLastError();
     }
-    const bool sk = p2 && a.g.S == SK_DVR;
+    const bool sk = p2 && a.g.S == SK_DVR, sk16 = p2 && a.g.S == SK_DVR16;
     if (mode == 0 && fp16) {
         if (sk) launch_one<C, VS, 0, true, true, false, false, SK_DVR>(a, blocks, threads, st, pdl);
+        else if (sk16) launch_one<C, VS, 0, true, true, false, false, SK_DVR16>(a, blocks, threads, st, pdl);
         else if (p2) launch_one<C, VS, 0, true, true>(a, blocks, threads, st, pdl);
         else launch_one<C, VS, 0, false, true>(a, blocks, threads, st, pdl);
     } else if (mode == 0) {
         if (sk) launch_one<C, VS, 0, true, false, false, false, SK_DVR>(a, blocks, threads, st, pdl);
+        else if (sk16) launch_one<C, VS, 0, true, false, false, false, SK_DVR16>(a, blocks, threads, st, pdl);
         else if (p2) launch_one<C, VS, 0, true, false>(a, blocks, threads, st, pdl);
         else launch_one<C, VS, 0, false, false>(a, blocks, threads, st, pdl);
     } else if (mode == 2) {
@@ -2182,6 +2186,9 @@ static cudaError_t launch_tail_c(const RenderArgs& a, int fp16, int blocks, int 
     if (a.g.pow2 && a.g.S == SK_DVR) {
         if (fp16) launch_tail_one<C, VS, true, true, SK_DVR>(a, blocks, threads, st, pdl);
         else launch_tail_one<C, VS, true, false, SK_DVR>(a, blocks, threads, st, pdl);
+    } else if (a.g.pow2 && a.g.S == SK_DVR16) {
+        if (fp16) launch_tail_one<C, VS, true, true, SK_DVR16>(a, blocks, threads, st, pdl);
+        else launch_tail_one<C, VS, true, false, SK_DVR16>(a, blocks, threads, st, pdl);
     } else if (a.g.pow2) {
         if (fp16) launch_tail_one<C, VS, true, true>(a, blocks, threads, st, pdl);
         else launch_tail_one<C, VS, true, false>(a, blocks, threads, st, pdl);
