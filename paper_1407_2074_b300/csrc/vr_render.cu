@@ -135,7 +135,10 @@ struct TFLookup {
         xr = I * s_scl[c];
         const float x = __saturatef(xr);
         const float w = x * 255.0f;
-        i = min((int)w, 254);
+        // entry floor(255 x): at x = 1 that is entry 255 with lam = 0, whose difference to the next
+        // entry is stored as 0, so it reads entry 255 itself (the value the segment 254..255
+        // reaches at its end)
+        i = (int)w;
         lam = w - (float)i;
         const float4 T = s_tf[c * 256 + i], D = s_tf[(C + c) * 256 + i];
         // two packed FP32 FMAs (each element rounded as fmaf)
@@ -1015,7 +1018,7 @@ struct DVRCompositeH : NoHooks {
     __device__ __forceinline__ void lookup(int c, float I, float2& rg, float2& ba) const {
         const __half x = __hmul_sat(__float2half_rn(I), s_sh[c]);
         const float w = __half2float(x) * 255.0f;
-        const int i = min((int)w, 254);
+        const int i = (int)w; // entry 255 at x = 1 (its difference is 0), as in TFLookup
         const __half2 lam = __float2half2_rn(w - (float)i);
         const HalfEntry e = s_tfh[c * 256 + i];
         rg = __half22float2(__hfma2(lam, e.drg, e.rg));
