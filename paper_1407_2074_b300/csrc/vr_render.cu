@@ -575,32 +575,46 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
         }
         float I[C];
         if (cur.brick) {
-            cur.template interpolate<H>(p, I, f);
             if constexpr (F::kPairs) {
                 // the next sample too when it lies in the same brick node at the same level with a
                 // full segment: both are shaded before the two are composited in order, so the
-                // gathers and lookups of the second overlap those of the first
+                // gathers and lookups of the second overlap those of the first.  A sample without
+                // such a partner takes the same code with itself as the partner, composited once:
+                // one copy of the interpolation and shading in the loop.
+                bool two = false;
+                float p2[3] = {p[0], p[1], p[2]};
+                const float kf2 = kf + 1.0f;
                 if (ell == dt && k + 1 < klim) {
-                    const float kf2 = kf + 1.0f;
                     const float tk2 = __fadd_rn(t0, __fmul_rn(kf2, dt));
                     if (tk2 < t1 && __fsub_rn(t1, tk2) >= dt && tk2 < cur.tnext && tk2 < cur.tl_limit) {
-                        float p2[3];
-                        cur.position(tk2, p2);
-                        if (cur.in_box(p2)) {
-                            float I2[C];
-                            cur.template interpolate<H>(p2, I2, f);
-                            const int st = f.sample2(I, I2, dt);
-                            ++k;
-                            if (st == 1) break;
-                            kf = kf2;
-                            if (st == 2) {
-                                ++k;
-                                break;
-                            }
-                            continue;
+                        float q[3];
+                        cur.position(tk2, q);
+                        if (cur.in_box(q)) {
+                            two = true;
+#pragma unroll
+                            for (int a = 0; a < 3; ++a) p2[a] = q[a];
                         }
                     }
                 }
+                cur.template interpolate<H>(p, I, f);
+                float I2[C];
+                cur.template interpolate<H>(p2, I2, f);
+                const int st = f.sample2(I, I2, ell, two);
+                if (st == 1) {
+                    ++k;
+                    break;
+                }
+                if (two) {
+                    ++k;
+                    kf = kf2;
+                    if (st == 2) {
+                        ++k;
+                        break;
+                    }
+                }
+                continue;
+            } else {
+                cur.template interpolate<H>(p, I, f);
             }
         } else {
             cur.template average<H>(I, f);
@@ -620,7 +634,12 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
                 }
             }
         }
-        if (f.sample(I, ell)) {
+        bool stop1;
+        if constexpr (F::kPairs)
+            stop1 = f.sample2(I, I, ell, false) == 1;
+        else
+            stop1 = f.sample(I, ell);
+        if (stop1) {
             ++k;
             break;
         }
@@ -981,12 +1000,14 @@ struct DVRComposite : NoHooks {
         }
         return composite_run(lnq, K, n, ert, T, Cr, Cg, Cb, stop);
     }
-    // Two full-segment samples: both shaded first (their gathers and lookups overlap), then
-    // composited in order.  Returns 1 when the first sample terminates the ray (the second is
-    // dropped), 2 when the second does, else 0.
-    __device__ __forceinline__ int sample2(const float (&I1)[C], const float (&I2)[C], float ell) {
+    // Two samples shaded first (their gathers and lookups overlap), the first with segment ell,
+    // the second with a full one, then composited in order -- the second only when two.  Returns 1
+    // when the first sample terminates the ray (the second is dropped), 2 when the second does,
+    // else 0.
+    __device__ __forceinline__ int sample2(const float (&I1)[C], const float (&I2)[C], float ell, bool two) {
         const Shaded s1 = shade(I1, ell), s2 = shade(I2, ell);
         if (update(s1)) return 1;
+        if (!two) return 0;
         return update(s2) ? 2 : 0;
     }
     __device__ __forceinline__ bool sample(const float (&I)[C], float ell) { return update(shade(I, ell)); }
@@ -1062,9 +1083,10 @@ struct DVRCompositeH : NoHooks {
         }
         return composite_run(lnq, K, n, ert, T, Cr, Cg, Cb, stop);
     }
-    __device__ __forceinline__ int sample2(const float (&I1)[C], const float (&I2)[C], float ell) {
+    __device__ __forceinline__ int sample2(const float (&I1)[C], const float (&I2)[C], float ell, bool two) {
         const Shaded s1 = shade(I1, ell), s2 = shade(I2, ell);
         if (update(s1)) return 1;
+        if (!two) return 0;
         return update(s2) ? 2 : 0;
     }
     __device__ __forceinline__ bool sample(const float (&I)[C], float ell) { return update(shade(I, ell)); }
@@ -1121,7 +1143,7 @@ struct MIPMax : NoHooks {
         return false;
     }
     static constexpr bool kPairs = true;
-    __device__ __forceinline__ int sample2(const float (&I1)[C], const float (&I2)[C], float) {
+    __device__ __forceinline__ int sample2(const float (&I1)[C], const float (&I2)[C], float, bool) {
 #pragma unroll
         for (int c = 0; c < C; ++c) mx[c] = fmaxf(mx[c], fmaxf(I1[c], I2[c]));
         return 0;
