@@ -574,16 +574,18 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
             }
         }
         float I[C];
-        if (cur.brick) {
-            if constexpr (F::kPairs) {
-                // the next sample too when it lies in the same brick node at the same level with a
-                // full segment: both are shaded before the two are composited in order, so the
-                // gathers and lookups of the second overlap those of the first.  A sample without
-                // such a partner takes the same code with itself as the partner, composited once:
-                // one copy of the interpolation and shading in the loop.
-                bool two = false;
+        if constexpr (F::kPairs) {
+            // A brick sample takes the next sample too when it lies in the same brick node at the
+            // same level with a full segment: both are shaded before the two are composited in
+            // order, so the gathers and lookups of the second overlap those of the first.  A sample
+            // without such a partner -- and a sample of a brick-less node that starts no run --
+            // takes the same code with itself as the partner, composited once: every lane of the
+            // warp meets at one copy of the shading in the loop.
+            bool two = false;
+            const float kf2 = kf + 1.0f;
+            float I2[C];
+            if (cur.brick) {
                 float p2[3] = {p[0], p[1], p[2]};
-                const float kf2 = kf + 1.0f;
                 if (ell == dt && k + 1 < klim) {
                     const float tk2 = __fadd_rn(t0, __fmul_rn(kf2, dt));
                     if (tk2 < t1 && __fsub_rn(t1, tk2) >= dt && tk2 < cur.tnext && tk2 < cur.tl_limit) {
@@ -597,51 +599,65 @@ __device__ __forceinline__ long long march(const Geo& g, const uint16_t* __restr
                     }
                 }
                 cur.template interpolate<H>(p, I, f);
-                float I2[C];
                 cur.template interpolate<H>(p2, I2, f);
-                const int st = f.sample2(I, I2, ell, two);
-                if (st == 1) {
+            } else {
+                cur.template average<H>(I, f);
+                if constexpr (F::kRuns) if (ell == dt) {
+                    // composite the run of equal samples through this brick-less node in one step
+                    const int n = cur.run_length(k, tk, t0, t1, dt, klim);
+                    if (n >= 2) {
+                        bool stop = false;
+                        const int used = (int)f.run(I, n, dt, stop);
+                        k += used - 1;
+                        kf = (float)k;
+                        if (stop) {
+                            ++k;
+                            break;
+                        }
+                        continue;
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < C; ++c) I2[c] = I[c];
+            }
+            const int st = f.sample2(I, I2, ell, two);
+            if (st == 1) {
+                ++k;
+                break;
+            }
+            if (two) {
+                ++k;
+                kf = kf2;
+                if (st == 2) {
                     ++k;
                     break;
                 }
-                if (two) {
-                    ++k;
-                    kf = kf2;
-                    if (st == 2) {
-                        ++k;
-                        break;
-                    }
-                }
-                continue;
-            } else {
-                cur.template interpolate<H>(p, I, f);
             }
         } else {
-            cur.template average<H>(I, f);
-            if constexpr (F::kRuns) if (ell == dt) {
-                // composite the run of equal samples through this brick-less node in one step
-                const int n = cur.run_length(k, tk, t0, t1, dt, klim);
-                if (n >= 2) {
-                    bool stop = false;
-                    const int used = (int)f.run(I, n, dt, stop);
-                    k += used - 1;
-                    kf = (float)k;
-                    if (stop) {
-                        ++k;
-                        break;
+            if (cur.brick) {
+                cur.template interpolate<H>(p, I, f);
+            } else {
+                cur.template average<H>(I, f);
+                if constexpr (F::kRuns) if (ell == dt) {
+                    // composite the run of equal samples through this brick-less node in one step
+                    const int n = cur.run_length(k, tk, t0, t1, dt, klim);
+                    if (n >= 2) {
+                        bool stop = false;
+                        const int used = (int)f.run(I, n, dt, stop);
+                        k += used - 1;
+                        kf = (float)k;
+                        if (stop) {
+                            ++k;
+                            break;
+                        }
+                        continue;
                     }
-                    continue;
                 }
             }
-        }
-        bool stop1;
-        if constexpr (F::kPairs)
-            stop1 = f.sample2(I, I, ell, false) == 1;
-        else
-            stop1 = f.sample(I, ell);
-        if (stop1) {
-            ++k;
-            break;
+            if (f.sample(I, ell)) {
+                ++k;
+                break;
+            }
         }
     }
     return k;
