@@ -151,11 +151,10 @@ static void dfree(vr_ctx* c, void* p) {
         cudaFree(p);
 }
 
-// Tile order of a vr_render call: when the previous call had the same tile grid, its measured tile
-// costs order the queue (costliest first); this call's costs are kept for the next.
-static vr_status order_prepare(vr_ctx* c, RenderArgs& a, const CamParam* cams, int n, long long tiles, cudaStream_t st) {
-    if (!c->tile_order_mode) return VR_OK;
-    unsigned long long sig = 1469598103934665603ull; // FNV-1a over the grid
+// The tile grid of a call (FNV-1a over the views' sizes and the tile shape): tile costs measured
+// by one call order the queue of another only when both have the same grid.
+static unsigned long long grid_sig(const vr_ctx* c, const CamParam* cams, int n) {
+    unsigned long long sig = 1469598103934665603ull;
     auto mix = [&](long long v) {
         sig ^= (unsigned long long)v;
         sig *= 1099511628211ull;
@@ -167,6 +166,14 @@ static vr_status order_prepare(vr_ctx* c, RenderArgs& a, const CamParam* cams, i
         mix(cams[i].W);
         mix(cams[i].H);
     }
+    return sig;
+}
+
+// Tile order of a vr_render call: when the previous call had the same tile grid, its measured tile
+// costs order the queue (costliest first); this call's costs are kept for the next.
+static vr_status order_prepare(vr_ctx* c, RenderArgs& a, const CamParam* cams, int n, long long tiles, cudaStream_t st) {
+    if (!c->tile_order_mode) return VR_OK;
+    const unsigned long long sig = grid_sig(c, cams, n);
     if (tiles > c->lpt_cap) {
         CK(c, cudaDeviceSynchronize()); // the old buffers may still be in use (any stream)
         dfree(c, c->lpt_cost);
@@ -826,6 +833,14 @@ static vr_status render_backward(vr_ctx* c, const vr_camera* cams, int n, const 
         }
         CK(c, cudaMemsetAsync(c->d_gacc, 0, nb, st));
         a.dacc = c->d_gacc;
+    }
+    // the adjoint re-marches the forward's samples ray by ray: when the last vr_render had this
+    // tile grid, the tile costs it measured order the queue (costliest first), so that the long
+    // tiles do not start last (8192 tiles of a 512^2 view are under 3 per warp of the grid)
+    if (c->tile_order_mode && !c->grad_fp64 && c->lpt_have && tiles <= c->lpt_cap &&
+        grid_sig(c, c->h_cams, n) == c->lpt_sig) {
+        CK(c, launch_tile_order(c->lpt_cost, tiles, c->lpt_aux, c->lpt_order, st));
+        a.tile_order = c->lpt_order;
     }
     CK(c, launch_render_backward(a, grid_for(c, tiles, 128, 5), 128, st));
     return VR_OK;

@@ -1531,15 +1531,17 @@ struct DVRAdjoint : NoHooks {
     // Per channel, the table-entry pair (i, i+1) this lane is accumulating into and the pending
     // sums S = sum g and L = sum lam g (entry i receives S - L, entry i+1 receives L).  Samples
     // of one ray mostly stay on one pair, so shared-memory atomics happen once per change of
-    // pair instead of once per sample (32 lanes hitting one entry serialise).
+    // pair instead of once per sample (32 lanes hitting one entry serialise).  A sample's colour
+    // gradient is gC w (gC the ray's image gradient, w the sample's weight), so for colour only
+    // the weights are summed (pW, pWL) and gC is applied at the flush; opacity keeps pA, pAL.
+    // Four sums per channel instead of eight keep the lane's state in registers.
     int pk[C];
-    R pS[C][4], pL[C][4];
+    R pW[C], pWL[C], pA[C], pAL[C];
     __device__ __forceinline__ void reset() {
 #pragma unroll
         for (int c = 0; c < C; ++c) {
             pk[c] = -1;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) pS[c][q] = pL[c][q] = (R)0;
+            pW[c] = pWL[c] = pA[c] = pAL[c] = (R)0;
         }
     }
     __device__ __forceinline__ void flush(int c) {
@@ -1547,36 +1549,35 @@ struct DVRAdjoint : NoHooks {
         R* e0 = s_dtf + (c * 256 + pk[c]) * 4;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const R lo = pS[c][q] - pL[c][q];
+            const R S = q < 3 ? gC[q] * pW[c] : pA[c], L = q < 3 ? gC[q] * pWL[c] : pAL[c];
+            const R lo = S - L;
             if (lo != (R)0) atomicAdd(e0 + q, lo);
-            if (pL[c][q] != (R)0) atomicAdd(e0 + 4 + q, pL[c][q]);
-            pS[c][q] = pL[c][q] = (R)0;
+            if (L != (R)0) atomicAdd(e0 + 4 + q, L);
         }
+        pW[c] = pWL[c] = pA[c] = pAL[c] = (R)0;
     }
     __device__ __forceinline__ void flush_all() {
 #pragma unroll
         for (int c = 0; c < C; ++c) flush(c);
     }
-    // table gradient gq (rgba) of channel c at entry i, position lam, slope dT = T[i+1] - T[i], and
-    // the scale gradient (x = s I / 65535 inside (0, 1))
-    __device__ __forceinline__ void accumulate(int c, int i, R lam, const R (&dT)[4], bool inside, const R (&gq)[4],
-                                               R I) {
-        const R glam = gq[0] * dT[0] + gq[1] * dT[1] + gq[2] * dT[2] + gq[3] * dT[3];
+    // table gradient (gC w, ga) (rgba) of channel c at entry i, position lam, slope dT = T[i+1] -
+    // T[i], and the scale gradient (x = s I / 65535 inside (0, 1))
+    __device__ __forceinline__ void accumulate(int c, int i, R lam, const R (&dT)[4], bool inside, R w, R ga, R I) {
+        const R glam = w * (gC[0] * dT[0] + gC[1] * dT[1] + gC[2] * dT[2]) + ga * dT[3];
         if (i != pk[c]) {
             flush(c);
             pk[c] = i;
         }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            pS[c][q] += gq[q];
-            pL[c][q] += lam * gq[q];
-        }
+        pW[c] += w;
+        pWL[c] += lam * w;
+        pA[c] += ga;
+        pAL[c] += lam * ga;
         if (inside) dsc[c] += glam * (R)255.0f * I * (R)(1.0f / 65535.0f);
     }
-    __device__ __forceinline__ void accumulate(int c, const TFLookup<C>& t, const R (&gq)[4], float I) {
+    __device__ __forceinline__ void accumulate(int c, const TFLookup<C>& t, R w, R ga, float I) {
         const float4 Dv = s_tf[(C + c) * 256 + t.i];
         const R dT[4] = {(R)Dv.x, (R)Dv.y, (R)Dv.z, (R)Dv.w};
-        accumulate(c, t.i, (R)t.lam, dT, t.xr > 0.0f && t.xr < 1.0f, gq, (R)I);
+        accumulate(c, t.i, (R)t.lam, dT, t.xr > 0.0f && t.xr < 1.0f, w, ga, (R)I);
     }
     __device__ __forceinline__ R suffix(const R (&Cj)[3]) const {
         return -(gC[0] * (Cf[0] - Cj[0]) + gC[1] * (Cf[1] - Cj[1]) + gC[2] * (Cf[2] - Cj[2])) + gAf * Tf;
@@ -1606,9 +1607,8 @@ struct DVRAdjoint : NoHooks {
                 const double w = Tc * sd.a[c];
                 const double ga = Tc * (gC[0] * sd.rgb[c][0] + gC[1] * sd.rgb[c][1] + gC[2] * sd.rgb[c][2]) +
                                   suffix(Cj) / sd.oma[c];
-                const double gq[4] = {gC[0] * w, gC[1] * w, gC[2] * w,
-                                      sd.clamped[c] ? 0.0 : ga * (double)ell * sd.oma[c] / (1.0 - sd.al[c])};
-                accumulate(c, sd.i[c], sd.lam[c], sd.dT[c], sd.inside[c], gq, Id[c]);
+                accumulate(c, sd.i[c], sd.lam[c], sd.dT[c], sd.inside[c], w,
+                           sd.clamped[c] ? 0.0 : ga * (double)ell * sd.oma[c] / (1.0 - sd.al[c]), Id[c]);
             }
 #pragma unroll
             for (int i = 0; i < 3; ++i) Cd[i] += Td * sd.K[i];
@@ -1636,8 +1636,7 @@ struct DVRAdjoint : NoHooks {
                 const float Tc = T0 * Pc;
                 const float w = Tc * a;
                 const float ga = Tc * (gC[0] * t.r + gC[1] * t.g + gC[2] * t.b) + suffix(Cj) / oma;
-                const float gq[4] = {gC[0] * w, gC[1] * w, gC[2] * w, clamped ? 0.0f : ga * ell * oma / (1.0f - al)};
-                accumulate(c, t, gq, I[c]);
+                accumulate(c, t, w, clamped ? 0.0f : ga * ell * oma / (1.0f - al), I[c]);
             }
             Cp[0] = fmaf(T, s.r, Cp[0]);
             Cp[1] = fmaf(T, s.g, Cp[1]);
@@ -1676,9 +1675,8 @@ struct DVRAdjoint : NoHooks {
                     T0 * sd.P[c] * (gC[0] * sd.rgb[c][0] + gC[1] * sd.rgb[c][1] + gC[2] * sd.rgb[c][2]) * Sg +
                     (alpha0 * nj + beta * (nj - Sg) + gamma * Sg) / sd.oma[c];
                 const double wsum = T0 * sd.P[c] * sd.a[c] * Sg;
-                const double gq[4] = {gC[0] * wsum, gC[1] * wsum, gC[2] * wsum,
-                                      sd.clamped[c] ? 0.0 : ga * (double)ell * sd.oma[c] / (1.0 - sd.al[c])};
-                accumulate(c, sd.i[c], sd.lam[c], sd.dT[c], sd.inside[c], gq, Id[c]);
+                accumulate(c, sd.i[c], sd.lam[c], sd.dT[c], sd.inside[c], wsum,
+                           sd.clamped[c] ? 0.0 : ga * (double)ell * sd.oma[c] / (1.0 - sd.al[c]), Id[c]);
             }
 #pragma unroll
             for (int i = 0; i < 3; ++i) Cd[i] += Td * sd.K[i] * Sg;
@@ -1714,9 +1712,7 @@ struct DVRAdjoint : NoHooks {
                                  (alpha0 * nj + beta * (nj - Sg) + gamma * Sg) / oma[c];
                 const float wsum = T0 * Pw[c] * a[c] * Sg;
                 const bool clamped = !(t[c].al >= 0.0f && t[c].al <= ALPHA_MAX);
-                const float gq[4] = {gC[0] * wsum, gC[1] * wsum, gC[2] * wsum,
-                                     clamped ? 0.0f : ga * ell * oma[c] / (1.0f - al[c])};
-                accumulate(c, t[c], gq, I[c]);
+                accumulate(c, t[c], wsum, clamped ? 0.0f : ga * ell * oma[c] / (1.0f - al[c]), I[c]);
             }
         }
         return j;
@@ -1725,7 +1721,9 @@ struct DVRAdjoint : NoHooks {
 
 // 5 resident 128-thread CTAs per SM (96 registers): measured faster than 3 (127 registers) or 6.
 // D: the FP64 gradient-check mode (double sums; per-CTA sums added into a double buffer, a.dacc).
-template <int C, int VS, bool POW2, bool XF = false, bool D = false>
+// SK: the slot edge as a compile-time constant (0: read from the geometry), as in render_kernel.
+// With a.tile_order the queue hands out tiles costliest first (the forward's measured tile costs).
+template <int C, int VS, bool POW2, bool XF = false, bool D = false, int SK = 0>
 __global__ void __launch_bounds__(128, 5) render_backward_kernel(RenderArgs a) {
     using R = std::conditional_t<D, double, float>;
     extern __shared__ float4 s_tf[];
@@ -1744,6 +1742,7 @@ __global__ void __launch_bounds__(128, 5) render_backward_kernel(RenderArgs a) {
         if (lane == 0) tile = atomicAdd(a.counter, 1u);
         tile = __shfl_sync(0xffffffffu, tile, 0);
         if ((long long)tile >= a.total_tiles) break;
+        if (a.tile_order) tile = a.tile_order[tile];
         const int ci = find_camera(a.cams, a.n_cams, tile);
         const CamParam& cp = a.cams[ci];
         const long long lt = (long long)tile - cp.tile_begin;
@@ -1771,7 +1770,7 @@ __global__ void __launch_bounds__(128, 5) render_backward_kernel(RenderArgs a) {
         } else if constexpr (XF) {
             march_xf<C, VS, POW2>(a.g, a.pool, a.rnodes, cp, d, t0, t1, a.xf, fw);
         } else {
-            march<C, VS, POW2, false>(a.g, a.pool, a.rnodes, cp, d, t0, t1, fw);
+            march<C, VS, POW2, false, decltype(fw), SK>(a.g, a.pool, a.rnodes, cp, d, t0, t1, fw);
         }
         DVRAdjoint<C, D> bw;
         bw.s_tf = s_tf;
@@ -1800,7 +1799,7 @@ __global__ void __launch_bounds__(128, 5) render_backward_kernel(RenderArgs a) {
         if constexpr (XF)
             march_xf<C, VS, POW2>(a.g, a.pool, a.rnodes, cp, d, t0, t1, a.xf, bw);
         else
-            march<C, VS, POW2, false>(a.g, a.pool, a.rnodes, cp, d, t0, t1, bw);
+            march<C, VS, POW2, false, decltype(bw), SK>(a.g, a.pool, a.rnodes, cp, d, t0, t1, bw);
         bw.flush_all();
 #pragma unroll
         for (int c = 0; c < C; ++c) dsc[c] += bw.dsc[c];
@@ -2259,17 +2258,23 @@ cudaError_t launch_render(const RenderArgs& a, int mode, int fp16, int blocks, i
     }
 }
 
-template <int C, int VS, bool POW2, bool XF, bool D>
+template <int C, int VS, bool POW2, bool XF, bool D, int SK = 0>
 static void launch_bwd_one(const RenderArgs& a, int blocks, int threads, cudaStream_t st) {
     const size_t smem = (size_t)C * 512 * sizeof(float4) + (size_t)C * 1024 * (D ? sizeof(double) : sizeof(float));
-    cudaFuncSetAttribute(render_backward_kernel<C, VS, POW2, XF, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(render_backward_kernel<C, VS, POW2, XF, D, SK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
-    render_backward_kernel<C, VS, POW2, XF, D><<<blocks, threads, smem, st>>>(a);
+    render_backward_kernel<C, VS, POW2, XF, D, SK><<<blocks, threads, smem, st>>>(a);
     if (D) grad_convert_kernel<<<(C * 1024 + 255) / 256, 256, 0, st>>>(C, a.dacc, a.dtf, a.dscale);
 }
 
 template <int C, int VS, bool D>
 static void launch_bwd_d(const RenderArgs& a, int blocks, int threads, cudaStream_t st) {
+    if constexpr (!D) { // the training path: the slot edge as a constant where it is one of two
+        if (a.g.pow2 && !a.has_xf && a.g.S == SK_DVR)
+            return launch_bwd_one<C, VS, true, false, D, SK_DVR>(a, blocks, threads, st);
+        if (a.g.pow2 && !a.has_xf && a.g.S == SK_DVR16)
+            return launch_bwd_one<C, VS, true, false, D, SK_DVR16>(a, blocks, threads, st);
+    }
     if (a.g.pow2) {
         if (a.has_xf) launch_bwd_one<C, VS, true, true, D>(a, blocks, threads, st);
         else launch_bwd_one<C, VS, true, false, D>(a, blocks, threads, st);
