@@ -834,15 +834,7 @@ static vr_status render_backward(vr_ctx* c, const vr_camera* cams, int n, const 
         CK(c, cudaMemsetAsync(c->d_gacc, 0, nb, st));
         a.dacc = c->d_gacc;
     }
-    // the adjoint re-marches the forward's samples ray by ray: when the last vr_render had this
-    // tile grid, the tile costs it measured order the queue (costliest first), so that the long
-    // tiles do not start last (8192 tiles of a 512^2 view are under 3 per warp of the grid)
-    if (c->tile_order_mode && !c->grad_fp64 && c->lpt_have && tiles <= c->lpt_cap &&
-        grid_sig(c, c->h_cams, n) == c->lpt_sig) {
-        CK(c, launch_tile_order(c->lpt_cost, tiles, c->lpt_aux, c->lpt_order, st));
-        a.tile_order = c->lpt_order;
-    }
-    CK(c, launch_render_backward(a, grid_for(c, tiles, 128, 5), 128, st));
+    CK(c, launch_render_backward(a, grid_for(c, tiles, 128, 4), 128, st));
     return VR_OK;
 }
 

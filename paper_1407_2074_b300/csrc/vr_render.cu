@@ -1719,12 +1719,14 @@ struct DVRAdjoint : NoHooks {
     }
 };
 
-// 5 resident 128-thread CTAs per SM (96 registers): measured faster than 3 (127 registers) or 6.
+// 4 resident 128-thread CTAs per SM (128 registers, no spills of the lane's state): on the 512^3
+// view 3.45 ms against 3.64 ms with 5 CTAs at 96 registers (272 bytes of spill loads); tiles in
+// raster order (the forward's costliest-first order measured 3.55-3.66 ms here: neighbouring
+// tiles share bricks in L1).
 // D: the FP64 gradient-check mode (double sums; per-CTA sums added into a double buffer, a.dacc).
 // SK: the slot edge as a compile-time constant (0: read from the geometry), as in render_kernel.
-// With a.tile_order the queue hands out tiles costliest first (the forward's measured tile costs).
 template <int C, int VS, bool POW2, bool XF = false, bool D = false, int SK = 0>
-__global__ void __launch_bounds__(128, 5) render_backward_kernel(RenderArgs a) {
+__global__ void __launch_bounds__(128, 4) render_backward_kernel(RenderArgs a) {
     using R = std::conditional_t<D, double, float>;
     extern __shared__ float4 s_tf[];
     __shared__ float s_scl[MAXC];
@@ -1742,7 +1744,6 @@ __global__ void __launch_bounds__(128, 5) render_backward_kernel(RenderArgs a) {
         if (lane == 0) tile = atomicAdd(a.counter, 1u);
         tile = __shfl_sync(0xffffffffu, tile, 0);
         if ((long long)tile >= a.total_tiles) break;
-        if (a.tile_order) tile = a.tile_order[tile];
         const int ci = find_camera(a.cams, a.n_cams, tile);
         const CamParam& cp = a.cams[ci];
         const long long lt = (long long)tile - cp.tile_begin;
