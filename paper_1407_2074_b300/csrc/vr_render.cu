@@ -1719,6 +1719,8 @@ struct DVRAdjoint : NoHooks {
     }
 };
 
+constexpr unsigned BWD_REFILL = 8; // idle lanes of a warp that make it regroup (per-lane ray queue)
+
 // 4 resident 128-thread CTAs per SM (128 registers, no spills of the lane's state): on the 512^3
 // view 3.45 ms against 3.64 ms with 5 CTAs at 96 registers (272 bytes of spill loads); tiles in
 // raster order (the forward's costliest-first order measured 3.55-3.66 ms here: neighbouring
@@ -1739,7 +1741,92 @@ __global__ void __launch_bounds__(128, 4) render_backward_kernel(RenderArgs a) {
     R dsc[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) dsc[c] = (R)0;
+    bool lane_queue = false;
+    if constexpr (!XF && !D) lane_queue = a.fwd_img != 0;
+    if constexpr (!XF && !D) if (lane_queue) {
+        // Rays handed out one per lane (ray r: lane r % 32 of tile r / 32), so that a lane whose
+        // ray has ended takes the next ray instead of idling until the warp's longest ray ends.
+        // Once BWD_REFILL lanes of a warp are idle, the marching lanes stop at their next 16-step
+        // check (march's exact stop: the state before sample k stays in bw) and the warp regroups:
+        // idle lanes take new rays, stopped lanes resume at their sample.  After the queue is
+        // empty every lane marches its ray to the end.
+        __shared__ unsigned s_stop[4], s_idle[4]; // per warp of the 128-thread CTA
+        unsigned long long* rq = reinterpret_cast<unsigned long long*>(a.counter);
+        const unsigned long long nrays = (unsigned long long)a.total_tiles * 32ull;
+        const int wib = threadIdx.x >> 5;
+        bool have = false, empty = false;
+        int k0 = 0;
+        const CamParam* cpp = a.cams;
+        float d[3] = {0.0f, 0.0f, 0.0f}, t0 = 0.0f, t1 = 0.0f;
+        DVRAdjoint<C, false> bw;
+        for (;;) {
+            unsigned need = __ballot_sync(0xffffffffu, !have);
+            while (need != 0u && !empty) {
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(rq, (unsigned long long)__popc(need));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (base + (unsigned long long)__popc(need) >= nrays) empty = true; // uniform in the warp
+                if (!have) {
+                    const unsigned long long r = base + (unsigned long long)__popc(need & ((1u << lane) - 1u));
+                    if (r < nrays) {
+                        const long long tile = (long long)(r >> 5);
+                        cpp = &a.cams[find_camera(a.cams, a.n_cams, tile)];
+                        int px, py;
+                        tile_pixel(tile - cpp->tile_begin, cpp->tiles_x, a.tile_w, a.tile_h, (int)(r & 31u), px, py);
+                        if (px < cpp->W && py < cpp->H && ray_setup(*cpp, a.g, px, py, d, t0, t1)) {
+                            const long long pix = (long long)py * cpp->W + px;
+                            const float4 gl = reinterpret_cast<const float4*>(cpp->dimg)[pix];
+                            if (gl.x != 0.0f || gl.y != 0.0f || gl.z != 0.0f || gl.w != 0.0f) {
+                                // the ray's final colour and transmittance from the forward image
+                                const float4 im = reinterpret_cast<const float4*>(cpp->img)[pix];
+                                bw = DVRAdjoint<C, false>();
+                                bw.s_tf = s_tf;
+                                bw.s_scl = s_scl;
+                                bw.s_raw = s_raw;
+                                bw.s_dtf = s_dtf;
+                                bw.ert = cpp->ert;
+                                bw.gC[0] = gl.x;
+                                bw.gC[1] = gl.y;
+                                bw.gC[2] = gl.z;
+                                bw.gAf = gl.w;
+                                bw.Cf[0] = im.x;
+                                bw.Cf[1] = im.y;
+                                bw.Cf[2] = im.z;
+                                bw.Tf = 1.0f - im.w;
+#pragma unroll
+                                for (int c = 0; c < C; ++c) bw.dsc[c] = 0.0f;
+                                bw.reset();
+                                k0 = 0;
+                                have = true;
+                            }
+                        }
+                    }
+                }
+                need = __ballot_sync(0xffffffffu, !have);
+            }
+            if (__ballot_sync(0xffffffffu, have) == 0u) break; // the queue is empty and no lane holds a ray
+            if (lane == 0) {
+                s_stop[wib] = 0u;
+                s_idle[wib] = 0u;
+            }
+            __syncwarp();
+            if (have) {
+                const long long r = march<C, VS, POW2, false, DVRAdjoint<C, false>, SK>(
+                    a.g, a.pool, a.rnodes, *cpp, d, t0, t1, bw, nullptr, k0, MAX_SAMPLES, empty ? nullptr : &s_stop[wib], 0);
+                if (r < 0) {
+                    k0 = (int)(-(r + 1)); // stopped for a regrouping: resume at sample k0
+                } else {
+                    bw.flush_all();
+#pragma unroll
+                    for (int c = 0; c < C; ++c) dsc[c] += bw.dsc[c];
+                    have = false;
+                    if (!empty && atomicAdd(&s_idle[wib], 1u) + 1u >= BWD_REFILL) *(volatile unsigned*)&s_stop[wib] = 1u;
+                }
+            }
+        }
+    }
     for (;;) {
+        if (lane_queue) break;
         unsigned int tile = 0;
         if (lane == 0) tile = atomicAdd(a.counter, 1u);
         tile = __shfl_sync(0xffffffffu, tile, 0);
