@@ -251,3 +251,39 @@ def test_backward_from_forward_images():
     _grad_close(c_tf.cpu().numpy(), rtf, fp64=True)
     r.set_gradient_precision(False)
     r.close()
+
+
+def test_backward_from_images_several_views_in_one_launch():
+    """The per-lane ray queue of the backward from forward images (rays handed out one per lane
+    over the tiles of all views, a warp regrouping when lanes fall idle): one launch over three
+    views of different, ragged sizes gives the sum of the three single-view gradients (the
+    adjoint is linear in dL/dimage), up to the order of the floating-point atomics."""
+    import torch
+
+    w, vol, r, _ = _setup(ert=0.99)
+    tf = w.tf()
+    tf[..., 3] = np.minimum(1.0, tf[..., 3] * 4.0)
+    sc = np.array([1.0, 0.9, 1.1], np.float32)
+    r.set_transfer_functions(torch.from_numpy(tf), torch.from_numpy(sc))
+    cams = []
+    for i, (wd, ht) in enumerate(((40, 40), (37, 23), (64, 48))):
+        cam = dict(w.cameras[i % len(w.cameras)])
+        cam["width"], cam["height"] = wd, ht
+        cam["ert_alpha"] = 0.99
+        cams.append(cam)
+    rng = np.random.default_rng(9)
+    gs = [torch.from_numpy(rng.normal(size=(c["height"], c["width"], 4)).astype(np.float32)).cuda() for c in cams]
+    fwd = r.render(cams)
+    all_tf, all_sc = r.render_backward(cams, gs, images=fwd)
+    all_tf, all_sc = all_tf.cpu().numpy().astype(np.float64), all_sc.cpu().numpy().astype(np.float64)
+    sum_tf, sum_sc = np.zeros_like(all_tf), np.zeros_like(all_sc)
+    for cam, g, im in zip(cams, gs, fwd):
+        one = r.render([cam])[0]
+        assert torch.equal(one, im)  # a ray does not depend on the other views of the launch
+        t, s = r.render_backward([cam], [g], images=[one])
+        sum_tf += t.cpu().numpy()
+        sum_sc += s.cpu().numpy()
+    assert np.abs(all_tf).max() > 0.0
+    assert np.linalg.norm(all_tf - sum_tf) <= 1e-5 * np.linalg.norm(sum_tf)
+    assert np.abs(all_sc - sum_sc).max() <= 1e-5 * np.abs(sum_sc).max()
+    r.close()
