@@ -764,12 +764,13 @@ __device__ __forceinline__ long long march_group(const Geo& g, const uint16_t* _
 // (((m0 p0 + m1 p1) + m2 p2) + m3).  Each channel descends from its own point and keeps its own
 // node cache; the node test checks both faces because rounded transformed positions
 // need not be monotone.  Samples are composited one by one (no closed-form runs).
-template <int C, int VS, bool POW2, class F>
+template <int C, int VS, bool POW2, class F, int SK = 0>
 __device__ __forceinline__ long long march_xf(const Geo& g, const uint16_t* __restrict__ pool,
                                               const RNode* __restrict__ rn, const CamParam& cp, const float d[3],
                                               float t0, float t1, const float (*xf)[12], F& f) {
     const float dt = cp.dt;
-    const int N = g.N, M = g.M, S = g.S;
+    // SK: the slot edge as a compile-time constant (0: read from the geometry)
+    const int N = g.N, M = SK > 0 ? SK - 2 : g.M, S = SK > 0 ? SK : g.S;
     int Lstar = 0;
     float tnext = (N >= 1) ? cp.tl[1] : CUDART_INF_F;
     int nlev[C];
@@ -1298,7 +1299,7 @@ __global__ void __launch_bounds__(RENDER_MAX_THREADS, 1) render_kernel(RenderArg
             }
             long long n;
             if constexpr (XF) {
-                n = march_xf<C, VS, POW2>(a.g, a.pool, a.rnodes, *cp, dd, r0, r1, a.xf, f);
+                n = march_xf<C, VS, POW2, F, SK>(a.g, a.pool, a.rnodes, *cp, dd, r0, r1, a.xf, f);
             } else if constexpr (CONT) {
                 n = march<C, VS, POW2, H, F, SK>(a.g, a.pool, a.rnodes, *cp, dd, r0, r1, f, nullptr, 0, MAX_SAMPLES, dry,
                                           a.cont_min);
@@ -2259,7 +2260,10 @@ static cudaError_t launch_fwd_c(const RenderArgs& a, int mode, int fp16, int blo
     }
     if (a.has_xf && (mode == 0 || mode == 1)) { // per-channel transforms: FP32 interpolation
         if (mode == 0) {
-            if (p2) launch_one<C, VS, 0, true, false, true>(a, blocks, threads, st);
+            if (p2 && a.g.S == SK_DVR) launch_one<C, VS, 0, true, false, true, false, SK_DVR>(a, blocks, threads, st);
+            else if (p2 && a.g.S == SK_DVR16)
+                launch_one<C, VS, 0, true, false, true, false, SK_DVR16>(a, blocks, threads, st);
+            else if (p2) launch_one<C, VS, 0, true, false, true>(a, blocks, threads, st);
             else launch_one<C, VS, 0, false, false, true>(a, blocks, threads, st);
         } else {
             if (p2) launch_one<C, VS, 1, true, false, true>(a, blocks, threads, st);
